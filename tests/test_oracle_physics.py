@@ -1,0 +1,108 @@
+"""Physics pins of the oracle: the paper's thermodynamic-consistency claim
+(text after Eq. 16: coexistence densities and the interface given by the
+pressure tensor of Eq. 11) and Laplace's law for a static droplet (the
+equilibrium-droplet run described after Eq. 19)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle, thermo
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def _width_5_95(prof, x, rv, rl):
+    lvl = lambda fr: np.interp(rv + fr * (rl - rv), prof, x)
+    return lvl(0.95) - lvl(0.05)
+
+
+def test_flat_interface_coexistence_and_width():
+    # A periodic liquid slab started from the square-gradient equilibrium
+    # profile must stay at the Maxwell densities (within 1%) and keep the
+    # interface width W = 10 that K_INT prescribes (the paper measured
+    # 9.961104 for its droplet); 10,000 steps at T_r = 0.8.
+    N = 128
+    cfg = thermo.Config(nx=N, ny=4)
+    o = Oracle(cfg)
+    p = o.p
+    x = np.arange(N, dtype=float)
+    z = np.minimum(x - N / 4, 3 * N / 4 - x)
+    r1 = thermo.planar_profile(p.T0, cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS, cfg.K_INT, z)
+    rho = np.repeat(r1[None, :], 4, axis=0)
+    o.init_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+    c0 = o.conservation()
+    o.step(10000)
+    m = o.moments()
+    r, T = m["rho"][0], m["T"][0]
+    rv, rl = r[0], r[N // 2]
+    Mv, _, _ = thermo.maxwell(T[0], cfg.a_t, cfg.b_t, cfg.R)
+    _, Ml, _ = thermo.maxwell(T[N // 2], cfg.a_t, cfg.b_t, cfg.R)
+    assert abs(rv / Mv - 1) < 0.01
+    assert abs(rl / Ml - 1) < 0.01
+    xs = np.arange(N // 4 - 20, N // 4 + 20)
+    assert _width_5_95(r[xs], xs, rv, rl) == pytest.approx(10.0, rel=0.02)
+    # temperature stays uniform to 0.1% of T_c, velocities die out
+    assert np.abs(T / p.Tc - 0.8).max() < 1e-3
+    assert np.abs(m["ux"]).max() < 1e-5 * p.c
+    c1 = o.conservation()
+    assert c1[0] == pytest.approx(c0[0], rel=1e-12)
+    # total energy including rho eps_p: bounded drift (not a discrete invariant)
+    assert abs(c1[4] / c0[4] - 1) < 1e-3
+
+
+def test_tanh_slab_relaxes_to_coexistence():
+    # The benchmark's initial state: tanh edges of width 4 between the
+    # Maxwell densities. Latent heat makes the two bulks settle at slightly
+    # different temperatures within 10,000 steps; each bulk density must be
+    # within 1% of the Maxwell density at its own measured temperature.
+    from paper_2106_01557_gb300 import inputs
+    N = 128
+    cfg = thermo.Config(nx=N, ny=4)
+    o = Oracle(cfg)
+    p = o.p
+    rho = inputs.slab(N, 4, p.rho_v, p.rho_l, N / 4, 3 * N / 4, 4.0)
+    o.init_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+    o.step(10000)
+    m = o.moments()
+    r, T = m["rho"][0], m["T"][0]
+    Mv, _, _ = thermo.maxwell(T[0], cfg.a_t, cfg.b_t, cfg.R)
+    _, Ml, _ = thermo.maxwell(T[N // 2], cfg.a_t, cfg.b_t, cfg.R)
+    assert abs(r[0] / Mv - 1) < 0.01
+    assert abs(r[N // 2] / Ml - 1) < 0.01
+
+
+@pytest.mark.slow
+def test_laplace_law_static_droplets():
+    # Pressure jump across static droplets against 1/R (R the equimolar
+    # radius); the slope is the surface tension. Prescribed sigma = 0.01; the
+    # paper's own run measured 0.0101676 (with the cubic-velocity correction
+    # of its ref. [Huang2020], not part of this model). Here the droplets are
+    # small (R/W = 2..4), so the bound is loose: 15%.
+    N = 128
+    res = []
+    for R in (20.0, 30.0, 40.0):
+        cfg = thermo.Config(nx=N, ny=N)
+        o = Oracle(cfg)
+        p = o.p
+        yy, xx = np.meshgrid(np.arange(N) + 0.0, np.arange(N) + 0.0, indexing="ij")
+        rr = np.hypot(xx - N / 2, yy - N / 2)
+        rho = thermo.planar_profile(p.T0, cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS, cfg.K_INT, R - rr)
+        o.init_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+        o.step(10000)
+        m = o.moments()
+        r, T = m["rho"], m["T"]
+        c = N // 2
+        dp = (thermo.p_eos(r[c, c], T[c, c], cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS)
+              - thermo.p_eos(r[0, 0], T[0, 0], cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS))
+        area = ((r - r[0, 0]) / (r[c, c] - r[0, 0])).sum()
+        res.append((1.0 / np.sqrt(area / np.pi), dp))
+        # spurious currents stay small against the lattice speed
+        assert np.hypot(m["ux"], m["uy"]).max() < 1e-3 * p.c
+    x = np.array([a for a, _ in res])
+    y = np.array([b for _, b in res])
+    slope, icpt = np.polyfit(x, y, 1)
+    sigma = GOLD["simulation_parameters"]["sigma_prescribed"]
+    assert slope == pytest.approx(sigma, rel=0.15)
+    assert abs(icpt) < 0.1 * y.min()

@@ -1,0 +1,201 @@
+"""Pins of the oracle's lattice Boltzmann step against identities the paper
+and the mathematics fix: orthogonality of M (SM Eq. S2), the moments of the
+equilibria (SM Eq. S3a, S4a with Eq. 15), the pair force on a sinusoid
+(Eq. 13), exact recovery of the prescribed fields (Eq. 14), exact mass and
+momentum conservation and the g budget (Eq. 12, 14), the rest state, and
+the lattice symmetries (reflection, quarter turn) that a transposed entry or
+flipped sign in S, L or Y would break."""
+import numpy as np
+import pytest
+
+from oracle import M_and_inverse, Oracle, thermo
+from paper_2106_01557_gb300 import inputs
+
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
+def random_state(n=8, seed=0, walls=0, amp_u=0.02, **kw):
+    cfg = thermo.Config(nx=n, ny=n, walls=walls, **kw)
+    o = Oracle(cfg)
+    p = o.p
+    rho = inputs.perturbed(np.full((n, n), 0.5 * (p.rho_v + p.rho_l)), 0.8, seed)
+    ux, uy = inputs.random_velocity((n, n), amp_u * p.c, seed + 1)
+    T = inputs.perturbed(np.full((n, n), p.T0), 0.05, seed + 2)
+    o.init_fields(rho, ux, uy, T)
+    # break the exact equilibrium so that every non-equilibrium term is active
+    rng = np.random.default_rng(seed + 3)
+    o.f *= 1.0 + 0.01 * rng.uniform(-1, 1, o.f.shape)
+    o.g *= 1.0 + 0.01 * rng.uniform(-1, 1, o.g.shape)
+    return o
+
+
+def test_M_orthogonal_and_inverse():
+    M, Mi = M_and_inverse()
+    assert np.abs(M @ Mi - np.eye(9)).max() < 1e-15
+    # Lallemand-Luo basis: rows mutually orthogonal with these norms
+    assert np.array_equal(M @ M.T, np.diag([9.0, 36, 36, 6, 12, 6, 12, 4, 4]))
+    # rows 3 and 5 are the lattice velocities (SM Eq. S1 / Eq. S2 agree)
+    assert np.array_equal(M[3], EX) and np.array_equal(M[5], EY)
+
+
+def test_init_recovers_prescribed_fields():
+    o = random_state(seed=4)
+    n = o.nx
+    p = o.p
+    rho = inputs.perturbed(np.full((n, n), 0.1), 0.5, 11)
+    ux, uy = inputs.random_velocity((n, n), 0.03 * p.c, 12)
+    T = inputs.perturbed(np.full((n, n), p.T0), 0.1, 13)
+    o.init_fields(rho, ux, uy, T)
+    m = o.moments()
+    assert np.abs(m["rho"] - rho).max() < 1e-15
+    assert np.abs(m["ux"] - ux).max() < 1e-15 * p.c * 10
+    assert np.abs(m["uy"] - uy).max() < 1e-15 * p.c * 10
+    assert np.abs(m["T"] / T - 1).max() < 1e-13
+
+
+def test_equilibrium_moments_give_the_recovered_eos():
+    # On a uniform state F = 0 and f = f^eq. Its second moments must be
+    # p_BE delta + rho u u with p_BE = p_EOS + a rho^2 (Eq. 15, 17, text
+    # after Eq. 11), and g^eq must carry rho e_k and the enthalpy flux
+    # rho h_k u with rho h_k = rho e_k + p_BE (Eq. 15).
+    n = 4
+    for rho0, u0, v0, Tr in [(0.02, 0.01, -0.02, 0.8), (0.3, -0.03, 0.01, 0.7), (0.15, 0.0, 0.04, 0.9)]:
+        o = Oracle(thermo.Config(nx=n, ny=n))
+        p = o.p
+        T0 = Tr * p.Tc
+        u, v = u0 * p.c, v0 * p.c
+        o.init_fields(np.full((n, n), rho0), np.full((n, n), u), np.full((n, n), v), np.full((n, n), T0))
+        f = o.f[:, 0, 0]
+        g = o.g[:, 0, 0]
+        ex, ey = p.c * EX, p.c * EY
+        pBE = thermo.p_eos(rho0, T0, p.a_t, p.b_t, p.R, p.K_EOS) + p.a * rho0 ** 2
+        assert f.sum() == pytest.approx(rho0, rel=1e-14)
+        assert (ex * f).sum() == pytest.approx(rho0 * u, rel=1e-13, abs=1e-17)
+        assert (ex * ex * f).sum() == pytest.approx(pBE + rho0 * u * u, rel=1e-12)
+        assert (ey * ey * f).sum() == pytest.approx(pBE + rho0 * v * v, rel=1e-12)
+        assert (ex * ey * f).sum() == pytest.approx(rho0 * u * v, rel=1e-12, abs=1e-17)
+        rek = rho0 * p.cv * T0 + 0.5 * rho0 * (u * u + v * v)
+        assert g.sum() == pytest.approx(rek, rel=1e-13)
+        assert (ex * g).sum() == pytest.approx((rek + pBE) * u, rel=1e-12, abs=1e-18)
+        assert (ey * g).sum() == pytest.approx((rek + pBE) * v, rel=1e-12, abs=1e-18)
+
+
+def test_pair_force_on_sinusoid_is_exact():
+    # Eq. 13 with weights 1/3 and 1/12 on rho = r0 + A sin(k x):
+    # sum_i w_i rho(x + e_i) e_i = A cos(k x) sin(k) exactly (dx = 1).
+    n = 32
+    o = Oracle(thermo.Config(nx=n, ny=8))
+    p = o.p
+    k = 2 * np.pi / n * 3
+    x = np.arange(n)
+    rho = np.repeat((0.1 + 0.05 * np.sin(k * x))[None, :], 8, axis=0)
+    o.init_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+    m = o.moments()
+    expect = p.G2 * rho * 0.05 * np.cos(k * x)[None, :] * np.sin(k)
+    assert np.abs(m["Fpx"] - expect).max() < 1e-15 * p.G2
+    assert np.abs(m["Fpy"]).max() < 1e-16 * p.G2
+
+
+def test_rest_state_is_a_fixed_point():
+    n = 8
+    o = Oracle(thermo.Config(nx=n, ny=n))
+    p = o.p
+    o.init_fields(np.full((n, n), p.rho_l), np.zeros((n, n)), np.zeros((n, n)), np.full((n, n), p.T0))
+    f0, g0 = o.f.copy(), o.g.copy()
+    o.step(50)
+    assert np.abs(o.f - f0).max() < 1e-14 * np.abs(f0).max()
+    assert np.abs(o.g - g0).max() < 1e-14 * np.abs(g0).max()
+
+
+def test_uniform_flow_is_a_fixed_point():
+    n = 8
+    o = Oracle(thermo.Config(nx=n, ny=n))
+    p = o.p
+    o.init_fields(np.full((n, n), p.rho_v), np.full((n, n), 0.02 * p.c), np.full((n, n), -0.01 * p.c),
+                  np.full((n, n), p.T0))
+    f0 = o.f.copy()
+    o.step(20)
+    assert np.abs(o.f - f0).max() < 1e-14 * np.abs(f0).max()
+
+
+def test_exact_conservation_on_periodic_box():
+    o = random_state(seed=7)
+    p = o.p
+    c0 = o.conservation()
+    m0 = o.moments()
+    sum_g0 = o.g.sum()
+    q0 = m0["q"].sum()
+    o.step(1)
+    c1 = o.conservation()
+    # mass: F_m[0] = 0 and the rho row of m - m^eq vanishes
+    assert c1[0] == pytest.approx(c0[0], rel=1e-14)
+    # momentum: sum of F_pair cancels pairwise; no body force
+    scale = c0[0] * p.c
+    assert abs(c1[1] - c0[1]) < 1e-14 * scale
+    assert abs(c1[2] - c0[2]) < 1e-14 * scale
+    # g budget: sum g^{n+1} = sum g^n + dt sum q^n (row 0 of Eq. 12c)
+    assert o.g.sum() == pytest.approx(sum_g0 + p.dt * q0, rel=1e-14)
+    o.step(20)
+    c2 = o.conservation()
+    assert c2[0] == pytest.approx(c0[0], rel=1e-13)
+    assert abs(c2[1] - c0[1]) < 1e-13 * scale
+
+
+def test_body_force_momentum_budget():
+    o = random_state(seed=9, accel_x=1e-4, accel_y=-2e-4)
+    p = o.p
+    c0 = o.conservation()
+    o.step(3)
+    c1 = o.conservation()
+    assert c1[1] - c0[1] == pytest.approx(3 * p.dt * c0[0] * 1e-4, rel=1e-10)
+    assert c1[2] - c0[2] == pytest.approx(-3 * p.dt * c0[0] * 2e-4, rel=1e-10)
+
+
+def _rotate(a):
+    """Quarter turn of a population array (9, n, n): position (x, y) ->
+    (-y, x), direction (ex, ey) -> (-ey, ex)."""
+    perm = {0: 0, 1: 2, 2: 3, 3: 4, 4: 1, 5: 6, 6: 7, 7: 8, 8: 5}
+    out = np.empty_like(a)
+    for i, j in perm.items():
+        # new[y', x'] with x' = -y, y' = x  ->  new = rot90 of the plane
+        out[j] = np.rot90(a[i], k=1, axes=(1, 0))
+    return out
+
+
+def _mirror(a):
+    """Reflection x -> -x: (ex, ey) -> (-ex, ey)."""
+    perm = {0: 0, 1: 3, 2: 2, 3: 1, 4: 4, 5: 6, 6: 5, 7: 8, 8: 7}
+    out = np.empty_like(a)
+    for i, j in perm.items():
+        out[j] = np.roll(a[i][:, ::-1], 1, axis=1)
+    return out
+
+
+@pytest.mark.parametrize("sym", ["rotate", "mirror"])
+def test_step_commutes_with_lattice_symmetries(sym):
+    T = _rotate if sym == "rotate" else _mirror
+    a = random_state(n=8, seed=21)
+    b = Oracle(a.cfg, a.p)
+    b.set_populations(T(a.f), T(a.g))
+    a.step(3)
+    b.step(3)
+    assert np.abs(T(a.f) - b.f).max() < 1e-14 * np.abs(a.f).max()
+    assert np.abs(T(a.g) - b.g).max() < 1e-14 * np.abs(a.g).max()
+
+
+def test_single_node_collision_budget():
+    # Eq. 12b, 12c at one node: mass unchanged, momentum advanced by dt F,
+    # energy moment advanced by dt q.
+    o = random_state(seed=3)
+    p = o.p
+    rng = np.random.default_rng(5)
+    fl = o.f[:, 2, 3].copy()
+    gl = o.g[:, 2, 3].copy()
+    rho_nb = fl.sum() * (1 + 0.2 * rng.uniform(-1, 1, 9))
+    fb, gb, macro = o.collide_node(fl, gl, rho_nb)
+    rho, ux, uy, T, Fx, Fy, q, rek = macro
+    assert fb.sum() == pytest.approx(fl.sum(), rel=1e-15)
+    assert p.c * (EX * fb).sum() == pytest.approx(p.c * (EX * fl).sum() + p.dt * Fx, rel=1e-13)
+    assert p.c * (EY * fb).sum() == pytest.approx(p.c * (EY * fl).sum() + p.dt * Fy, rel=1e-13)
+    assert gb.sum() == pytest.approx(gl.sum() + p.dt * q, rel=1e-14)

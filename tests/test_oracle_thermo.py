@@ -1,0 +1,125 @@
+"""Pins of the oracle's thermodynamics against what the paper and the
+mathematics fix (Eq. 16-19 and the simulation paragraph after Eq. 19)."""
+import json
+import math
+import os
+
+import pytest
+
+from oracle import thermo
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+SP = GOLD["simulation_parameters"]
+
+
+def test_critical_point_is_stationary_inflection():
+    # Eq. 17: with the printed A, B the EOS has its critical point at (Tc, pc):
+    # p(rho_c, Tc) = pc, dp/drho = d2p/drho2 = 0 there.
+    a, b, R = SP["a_tilde"], SP["b_tilde"], SP["R"]
+    Tc, pc = thermo.critical_point(a, b, R)
+    rc = thermo.critical_density(a, b, R)
+    assert thermo.p_eos(rc, Tc, a, b, R) == pytest.approx(pc, rel=1e-9)
+    assert abs(thermo.dp_eos_drho(rc, Tc, a, b, R)) < 1e-9 * pc / rc
+    # Carnahan-Starling critical packing fraction, a textbook number
+    assert b * rc / 4.0 == pytest.approx(0.1304438842, rel=1e-8)
+
+
+def test_cs_derivative_matches_finite_difference():
+    a, b, R = 1.0, 4.0, 1.0
+    for rho in (0.02, 0.13, 0.3, 0.4):
+        h = 1e-6
+        fd = (thermo.p_cs(rho + h, 0.07, b, R) - thermo.p_cs(rho - h, 0.07, b, R)) / (2 * h)
+        assert thermo.dp_cs_drho(rho, 0.07, b, R) == pytest.approx(fd, rel=1e-8)
+
+
+def test_free_energy_is_consistent_with_eos():
+    # p = rho mu - psi and Gibbs-Duhem d mu = dp / rho at constant T
+    a, b, R, T = 1.0, 4.0, 1.0, 0.075
+    for rho in (0.01, 0.1, 0.25, 0.35):
+        p = thermo.p_eos(rho, T, a, b, R)
+        assert rho * thermo.mu(rho, T, a, b, R) - thermo.psi(rho, T, a, b, R) == pytest.approx(p, rel=1e-11, abs=1e-15)
+        h = 1e-6
+        dmu = (thermo.mu(rho + h, T, a, b, R) - thermo.mu(rho - h, T, a, b, R)) / (2 * h)
+        assert dmu == pytest.approx(thermo.dp_eos_drho(rho, T, a, b, R) / rho, rel=1e-7)
+
+
+@pytest.mark.parametrize("Tr", [0.6, 0.7, 0.8, 0.85, 0.9, 0.95])
+def test_maxwell_equal_area(Tr):
+    a, b, R = 1.0, 4.0, 1.0
+    Tc, _ = thermo.critical_point(a, b, R)
+    rv, rl, ps = thermo.maxwell(Tr * Tc, a, b, R)
+    assert rv < rl
+    assert thermo.p_eos(rv, Tr * Tc, a, b, R) == pytest.approx(ps, rel=1e-12)
+    assert thermo.p_eos(rl, Tr * Tc, a, b, R) == pytest.approx(ps, rel=1e-10)
+    # equal areas in the (v, p) plane, an independent statement of coexistence
+    scale = ps * (1.0 / rv - 1.0 / rl)
+    assert abs(thermo.equal_area_residual(Tr * Tc, rv, rl, ps, a, b, R)) < 1e-10 * scale
+
+
+def test_maxwell_near_critical_collapses():
+    Tc, _ = thermo.critical_point(1.0, 4.0, 1.0)
+    rc = thermo.critical_density(1.0, 4.0, 1.0)
+    rv, rl, _ = thermo.maxwell(0.999 * Tc, 1.0, 4.0, 1.0)
+    assert rv < rc < rl and (rl - rv) / rc < 0.2
+
+
+def test_paper_K_values_give_prescribed_sigma_and_W():
+    # The paper states that sigma = 0.01 and W = 10 at Tr0 = 0.8 imply
+    # K_EOS = 0.479820 and K_INT = 2.294922 (6 printed digits). Square-
+    # gradient theory with kappa = G^2 dx^4 / 4 (Eq. 16) and G of Eq. 18,
+    # W read as the 5%-95% width, must return the prescribed values to the
+    # precision the printed K values carry.
+    a, b, R = SP["a_tilde"], SP["b_tilde"], SP["R"]
+    Tc, _ = thermo.critical_point(a, b, R)
+    sig, W = thermo.surface_tension_and_width(SP["Tr0"] * Tc, a, b, R, SP["K_EOS"], SP["K_INT"])
+    assert sig == pytest.approx(SP["sigma_prescribed"], rel=2e-6)
+    assert W == pytest.approx(SP["W_prescribed"], rel=2e-6)
+
+
+def test_sigma_and_W_scaling():
+    # "sigma proportional to K_EOS K_INT and W proportional to K_INT" (after Eq. 19)
+    Tc, _ = thermo.critical_point(1.0, 4.0, 1.0)
+    s1, w1 = thermo.surface_tension_and_width(0.8 * Tc, 1.0, 4.0, 1.0, 0.5, 2.0)
+    s2, w2 = thermo.surface_tension_and_width(0.8 * Tc, 1.0, 4.0, 1.0, 1.0, 3.0)
+    assert s2 / s1 == pytest.approx(3.0, rel=1e-8)
+    assert w2 / w1 == pytest.approx(1.5, rel=1e-8)
+
+
+def test_planar_profile_width():
+    import numpy as np
+    Tc, _ = thermo.critical_point(1.0, 4.0, 1.0)
+    T = 0.8 * Tc
+    rv, rl, _ = thermo.maxwell(T, 1.0, 4.0, 1.0)
+    z = np.linspace(-15, 15, 601)
+    prof = thermo.planar_profile(T, 1.0, 4.0, 1.0, SP["K_EOS"], SP["K_INT"], z)
+    assert np.all(np.diff(prof) >= 0)
+    lvl = lambda frac: np.interp(rv + frac * (rl - rv), prof, z)
+    assert lvl(0.95) - lvl(0.05) == pytest.approx(10.0, rel=1e-3)
+
+
+def test_model_coefficients_and_constraints():
+    # SM: k = 1 - varpi, h = 6 varpi (1-varpi)/(1-3 varpi), b = (1-varpi)/(1-3 varpi),
+    # beta = -2/(1-varpi); with varpi = 1/6 these are 5/6, 5/3, 5/3, -12/5.
+    p = thermo.derive_params(thermo.Config())
+    assert p.kS == pytest.approx(5 / 6, rel=1e-15)
+    assert p.hS == pytest.approx(5 / 3, rel=1e-15)
+    assert p.bS == pytest.approx(5 / 3, rel=1e-15)
+    assert p.beta == pytest.approx(-12 / 5, rel=1e-15)
+    tau = lambda s: 1.0 / s - 0.5
+    assert tau(p.sp) * tau(p.sq) == pytest.approx(1 / 12, rel=1e-13)
+    assert (p.kS + 1) * tau(p.se) * tau(p.sq) == pytest.approx(1 / 12, rel=1e-13)
+    # Eq. 16 and Eq. 18
+    assert p.a == pytest.approx(p.G2 / 2, rel=1e-15)
+    assert p.kappa == pytest.approx(p.G2 / 4, rel=1e-15)
+    assert p.c == pytest.approx(math.sqrt(3) * p.cs, rel=1e-15)
+    assert p.dt == pytest.approx(1 / p.c, rel=1e-15)
+
+
+def test_sound_speed_reduces_to_repulsive_stiffness():
+    # Eq. 19 with Eq. 17: dp_EOS/drho + 2 K_EOS a~ rho = K_EOS dp_CS/drho, so
+    # c_s^2 = K_INT^2 K_EOS dp_CS/drho at rho_l (checked by finite differences).
+    cfg = thermo.Config()
+    p = thermo.derive_params(cfg)
+    h = 1e-7
+    fd = (thermo.p_cs(p.rho_l + h, p.T0, cfg.b_t, cfg.R) - thermo.p_cs(p.rho_l - h, p.T0, cfg.b_t, cfg.R)) / (2 * h)
+    assert p.cs ** 2 == pytest.approx(cfg.K_INT ** 2 * cfg.K_EOS * fd, rel=1e-8)
