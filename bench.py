@@ -1,0 +1,309 @@
+"""Throughput of the fused f+g time step (MLUPS) and its HBM roofline.
+
+Default workload: 4096 x 1024 heated-wall boiling layout (bounce-back walls
+top and bottom, 32-cell hot spot at T/Tc = 0.95 on the bottom wall, bulk at
+T/Tc = 0.8, liquid below y = 768 and vapour above, body force 1e-5 down),
+FP32 population storage -- the "FP32 plain" form every other form is
+compared against. A step is one fused launch: pull streaming, density and
+pair force, EOS, f and g collision, store, and the FP64 conservation
+reduction. The state (2 x 302 MB) is larger than L2, so no flush is needed
+between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the method has no exchange between independent cases); the value
+is the sum of lattice updates over all ranks divided by the slowest rank's
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 4096, 1024
+Y_INT = 768
+
+
+def set_size(nx, ny):
+    global NX, NY
+    NX, NY = nx, ny
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def hbm_peak(peaks):
+    for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs", "hbm"):
+        if k in peaks:
+            v = peaks[k]
+            return float(v["value"] if isinstance(v, dict) else v)
+    return 6800.0
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def boiling_case(lbm, nx, ny, precision, stream_ptr=None):
+    from paper_2106_01557_gb300 import inputs
+    x0 = inputs.hot_spot_x0(nx, 32, seed=3)
+    cfg = lbm.default_config(nx, ny, precision=precision, walls=1, accel_y=-1e-5, Tr_bottom=0.8,
+                             Tr_hot=0.95, hot_x0=x0, hot_len=32, Tr_top=0.0)
+    if stream_ptr is not None:
+        cfg.stream = stream_ptr
+    lat = lbm.Lattice(cfg)
+    p = lat.params()
+    rho = inputs.layer(nx, ny, p["rho_v"], p["rho_l"], Y_INT * ny / 1024.0, 4.0)
+    T = np.full((ny, nx), p["T0"])
+    z = np.zeros((ny, nx))
+    return lat, (rho, z, z.copy(), T)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2106_01557_gb300 import lbm
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    prec = args.precision
+    lat, fields = boiling_case(lbm, NX, NY, prec, stream_ptr=stream.cuda_stream)
+    lat.set_fields(*fields)
+    nodes = NX * NY
+    bytes_step = lat.bytes_per_step()
+
+    for _ in range(args.warmup):
+        lat.step(1)
+    lat.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        time.sleep(0.3)
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        time.sleep(0.2)
+    lat.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    stats = lat.step_stats()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    mlups = nodes * world / (ms_step * 1e-3) / 1e6
+
+    # end to end through the public API with host buffers: set fields from
+    # pinned host memory, run K steps, read the moments back to the host
+    rho, ux, uy, T = (torch.from_numpy(a).pin_memory() for a in fields)
+    outs = {k: torch.empty((NY, NX), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy", "T")}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.set_fields(rho.numpy(), ux.numpy(), uy.numpy(), T.numpy())
+    lat.step(args.steps)
+    m = lat.moments()
+    for k in outs:
+        outs[k].numpy()[...] = m[k]
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": nodes * world * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 4 * 8 * nodes / args.steps, "d2h_bytes_per_step": 4 * 8 * nodes / args.steps,
+           "what": "lbm_set_fields(host) + lbm_step(K) + lbm_moments(host) per K steps"}
+
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        for vp in ("f64", "f16s", "bf16s"):
+            variants[vp] = variant_rate(lbm, torch, vp, min(args.steps, 50))
+    return {"ms_step": ms_step, "mlups": mlups, "bytes_step": bytes_step, "clocks": clk.summary(),
+            "e2e": e2e, "stats": stats.tolist(), "variants": variants}
+
+
+def variant_rate(lbm, torch, prec, steps):
+    stream = torch.cuda.Stream()
+    lat, fields = boiling_case(lbm, NX, NY, prec, stream_ptr=stream.cuda_stream)
+    lat.set_fields(*fields)
+    lat.step(3)
+    lat.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    lat.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    out = {"mlups": NX * NY / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+           "bytes_per_lu": lat.bytes_per_step() / (NX * NY)}
+    lat.close()
+    return out
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded
+    slice of the workload (4096 x 64 rows of the same layout with walls)."""
+    from oracle import Oracle, thermo
+    from paper_2106_01557_gb300 import inputs
+    nx, ny = 4096, 64
+    cfg = thermo.Config(nx=nx, ny=ny, walls=1, accel_y=-1e-5, Tr_bottom=0.8, Tr_hot=0.95,
+                        hot_x0=inputs.hot_spot_x0(nx, 32, seed=3), hot_len=32)
+    o = Oracle(cfg)
+    p = o.p
+    rho = inputs.layer(nx, ny, p.rho_v, p.rho_l, 48.0, 4.0)
+    o.init_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+    o.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(2)
+        steps += 2
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": nx * ny * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{nx}x{ny} slice of the workload, {steps} steps, FP64, OpenMP over rows"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=NX, help="smaller lattice for profiling captures")
+    ap.add_argument("--ny", type=int, default=NY)
+    args = ap.parse_args()
+    set_size(args.nx, args.ny)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    config = {"workload": f"boiling {NX}x{NY}, walls, hot spot 32 cells, g=1e-5, {args.precision.upper()} storage",
+              "nx": NX, "ny": NY, "precision": args.precision,
+              "l2": "state (2 x 302 MB FP32) larger than L2; no flush needed",
+              "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import torch  # noqa: F401  (only to keep the launch identical)
+        per = []
+        for _ in range(args.warmup):
+            pass
+        for _ in range(max(1, args.steps if args.steps <= 3 else 3)):
+            per.append(cpu_baseline(seconds=8.0))
+        v = float(np.median([p["value"] for p in per]))
+        line = {"impl": "reference", "metric": "MLUPS of the f+g step", "value": v, "unit": "MLUPS",
+                "n_gpus": args.gpus, "steps": len(per), "warmup": args.warmup, "higher_is_better": True,
+                "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"kind": "oracle", "cores": per[0]["cores"], "sample": per[0]["sample"], "value": v},
+                "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    peaks, kind = measured_peaks()
+    hbm = hbm_peak(peaks)
+    achieved = res["bytes_step"] / (res["ms_step"] * 1e-3) / 1e9
+    line = {
+        "metric": "MLUPS of the fused f+g step (FP32 plain)", "value": res["mlups"], "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "f32": "f32", "f16s": "f16 storage / f32 math",
+                  "bf16s": "bf16 storage / f32 math"}[args.precision],
+        "data": "synthetic", "config": config,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_kind": kind,
+                     "algorithmic_bytes_per_lu": res["bytes_step"] / (NX * NY),
+                     "timing": "CUDA events over the timed steps on the launching stream / steps"},
+        "gpu_launches": args.steps,
+        "clocks": res["clocks"], "e2e": res["e2e"],
+        "variants": res["variants"],
+        "conservation_last_step": res["stats"],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

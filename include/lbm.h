@@ -1,0 +1,186 @@
+/*
+ * liblbm: GPU (sm_103a) implementation of the double-distribution-function
+ * D2Q9 lattice Boltzmann model of the liquid-vapor phase transition of
+ * Huang, Wu & Adams (PRL 2021), "Mesoscopic lattice Boltzmann modeling of
+ * the liquid-vapor phase transition".
+ *
+ * The library advances the density DF f (mass, momentum) and the total-
+ * kinetic-energy DF g (energy) by the fused per-step update of Eq. 12a-c:
+ * pair force (Eq. 13) on the density field, moments (Eq. 14), dense-gas EOS
+ * (Eq. 17), collision of f and g in moment space with the force, source,
+ * compensation and viscous-dissipation terms of Supplemental Material (SM)
+ * Eq. S3-S6, and pull streaming, with the conservation sums reduced in the
+ * same pass.
+ *
+ * Conventions used by every call:
+ *   - status: every function returns 0 (LBM_OK) or a negative LBM_ERR_*.
+ *     lbm_last_error() returns a message for the calling thread's last
+ *     failure. No call aborts the process.
+ *   - units: lattice spacing dx = 1 and R, a~, b~ as configured; the lattice
+ *     speed is c = sqrt(3) c_s with c_s from Eq. 19, so the time step is
+ *     dt = 1 / c (not 1).
+ *   - fields: row-major [ny][nx] arrays of double, index y * nx + x.
+ *   - populations: [9][ny][nx] double, direction i as in SM Eq. S1:
+ *     (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1); they are
+ *     the post-streaming (pre-collision) populations whose moments Eq. 14
+ *     defines.
+ *   - memory: the handle owns all device memory it allocates in lbm_init and
+ *     frees it in lbm_destroy. Pointers passed in are never retained past
+ *     the call. "on_device" arguments say whether a field pointer is device
+ *     memory (1) or host memory (0).
+ *   - streams: work is issued on cfg.stream (a cudaStream_t, or NULL for a
+ *     stream the handle creates). lbm_step is asynchronous; errors detected
+ *     on the device (non-finite density, a timed-out wait) are reported by
+ *     the next synchronising call (lbm_synchronize, lbm_moments,
+ *     lbm_conservation, lbm_step_stats, lbm_get_populations).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)      /* invalid argument or configuration */
+#define LBM_ERR_CUDA (-2)     /* a CUDA runtime or driver call failed */
+#define LBM_ERR_OOM (-3)      /* device or host allocation failed */
+#define LBM_ERR_DIVERGED (-4) /* non-finite or non-positive density seen */
+#define LBM_ERR_TIMEOUT (-5)  /* a device-side wait ran out its bound */
+#define LBM_ERR_STATE (-6)    /* call not valid in the handle's state */
+#define LBM_ERR_IO (-7)       /* checkpoint file could not be read/written */
+
+/* Population storage precision. Collision arithmetic is FP64 for LBM_F64
+ * and FP32 otherwise. The shifted formats store l_i - l_i^rest, with
+ * l^rest the rest equilibrium at (rho_ref, T_ref, u = 0). */
+#define LBM_F64 0
+#define LBM_F32 1
+#define LBM_F16S 2
+#define LBM_BF16S 3
+
+/* Case description. lbm_default_config() fills the paper's simulation
+ * parameters (paragraph after Eq. 19): varpi = 1/6, gamma1 = -2,
+ * gamma2 = 2, a~ = 1, b~ = 4, R = 1, Tr0 = 0.8, K_EOS = 0.479820,
+ * K_INT = 2.294922, and for the rates the paper leaves open: s_p = 1,
+ * s_eps = 1, sigma_e = sigma_eps = sigma_p = 1, tau_j = 0.5 (vapour) and
+ * 5.0 (liquid) so that lambda_l = 10 lambda_v, c_v = 3/2 R, C_ref =
+ * rho_v c_v. */
+typedef struct lbm_config {
+    int32_t nx, ny;        /* lattice size; nx >= 8, ny >= 8 */
+    int32_t precision;     /* LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S */
+    int32_t walls;         /* 0: periodic box; 1: half-way bounce-back walls
+                              at y = -1/2 and y = ny - 1/2, periodic in x */
+    double a_t, b_t, R;    /* a~, b~ of Eq. 17 and the gas constant */
+    double K_EOS, K_INT;   /* scaling factors of Eq. 17-19 */
+    double Tr0;            /* reference reduced temperature: c_s (Eq. 19) is
+                              taken at rho_l(Tr0); also T_ref of the shift */
+    double varpi, gamma1, gamma2; /* model coefficients (SM Eq. S3-S5) */
+    double s_p, s_eps;     /* f relaxation rates; s_e, s_q follow from the
+                              constraint tau_p tau_q = (k+1) tau_e tau_q = 1/12 */
+    double sig_e, sig_eps, sig_p; /* g relaxation rates (SM Eq. S5b) */
+    double tau_j_v, tau_j_l;      /* tau_j = 1/sigma_j - 1/2, linear in rho
+                                     between rho_v and rho_l (clamped);
+                                     sigma_q = sigma_j */
+    double c_v;            /* specific heat in units of R */
+    double C_ref;          /* reference volumetric heat capacity; <= 0 means
+                              rho_v(Tr0) c_v */
+    double accel_x, accel_y;      /* body acceleration a (Eq. 14: F = F_pair + rho a) */
+    double Tr_bottom, Tr_top;     /* fixed wall reduced temperatures; <= 0: adiabatic */
+    double Tr_hot;                /* reduced temperature of a hot segment of the bottom wall */
+    int32_t hot_x0, hot_len;      /* hot segment: x in [hot_x0, hot_x0 + hot_len) mod nx */
+    double rho_ref;        /* shifted storage reference density; <= 0: (rho_v + rho_l)/2 */
+    void* stream;          /* cudaStream_t to issue work on; NULL: own stream */
+    int32_t device;        /* CUDA device ordinal */
+    int32_t reserved;
+} lbm_config;
+
+/* Quantities derived in lbm_init (Eq. 16-19, SM Eq. S3-S5 constants). */
+typedef struct lbm_params {
+    double Tc, pc;          /* critical point of Eq. 17 */
+    double T0;              /* Tr0 * Tc */
+    double rho_v, rho_l;    /* Maxwell coexistence densities at T0 */
+    double p_s;             /* saturation pressure at T0 (times K_EOS) */
+    double cs, c, dt;       /* Eq. 19; c = sqrt(3) c_s; dt = 1 / c */
+    double G2, a, kappa;    /* Eq. 18, Eq. 16 */
+    double cv, Cref;
+    double beta, kS, hS, bS; /* SM: beta, k, h, b */
+    double se, sq;          /* from the relaxation constraint */
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* lbm_last_error(void);
+
+/* Fill *cfg with the defaults described above for an nx x ny box. */
+void lbm_default_config(lbm_config* cfg, int32_t nx, int32_t ny);
+
+/* Create a case: validates cfg (LBM_ERR_ARG on e.g. s outside (0,2),
+ * non-positive K, Tr0 >= 1, nx or ny < 8), derives lbm_params (Maxwell
+ * coexistence at Tr0, Eq. 16-19), allocates two device copies of the
+ * f and g planes plus reduction scratch. Populations start at zero; call
+ * lbm_set_fields or lbm_set_populations next. */
+int lbm_init(const lbm_config* cfg, lbm_handle** out);
+
+int lbm_get_params(const lbm_handle* h, lbm_params* out);
+
+/* Initial populations from macroscopic fields (rho, u_x, u_y, T), each
+ * [ny][nx] double: m = m^eq - dt/2 F_m and n = n^eq - dt/2 q_m at every
+ * node (SM Eq. S3, S4), so that Eq. 14 returns the given fields exactly.
+ * Synchronous. */
+int lbm_set_fields(lbm_handle* h, const double* rho, const double* ux,
+                   const double* uy, const double* T, int on_device);
+
+/* Advance n >= 0 time steps (Eq. 12a-c), asynchronously on the stream. */
+int lbm_step(lbm_handle* h, int n);
+
+/* Macroscopic fields of the current state (Eq. 13, 14), [ny][nx] double
+ * each; any pointer may be NULL. Synchronous. */
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy,
+                double* T, int on_device);
+
+/* Conservation record of the current state, FP64 sums over all nodes:
+ * out[0] mass, out[1..2] momentum sum rho u (Eq. 14), out[3] sum rho e_k,
+ * out[4] total energy sum (rho e_k + rho eps_p), rho eps_p = rho V_mean / 2
+ * with V_mean = -2 a rho - kappa lap rho (Eq. 8, isotropic 9-point
+ * Laplacian), out[5] max |u|. Synchronous. */
+int lbm_conservation(lbm_handle* h, double out[6]);
+
+/* The same record, as reduced inside the most recent time step for the
+ * state that step started from; out[6] = number of nodes with a non-finite
+ * or non-positive density in it, out[7] = number of time steps the handle
+ * has executed. Synchronous. */
+int lbm_step_stats(lbm_handle* h, double out[8]);
+
+/* Read / write the post-streaming populations, host arrays [9][ny][nx]
+ * double each. Synchronous. Shifted formats round on write. */
+int lbm_get_populations(lbm_handle* h, double* f, double* g);
+int lbm_set_populations(lbm_handle* h, const double* f, const double* g);
+
+/* Checkpoint: the raw stored state (both DFs, storage precision), the step
+ * counter and the configuration, to a binary file; lbm_load requires a
+ * handle created with the same nx, ny and precision. Resume is bitwise. */
+int lbm_save(lbm_handle* h, const char* path);
+int lbm_load(lbm_handle* h, const char* path);
+
+/* Wait for queued work; reports device-side errors (LBM_ERR_DIVERGED,
+ * LBM_ERR_TIMEOUT). */
+int lbm_synchronize(lbm_handle* h);
+
+/* Steps taken since init (or restored by lbm_load). */
+int64_t lbm_step_count(const lbm_handle* h);
+
+/* Bytes of population traffic one time step moves at the algorithmic
+ * minimum (one read and one write of 18 populations per node). */
+double lbm_bytes_per_step(const lbm_handle* h);
+
+int lbm_destroy(lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -152,7 +152,7 @@ class Oracle:
         return out
 
     def conservation(self):
-        """[mass, sum rho u_x, sum rho u_y, sum g, total energy, max |u|] of
+        """[mass, sum rho u_x, sum rho u_y, sum rho e_k, total energy, max |u|] of
         the current state (Eq. 6 quantities; rho e = rho e_k + rho eps_p with
         rho eps_p = rho V_mean / 2, V_mean = -2 a rho - kappa lap rho, Eq. 8)."""
         m = self.moments()
@@ -160,7 +160,7 @@ class Oracle:
         lap = laplacian9(rho, self.p.walls)
         e_tot = m["rek"] - self.p.a * rho * rho - 0.5 * self.p.kappa * rho * lap
         return np.array([rho.sum(), (rho * m["ux"]).sum(), (rho * m["uy"]).sum(),
-                         self.g.sum(), e_tot.sum(),
+                         m["rek"].sum(), e_tot.sum(),
                          np.sqrt(m["ux"] ** 2 + m["uy"] ** 2).max()])
 
     def collide_node(self, fl, gl, rho_nb):

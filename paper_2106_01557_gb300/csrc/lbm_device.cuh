@@ -1,0 +1,303 @@
+// Device-side pieces of the liquid-vapor LB model shared by the kernels:
+// storage conversion, the D2Q9 moment transforms and the per-node collision
+// (Eq. 12b, 12c with SM Eq. S3-S6), written as fixed add/sub trees.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---- storage <-> compute ---------------------------------------------------
+template <class S, class C>
+struct Store;
+template <>
+struct Store<double, double> {
+    static __device__ __forceinline__ double ld(double v, double) { return v; }
+    static __device__ __forceinline__ double st(double v, double) { return v; }
+};
+template <>
+struct Store<float, float> {
+    static __device__ __forceinline__ float ld(float v, float) { return v; }
+    static __device__ __forceinline__ float st(float v, float) { return v; }
+};
+template <>
+struct Store<__half, float> {
+    static __device__ __forceinline__ float ld(__half v, float rest) { return rest + __half2float(v); }
+    static __device__ __forceinline__ __half st(float v, float rest) { return __float2half_rn(v - rest); }
+};
+template <>
+struct Store<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float ld(__nv_bfloat16 v, float rest) { return rest + __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 st(float v, float rest) { return __float2bfloat16_rn(v - rest); }
+};
+
+template <class C>
+__device__ __forceinline__ const KC<C>& kc(const Launch& L);
+template <>
+__device__ __forceinline__ const KC<float>& kc<float>(const Launch& L) { return L.kf; }
+template <>
+__device__ __forceinline__ const KC<double>& kc<double>(const Launch& L) { return L.kd; }
+
+// m = M l (SM Eq. S2)
+template <class C>
+__device__ __forceinline__ void moments9(const C l[9], C m[9]) {
+    const C ax = l[1] + l[2] + l[3] + l[4];
+    const C dg = l[5] + l[6] + l[7] + l[8];
+    m[0] = l[0] + ax + dg;
+    m[1] = C(-4) * l[0] - ax + C(2) * dg;
+    m[2] = C(4) * l[0] - C(2) * ax + dg;
+    const C dx = l[5] - l[6] - l[7] + l[8];
+    const C dy = l[5] + l[6] - l[7] - l[8];
+    m[3] = l[1] - l[3] + dx;
+    m[4] = C(-2) * (l[1] - l[3]) + dx;
+    m[5] = l[2] - l[4] + dy;
+    m[6] = C(-2) * (l[2] - l[4]) + dy;
+    m[7] = l[1] - l[2] + l[3] - l[4];
+    m[8] = l[5] - l[6] + l[7] - l[8];
+}
+
+// l = M^-1 m = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m
+template <class C>
+__device__ __forceinline__ void populations9(const C m[9], C l[9]) {
+    const C a0 = m[0] * C(1.0 / 9.0), a1 = m[1] * C(1.0 / 36.0), a2 = m[2] * C(1.0 / 36.0);
+    const C a3 = m[3] * C(1.0 / 6.0), a4 = m[4] * C(1.0 / 12.0);
+    const C a5 = m[5] * C(1.0 / 6.0), a6 = m[6] * C(1.0 / 12.0);
+    const C a7 = m[7] * C(0.25), a8 = m[8] * C(0.25);
+    l[0] = a0 - C(4) * a1 + C(4) * a2;
+    const C axis = a0 - a1 - C(2) * a2;
+    const C px = a3 - C(2) * a4, py = a5 - C(2) * a6;
+    l[1] = axis + px + a7;
+    l[2] = axis + py - a7;
+    l[3] = axis - px + a7;
+    l[4] = axis - py - a7;
+    const C diag = a0 + C(2) * a1 + a2;
+    const C qx = a3 + a4, qy = a5 + a6;
+    l[5] = diag + qx + qy + a8;
+    l[6] = diag - qx + qy - a8;
+    l[7] = diag - qx - qy + a8;
+    l[8] = diag + qx - qy - a8;
+}
+
+// Per-node macroscopic state (Eq. 13, 14) from the pulled populations and
+// the densities of the eight neighbours rn[1..8] (rn[i] = rho(x + e_i)).
+template <class C>
+struct NodeMacro {
+    C rho, inv_rho;
+    C gx, gy;      // sum_i omega_i rho(x+e_i) e_i = grad rho (F_pair = G^2 rho grad rho)
+    C Fhx, Fhy;    // F / c
+    C uhx, uhy;    // u / c
+    C q, rek, T;
+};
+
+template <class C>
+__device__ __forceinline__ void node_macro(const KC<C>& k, const C f[9], const C g[9], const C rn[9],
+                                           NodeMacro<C>& s) {
+    C rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    // Eq. 13 weights: 1/3 on the axes, 1/12 on the diagonals
+    const C third = C(1.0 / 3.0), twelfth = C(1.0 / 12.0);
+    s.gx = third * (rn[1] - rn[3]) + twelfth * ((rn[5] - rn[7]) + (rn[8] - rn[6]));
+    s.gy = third * (rn[2] - rn[4]) + twelfth * ((rn[5] - rn[7]) + (rn[6] - rn[8]));
+    s.rho = rho;
+    s.inv_rho = C(1) / rho;
+    s.Fhx = k.G2c * rho * s.gx + rho * k.axc;
+    s.Fhy = k.G2c * rho * s.gy + rho * k.ayc;
+    const C jx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
+    const C jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
+    // Eq. 14: rho u = sum e_i f_i + dt/2 F  ->  rho u^ = j^ + dt/2 F^
+    s.uhx = (jx + k.half_dt * s.Fhx) * s.inv_rho;
+    s.uhy = (jy + k.half_dt * s.Fhy) * s.inv_rho;
+    // q = F . u = c^2 F^ . u^
+    s.q = k.c2 * (s.Fhx * s.uhx + s.Fhy * s.uhy);
+    const C sg = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    s.rek = sg + k.half_dt * s.q;
+    const C ke = C(0.5) * k.c2 * (s.uhx * s.uhx + s.uhy * s.uhy);
+    s.T = (s.rek * s.inv_rho - ke) * k.inv_cv;
+}
+
+// p_BE = p_EOS + a rho^2 with Eq. 17
+template <class C>
+__device__ __forceinline__ C p_BE(const KC<C>& k, C rho, C T) {
+    const C th = k.b4 * rho;
+    const C om = C(1) - th;
+    const C z = (C(1) + th * (C(1) + th * (C(1) - th))) / (om * om * om);
+    return k.RK * rho * T * z + k.aK_eff * rho * rho;
+}
+
+// Equilibria of f and g at one node, used by initialisation:
+// m^eq (SM Eq. S3a), F_m (S3b), n^eq (S4a), q_m (S4b).
+template <class C>
+__device__ __forceinline__ void equilibria(const KC<C>& k, const NodeMacro<C>& s, C meq[9], C Fm[9],
+                                           C neq[9], C qm[9]) {
+    const C rho = s.rho, ux = s.uhx, uy = s.uhy;
+    const C u2 = ux * ux + uy * uy;
+    const C pbe = p_BE(k, rho, s.T);
+    const C eta = pbe * k.cs2_inv - rho;
+    const C rhk = s.rek + pbe;
+    meq[0] = rho;
+    meq[1] = C(-2) * rho + C(2) * eta + C(3) * rho * u2;
+    meq[2] = rho + k.beta * eta - C(3) * rho * u2;
+    meq[3] = rho * ux;
+    meq[4] = -rho * ux;
+    meq[5] = rho * uy;
+    meq[6] = -rho * uy;
+    meq[7] = rho * (ux * ux - uy * uy);
+    meq[8] = rho * ux * uy;
+    const C Fx = s.Fhx, Fy = s.Fhy;
+    const C FU = Fx * ux + Fy * uy;
+    Fm[0] = C(0);
+    Fm[1] = C(6) * FU;
+    Fm[2] = C(-6) * FU;
+    Fm[3] = Fx;
+    Fm[4] = -Fx;
+    Fm[5] = Fy;
+    Fm[6] = -Fy;
+    Fm[7] = C(2) * (Fx * ux - Fy * uy);
+    Fm[8] = Fx * uy + Fy * ux;
+    const C E = s.rek, CT = k.Cref * s.T;
+    neq[0] = E;
+    neq[1] = C(-4) * E + (C(4) + k.g1) * CT;
+    neq[2] = C(4) * E - (C(4) - k.g2) * CT;
+    neq[3] = rhk * ux;
+    neq[4] = -rhk * ux;
+    neq[5] = rhk * uy;
+    neq[6] = -rhk * uy;
+    neq[7] = C(0);
+    neq[8] = C(0);
+    qm[0] = s.q;
+    qm[1] = k.g1 * s.q;
+    qm[2] = k.g2 * s.q;
+    qm[3] = s.q * ux;
+    qm[4] = -s.q * ux;
+    qm[5] = s.q * uy;
+    qm[6] = -s.q * uy;
+    qm[7] = C(0);
+    qm[8] = C(0);
+}
+
+// The collision of both DFs at one node (Eq. 12b, 12c). On entry f, g hold
+// the pulled populations; on exit the post-collision ones. Rows 0, 3, 5 of
+// m - m^eq + dt/2 F_m and row 0 of n - n^eq + dt/2 q_m vanish by Eq. 14,
+// so s_0, s_j and sigma_0 never act and are not applied.
+template <class C>
+__device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const NodeMacro<C>& s) {
+    const C rho = s.rho, ux = s.uhx, uy = s.uhy;
+    const C u2 = ux * ux + uy * uy;
+    const C pbe = p_BE(k, rho, s.T);
+    const C eta = pbe * k.cs2_inv - rho;
+    const C rhk = s.rek + pbe;
+    const C Fx = s.Fhx, Fy = s.Fhy;
+    const C FU = Fx * ux + Fy * uy;
+
+    // ---- f: m_bar = m + dt F_m - S (m - m^eq + dt/2 F_m - Q_m) -----------
+    C m[9];
+    moments9(f, m);
+    const C meq1 = C(-2) * rho + C(2) * eta + C(3) * rho * u2;
+    const C meq2 = rho + k.beta * eta - C(3) * rho * u2;
+    const C meq7 = rho * (ux * ux - uy * uy);
+    const C meq8 = rho * ux * uy;
+    const C Fm1 = C(6) * FU, Fm7 = C(2) * (Fx * ux - Fy * uy), Fm8 = Fx * uy + Fy * ux;
+    // Q_m of SM Eq. S6a with grad rho = F_pair / (G^2 rho)
+    const C g2 = s.gx * s.gx + s.gy * s.gy;
+    const C Q1 = C(6) * k.qc * g2;
+    const C Q7 = k.qc * (s.gx * s.gx - s.gy * s.gy);
+    const C Q8 = k.qc * s.gx * s.gy;
+    const C w1 = m[1] - meq1 + k.half_dt * Fm1 - Q1;
+    const C w2 = m[2] - meq2 - k.half_dt * Fm1 + Q1;
+    const C w4 = m[4] + rho * ux - k.half_dt * Fx;
+    const C w6 = m[6] + rho * uy - k.half_dt * Fy;
+    const C w7 = m[7] - meq7 + k.half_dt * Fm7 - Q7;
+    const C w8 = m[8] - meq8 + k.half_dt * Fm8 - Q8;
+    // S of SM Eq. S5a; omega_e = s_e/2 - 1, omega_p = s_p/2 - 1
+    const C we = C(0.5) * k.se - C(1), wp = C(0.5) * k.sp - C(1);
+    const C sqw4 = k.sq * w4, sqw6 = k.sq * w6;
+    const C Sw1 = k.se * w1 + we * (k.kS * k.seps * w2 + k.hS * (ux * sqw4 + uy * sqw6));
+    const C Sw7 = k.sp * w7 + k.bS * wp * C(2) * (ux * sqw4 - uy * sqw6);
+    const C Sw8 = k.sp * w8 + k.bS * wp * (uy * sqw4 + ux * sqw6);
+    C mb[9];
+    mb[0] = m[0];
+    mb[1] = m[1] + k.dt * Fm1 - Sw1;
+    mb[2] = m[2] - k.dt * Fm1 - k.seps * w2;
+    mb[3] = m[3] + k.dt * Fx;
+    mb[4] = m[4] - k.dt * Fx - sqw4;
+    mb[5] = m[5] + k.dt * Fy;
+    mb[6] = m[6] - k.dt * Fy - sqw6;
+    mb[7] = m[7] + k.dt * Fm7 - Sw7;
+    mb[8] = m[8] + k.dt * Fm8 - Sw8;
+    // viscous-dissipation input of Eq. 12c: (m + m_bar)/2 - m^eq, columns e, pxx, pxy
+    const C d1 = C(0.5) * (m[1] + mb[1]) - meq1;
+    const C d7 = C(0.5) * (m[7] + mb[7]) - meq7;
+    const C d8 = C(0.5) * (m[8] + mb[8]) - meq8;
+    populations9(mb, f);
+
+    // ---- g: n_bar = n + dt q_m - L (n - n^eq + dt/2 q_m) + c^2 Y d -------
+    C n[9];
+    moments9(g, n);
+    const C E = s.rek, CT = k.Cref * s.T, q = s.q;
+    const C z1 = n[1] - (C(-4) * E + (C(4) + k.g1) * CT) + k.half_dt * k.g1 * q;
+    const C z2 = n[2] - (C(4) * E - (C(4) - k.g2) * CT) + k.half_dt * k.g2 * q;
+    const C qux = q * ux, quy = q * uy;
+    const C z3 = n[3] - rhk * ux + k.half_dt * qux;
+    const C z4 = n[4] + rhk * ux - k.half_dt * qux;
+    const C z5 = n[5] - rhk * uy + k.half_dt * quy;
+    const C z6 = n[6] + rhk * uy - k.half_dt * quy;
+    // sigma_j(rho): tau_j linear in rho between rho_v and rho_l; sigma_q = sigma_j
+    C wl = (rho - k.rho_v) * k.inv_drho;
+    wl = wl < C(0) ? C(0) : (wl > C(1) ? C(1) : wl);
+    const C sj = C(1) / (k.tauj_v + k.dtauj * wl + C(0.5));
+    const C sq = sj;
+    const C wj = C(0.5) * sj - C(1);
+    // c^2 Y d of SM Eq. S6b
+    const C yx = k.c2 * (ux * (d1 * C(1.0 / 3.0) + d7) + C(2) * uy * d8);
+    const C yy = k.c2 * (uy * (d1 * C(1.0 / 3.0) - d7) + C(2) * ux * d8);
+    C nb[9];
+    nb[0] = n[0] + k.dt * q;
+    nb[1] = n[1] + k.dt * k.g1 * q - k.sige * z1;
+    nb[2] = n[2] + k.dt * k.g2 * q - k.sigeps * z2;
+    nb[3] = n[3] + k.dt * qux - (sj * z3 + sq * wj * z4) + yx;
+    nb[4] = n[4] - k.dt * qux - sq * z4 - yx;
+    nb[5] = n[5] + k.dt * quy - (sj * z5 + sq * wj * z6) + yy;
+    nb[6] = n[6] - k.dt * quy - sq * z6 - yy;
+    nb[7] = n[7] - k.sigp * n[7];
+    nb[8] = n[8] - k.sigp * n[8];
+    populations9(nb, g);
+}
+
+// Rest equilibrium of g for a fixed-temperature wall: M^-1 n^eq(rho_w c_v T_w,
+// T_w, u = 0); returns the axis and diagonal populations (equal by symmetry).
+template <class C>
+__device__ __forceinline__ void g_rest_wall(const KC<C>& k, C rho_w, C T_w, C& g_axis, C& g_diag) {
+    const C E = rho_w * k.cv * T_w, CT = k.Cref * T_w;
+    const C n1 = C(-4) * E + (C(4) + k.g1) * CT;
+    const C n2 = C(4) * E - (C(4) - k.g2) * CT;
+    const C a0 = E * C(1.0 / 9.0), a1 = n1 * C(1.0 / 36.0), a2 = n2 * C(1.0 / 36.0);
+    g_axis = a0 - a1 - C(2) * a2;
+    g_diag = a0 + C(2) * a1 + a2;
+}
+
+// Store one post-collision value at physical (x, y) of plane p, with the
+// copies the periodic ghost cells need. y may be -1 or ny for a wall ghost.
+template <class S>
+__device__ __forceinline__ void put(S* __restrict__ out, const Geometry& G, int p, int x, int y, S v) {
+    S* base = out + (long long)p * G.plane;
+    const int HX = G.HX;
+    int rows[2];
+    int nr = 1;
+    rows[0] = y;
+    if (!G.walls) {
+        if (y < 2) rows[nr++] = y + G.ny;
+        else if (y >= G.ny - 2) rows[nr++] = y - G.ny;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (r >= nr) break;
+        S* row = base + (long long)(rows[r] + 2) * G.pitch + HX;
+        row[x] = v;
+        if (x < HX) row[x + G.nx] = v;
+        if (x >= G.nx - HX) row[x - G.nx] = v;
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,659 @@
+// Host runtime of liblbm: configuration checks, parameter derivation
+// (Eq. 16-19 and the Maxwell coexistence of Eq. 17), device buffers and
+// TMA descriptors, the step loop (CUDA graphs of step pairs), and the C ABI
+// declared in include/lbm.h.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Thermodynamics of Eq. 17 (per unit K_EOS): p(rho) and the chemical
+// potential mu(rho) = d psi / d rho of the Carnahan-Starling free energy.
+// ---------------------------------------------------------------------------
+struct Eos {
+    double a, b, R, T;
+    double p(double r) const {
+        const double t = 0.25 * b * r, o = 1.0 - t;
+        return r * R * T * (1.0 + t + t * t - t * t * t) / (o * o * o) - a * r * r;
+    }
+    double dp(double r) const {
+        const double t = 0.25 * b * r, o = 1.0 - t;
+        return R * T * (1.0 + 4.0 * t + 4.0 * t * t - 4.0 * t * t * t + t * t * t * t) / (o * o * o * o) - 2.0 * a * r;
+    }
+    double mu(double r) const {
+        const double t = 0.25 * b * r, o = 1.0 - t;
+        return R * T * (std::log(r) + (4.0 * t - 3.0 * t * t) / (o * o) + t * (4.0 - 2.0 * t) / (o * o * o)) -
+               2.0 * a * r;
+    }
+};
+
+template <class F>
+double bisect(F fn, double lo, double hi, int iters = 200) {
+    double flo = fn(lo);
+    for (int k = 0; k < iters; ++k) {
+        const double mid = 0.5 * (lo + hi);
+        const double fm = fn(mid);
+        if ((fm > 0) == (flo > 0)) { lo = mid; flo = fm; }
+        else hi = mid;
+        if (hi - lo <= 1e-17 * std::fabs(hi)) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Coexistence by a different route from a pressure bisection: bisect on the
+// vapour density rho_v in (0, spinodal_v); for each candidate the liquid
+// branch density with the same pressure is found and the chemical-potential
+// mismatch is the bisection function. Then two Newton polish steps on the
+// 2x2 system p(rl) = p(rv), mu(rl) = mu(rv).
+bool maxwell(const Eos& e, double* rv_out, double* rl_out, double* ps_out) {
+    const double rmax = 4.0 / e.b;
+    // spinodals: dp = 0 on either side of the minimum of dp
+    double rmin = 0.0, dmin = 1e300;
+    for (int k = 1; k < 4000; ++k) {
+        const double r = rmax * k / 4000.0;
+        const double d = e.dp(r);
+        if (d < dmin) { dmin = d; rmin = r; }
+    }
+    if (!(dmin < 0.0)) return false;
+    const double s1 = bisect([&](double r) { return e.dp(r); }, 1e-12 * rmax, rmin);
+    const double s2 = bisect([&](double r) { return e.dp(r); }, rmin, rmax * 0.9999);
+    const double p_s2 = e.p(s2);
+    auto liquid_at = [&](double ps) {
+        double hi = s2;
+        while (e.p(hi) < ps) hi = hi + 0.5 * (rmax - hi);
+        return bisect([&](double r) { return e.p(r) - ps; }, s2, hi);
+    };
+    // lowest admissible vapour density: its pressure must reach the liquid branch
+    double lo_v = 1e-14 * rmax;
+    if (p_s2 > 0.0) lo_v = bisect([&](double r) { return e.p(r) - p_s2; }, 1e-14 * rmax, s1);
+    auto mismatch = [&](double rv) { return e.mu(liquid_at(e.p(rv))) - e.mu(rv); };
+    const double lo = lo_v * (1.0 + 1e-12), hi = s1 * (1.0 - 1e-12);
+    if ((mismatch(lo) > 0) == (mismatch(hi) > 0)) return false;
+    double rv = bisect(mismatch, lo, hi, 300);
+    double rl = liquid_at(e.p(rv));
+    for (int it = 0; it < 2; ++it) {
+        // Newton: unknowns (rv, rl); F1 = p(rl) - p(rv), F2 = mu(rl) - mu(rv);
+        // d mu / d rho = (dp / d rho) / rho
+        const double F1 = e.p(rl) - e.p(rv), F2 = e.mu(rl) - e.mu(rv);
+        const double a11 = -e.dp(rv), a12 = e.dp(rl);
+        const double a21 = -e.dp(rv) / rv, a22 = e.dp(rl) / rl;
+        const double det = a11 * a22 - a12 * a21;
+        if (!(std::fabs(det) > 0)) break;
+        const double dv = (-F1 * a22 + F2 * a12) / det;
+        const double dl = (-a11 * F2 + a21 * F1) / det;
+        if (!std::isfinite(dv) || !std::isfinite(dl)) break;
+        rv += dv;
+        rl += dl;
+    }
+    *rv_out = rv;
+    *rl_out = rl;
+    *ps_out = e.p(rv);
+    return rv > 0 && rl > rv;
+}
+
+int storage_of(int precision) {
+    switch (precision) {
+        case LBM_F64: return S_F64;
+        case LBM_F32: return S_F32;
+        case LBM_F16S: return S_F16;
+        case LBM_BF16S: return S_BF16;
+    }
+    return -1;
+}
+
+size_t elem_size(int storage) { return storage == S_F64 ? 8 : (storage == S_F32 ? 4 : 2); }
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled get_encoder() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_config cfg;
+    lbm_params prm;
+    Launch L;
+    int storage;
+    size_t esize;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;  // index of the buffer holding the current state
+    CUtensorMap tmf[2], tmg[2];
+    double* partials = nullptr;  // step_blocks x NQ
+    double* stats = nullptr;     // NQ (step) + NQ (moments)
+    unsigned* counter = nullptr; // 2 counters
+    int* status = nullptr;
+    double* scratch = nullptr;   // 9 * 2 * n doubles (populations / fields)
+    size_t scratch_elems = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS steps starting from buffer 0
+    int64_t steps = 0;
+    static constexpr int GRAPH_STEPS = 20;  // even: the graph returns to buffer 0
+};
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+void lbm_default_config(lbm_config* c, int32_t nx, int32_t ny) {
+    std::memset(c, 0, sizeof(*c));
+    c->nx = nx;
+    c->ny = ny;
+    c->precision = LBM_F32;
+    c->walls = 0;
+    c->a_t = 1.0;
+    c->b_t = 4.0;
+    c->R = 1.0;
+    c->K_EOS = 0.479820;
+    c->K_INT = 2.294922;
+    c->Tr0 = 0.8;
+    c->varpi = 1.0 / 6.0;
+    c->gamma1 = -2.0;
+    c->gamma2 = 2.0;
+    c->s_p = 1.0;
+    c->s_eps = 1.0;
+    c->sig_e = 1.0;
+    c->sig_eps = 1.0;
+    c->sig_p = 1.0;
+    c->tau_j_v = 0.5;
+    c->tau_j_l = 5.0;
+    c->c_v = 1.5;
+    c->C_ref = 0.0;
+    c->rho_ref = 0.0;
+    c->stream = nullptr;
+    c->device = 0;
+}
+
+static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
+    auto in01 = [](double s) { return s > 0.0 && s < 2.0; };
+    if (c.nx < 8 || c.ny < 8) return fail(LBM_ERR_ARG, "nx and ny must be >= 8");
+    if ((long long)c.nx * c.ny > (1ll << 31)) return fail(LBM_ERR_ARG, "lattice too large");
+    if (storage_of(c.precision) < 0) return fail(LBM_ERR_ARG, "unknown precision");
+    if (c.walls != 0 && c.walls != 1) return fail(LBM_ERR_ARG, "walls must be 0 or 1");
+    if (!(c.a_t > 0 && c.b_t > 0 && c.R > 0 && c.K_EOS > 0 && c.K_INT > 0))
+        return fail(LBM_ERR_ARG, "a~, b~, R, K_EOS, K_INT must be positive");
+    if (!(c.Tr0 > 0.3 && c.Tr0 < 1.0)) return fail(LBM_ERR_ARG, "Tr0 must lie in (0.3, 1)");
+    if (!(c.varpi > 0 && c.varpi < 1.0 / 3.0)) return fail(LBM_ERR_ARG, "varpi must lie in (0, 1/3)");
+    if (!in01(c.s_p) || !in01(c.s_eps) || !in01(c.sig_e) || !in01(c.sig_eps) || !in01(c.sig_p))
+        return fail(LBM_ERR_ARG, "relaxation rates must lie in (0, 2)");
+    if (!(c.tau_j_v > 0 && c.tau_j_l > 0)) return fail(LBM_ERR_ARG, "tau_j must be positive");
+    if (!(c.c_v > 0)) return fail(LBM_ERR_ARG, "c_v must be positive");
+    if (c.hot_len < 0 || c.hot_len > c.nx) return fail(LBM_ERR_ARG, "hot_len out of range");
+    if (!std::isfinite(c.accel_x) || !std::isfinite(c.accel_y)) return fail(LBM_ERR_ARG, "non-finite acceleration");
+
+    // Eq. 17: a~ = A R^2 Tc^2 / pc, b~ = B R Tc / pc
+    const double A = 0.4963880577294099, B = 0.1872945669467330;
+    p.Tc = (B / A) * c.a_t / (c.b_t * c.R);
+    p.pc = B * c.R * p.Tc / c.b_t;
+    p.T0 = c.Tr0 * p.Tc;
+    Eos e{c.a_t, c.b_t, c.R, p.T0};
+    double ps;
+    if (!maxwell(e, &p.rho_v, &p.rho_l, &ps)) return fail(LBM_ERR_ARG, "no liquid-vapour coexistence at Tr0");
+    p.p_s = c.K_EOS * ps;
+    // Eq. 18, 19 (dx = 1): c_s^2 = K_INT^2 (dp_EOS/drho + 2 K_EOS a~ rho) at rho_l
+    p.G2 = c.K_INT * c.K_INT * 2.0 * c.K_EOS * c.a_t;
+    const double cs2 = c.K_INT * c.K_INT * (c.K_EOS * e.dp(p.rho_l) + 2.0 * c.K_EOS * c.a_t * p.rho_l);
+    if (!(cs2 > 0)) return fail(LBM_ERR_ARG, "non-positive sound speed");
+    p.cs = std::sqrt(cs2);
+    p.c = std::sqrt(3.0) * p.cs;
+    p.dt = 1.0 / p.c;
+    p.a = 0.5 * p.G2;      // Eq. 16
+    p.kappa = 0.25 * p.G2;
+    p.cv = c.c_v * c.R;
+    p.Cref = c.C_ref > 0 ? c.C_ref : p.rho_v * p.cv;
+    const double w = c.varpi;
+    p.kS = 1.0 - w;
+    p.hS = 6.0 * w * (1.0 - w) / (1.0 - 3.0 * w);
+    p.bS = (1.0 - w) / (1.0 - 3.0 * w);
+    p.beta = -2.0 / (1.0 - w);
+    const double tau_p = 1.0 / c.s_p - 0.5;
+    const double tau_q = 1.0 / (12.0 * tau_p);
+    const double tau_e = tau_p / (p.kS + 1.0);
+    p.sq = 1.0 / (tau_q + 0.5);
+    p.se = 1.0 / (tau_e + 0.5);
+    if (!in01(p.sq) || !in01(p.se)) return fail(LBM_ERR_ARG, "s_p gives s_q or s_e outside (0, 2)");
+
+    Geometry& G = L.geo;
+    const int storage = storage_of(c.precision);
+    int bx, by, hx;
+    step_tile(storage, &bx, &by, &hx);
+    G.nx = c.nx;
+    G.ny = c.ny;
+    G.walls = c.walls;
+    G.HX = hx;
+    int pitch = ((c.nx + 2 * hx + hx - 1) / hx) * hx;
+    if (pitch < bx + 2 * hx) pitch = bx + 2 * hx;
+    G.pitch = pitch;
+    G.nyp = c.ny + 4 > by + 4 ? c.ny + 4 : by + 4;
+    G.plane = (long long)G.pitch * G.nyp;
+    G.hot_x0 = ((c.hot_x0 % c.nx) + c.nx) % c.nx;
+    G.hot_len = c.hot_len;
+
+    auto fill = [&](auto& k, auto cast) {
+        k.c = cast(p.c);
+        k.c2 = cast(p.c * p.c);
+        k.dt = cast(p.dt);
+        k.half_dt = cast(0.5 * p.dt);
+        k.G2c = cast(p.G2 / p.c);
+        k.axc = cast(c.accel_x / p.c);
+        k.ayc = cast(c.accel_y / p.c);
+        k.a = cast(p.a);
+        k.half_kappa = cast(0.5 * p.kappa);
+        k.cs2_inv = cast(1.0 / cs2);
+        k.RK = cast(c.R * c.K_EOS);
+        k.aK_eff = cast(p.a - c.a_t * c.K_EOS);
+        k.b4 = cast(0.25 * c.b_t);
+        k.inv_cv = cast(1.0 / p.cv);
+        k.cv = cast(p.cv);
+        k.Cref = cast(p.Cref);
+        k.g1 = cast(c.gamma1);
+        k.g2 = cast(c.gamma2);
+        k.beta = cast(p.beta);
+        k.kS = cast(p.kS);
+        k.hS = cast(p.hS);
+        k.bS = cast(p.bS);
+        k.se = cast(p.se);
+        k.seps = cast(c.s_eps);
+        k.sq = cast(p.sq);
+        k.sp = cast(c.s_p);
+        k.sige = cast(c.sig_e);
+        k.sigeps = cast(c.sig_eps);
+        k.sigp = cast(c.sig_p);
+        k.tauj_v = cast(c.tau_j_v);
+        k.dtauj = cast(c.tau_j_l - c.tau_j_v);
+        k.rho_v = cast(p.rho_v);
+        k.inv_drho = cast(1.0 / (p.rho_l - p.rho_v));
+        k.qc = cast(p.G2 * p.dt * p.dt / 12.0);
+        k.T_bottom = cast(c.Tr_bottom > 0 ? c.Tr_bottom * p.Tc : 0.0);
+        k.T_top = cast(c.Tr_top > 0 ? c.Tr_top * p.Tc : 0.0);
+        k.T_hot = cast(c.Tr_hot > 0 ? c.Tr_hot * p.Tc : 0.0);
+    };
+    fill(L.kd, [](double v) { return v; });
+    fill(L.kf, [](double v) { return (float)v; });
+    if (c.hot_len > 0 && !(c.Tr_hot > 0)) return fail(LBM_ERR_ARG, "hot segment needs Tr_hot > 0");
+
+    // Rest populations of the shifted formats: M^-1 m^eq and M^-1 n^eq at
+    // (rho_ref, T0, u = 0), evaluated in FP64 then rounded to FP32 once.
+    for (int i = 0; i < 18; ++i) { L.kf.rest[i] = 0.0f; L.kd.rest[i] = 0.0; }
+    if (storage == S_F16 || storage == S_BF16) {
+        const double rho = c.rho_ref > 0 ? c.rho_ref : 0.5 * (p.rho_v + p.rho_l);
+        const double T = p.T0;
+        const double th = 0.25 * c.b_t * rho, om = 1.0 - th;
+        const double pbe = c.R * c.K_EOS * rho * T * (1.0 + th + th * th - th * th * th) / (om * om * om) +
+                           (p.a - c.a_t * c.K_EOS) * rho * rho;
+        const double eta = pbe / cs2 - rho;
+        const double m0 = rho, m1 = -2.0 * rho + 2.0 * eta, m2 = rho + p.beta * eta;
+        const double E = rho * p.cv * T, CT = p.Cref * T;
+        const double n0 = E, n1 = -4.0 * E + (4.0 + c.gamma1) * CT, n2 = 4.0 * E - (4.0 - c.gamma2) * CT;
+        auto rest = [](double a, double b, double cc, double* out) {
+            const double a0 = a / 9.0, a1 = b / 36.0, a2 = cc / 36.0;
+            out[0] = a0 - 4 * a1 + 4 * a2;
+            for (int i = 1; i <= 4; ++i) out[i] = a0 - a1 - 2 * a2;
+            for (int i = 5; i <= 8; ++i) out[i] = a0 + 2 * a1 + a2;
+        };
+        double rf[9], rg[9];
+        rest(m0, m1, m2, rf);
+        rest(n0, n1, n2, rg);
+        for (int i = 0; i < 9; ++i) {
+            L.kf.rest[i] = (float)rf[i];
+            L.kf.rest[9 + i] = (float)rg[i];
+            L.kd.rest[i] = (double)L.kf.rest[i];
+            L.kd.rest[9 + i] = (double)L.kf.rest[9 + i];
+        }
+    }
+    return LBM_OK;
+}
+
+static int make_maps(lbm_handle* h) {
+    EncodeTiled enc = get_encoder();
+    if (!enc) return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    const Geometry& G = h->L.geo;
+    int bx, by, hx;
+    step_tile(h->storage, &bx, &by, &hx);
+    CUtensorMapDataType dt = h->storage == S_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                             : h->storage == S_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : h->storage == S_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint64_t dims[3] = {(cuuint64_t)G.pitch, (cuuint64_t)G.nyp, 18};
+    cuuint64_t strides[2] = {(cuuint64_t)G.pitch * h->esize, (cuuint64_t)G.plane * h->esize};
+    cuuint32_t estr[3] = {1, 1, 1};
+    cuuint32_t boxf[3] = {(cuuint32_t)(bx + 2 * hx), (cuuint32_t)(by + 4), 9};
+    cuuint32_t boxg[3] = {(cuuint32_t)(bx + 2 * hx), (cuuint32_t)(by + 2), 9};
+    for (int b = 0; b < 2; ++b) {
+        CUresult r1 = enc(&h->tmf[b], dt, 3, h->buf[b], dims, strides, boxf, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r2 = enc(&h->tmg[b], dt, 3, h->buf[b], dims, strides, boxg, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
+            return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r1) + "/" +
+                                          std::to_string((int)r2) + ")");
+    }
+    return LBM_OK;
+}
+
+static void release(lbm_handle* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (int b = 0; b < 2; ++b)
+        if (h->buf[b]) cudaFree(h->buf[b]);
+    if (h->partials) cudaFree(h->partials);
+    if (h->stats) cudaFree(h->stats);
+    if (h->counter) cudaFree(h->counter);
+    if (h->status) cudaFree(h->status);
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+int lbm_init(const lbm_config* cfg, lbm_handle** out) {
+    if (!cfg || !out) return fail(LBM_ERR_ARG, "null argument");
+    *out = nullptr;
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(LBM_ERR_OOM, "host allocation failed");
+    h->cfg = *cfg;
+    int rc = derive(h->cfg, h->prm, h->L);
+    if (rc) { delete h; return rc; }
+    h->storage = storage_of(cfg->precision);
+    h->esize = elem_size(h->storage);
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaSetDevice"); }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device);
+    if (e != cudaSuccess || sms <= 0) { delete h; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    h->L.geo.sms = sms;
+    if (cfg->stream) {
+        h->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaStreamCreate"); }
+        h->own_stream = true;
+    }
+    const Geometry& G = h->L.geo;
+    const size_t bytes = (size_t)18 * G.plane * h->esize;
+    const size_t n = (size_t)G.nx * G.ny;
+    const int nb = std::max(step_blocks(h->storage, G), moments_blocks(G));
+    h->scratch_elems = 18 * n;
+    bool ok = cudaMalloc(&h->buf[0], bytes) == cudaSuccess && cudaMalloc(&h->buf[1], bytes) == cudaSuccess &&
+              cudaMalloc(&h->partials, (size_t)nb * NQ * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&h->stats, 2 * NQ * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&h->counter, 2 * sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&h->status, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->scratch, h->scratch_elems * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release(h);
+        delete h;
+        return fail(LBM_ERR_OOM, "device allocation failed");
+    }
+    ok = cudaMemsetAsync(h->buf[0], 0, bytes, h->stream) == cudaSuccess &&
+         cudaMemsetAsync(h->buf[1], 0, bytes, h->stream) == cudaSuccess &&
+         cudaMemsetAsync(h->stats, 0, 2 * NQ * sizeof(double), h->stream) == cudaSuccess &&
+         cudaMemsetAsync(h->counter, 0, 2 * sizeof(unsigned), h->stream) == cudaSuccess &&
+         cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess &&
+         cudaStreamSynchronize(h->stream) == cudaSuccess;
+    if (!ok) { release(h); delete h; return fail(LBM_ERR_CUDA, "device initialisation failed"); }
+    rc = make_maps(h);
+    if (rc) { release(h); delete h; return rc; }
+    e = prepare_step(h->storage);
+    if (e != cudaSuccess) { release(h); delete h; return cuda_fail(e, "cudaFuncSetAttribute"); }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_get_params(const lbm_handle* h, lbm_params* out) {
+    if (!h || !out) return fail(LBM_ERR_ARG, "null argument");
+    *out = h->prm;
+    return LBM_OK;
+}
+
+static int check_status(lbm_handle* h) {
+    CK(cudaStreamSynchronize(h->stream));
+    int st = 0;
+    CK(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(cudaMemset(h->status, 0, sizeof(int)));
+        if (st & ST_TIMEOUT) return fail(LBM_ERR_TIMEOUT, "a device-side wait exceeded its bound");
+        if (st & ST_NONFINITE) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density");
+    }
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_handle* h) {
+    if (!h) return fail(LBM_ERR_ARG, "null handle");
+    return check_status(h);
+}
+
+// Copy n doubles of a caller field into the scratch area (device), or
+// use the caller's device pointer directly.
+static const double* stage_in(lbm_handle* h, const double* src, size_t off, size_t n, int on_device,
+                              cudaError_t* e) {
+    if (on_device) return src;
+    double* dst = h->scratch + off;
+    *e = cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    return dst;
+}
+
+int lbm_set_fields(lbm_handle* h, const double* rho, const double* ux, const double* uy, const double* T,
+                   int on_device) {
+    if (!h || !rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "null argument");
+    const size_t n = (size_t)h->cfg.nx * h->cfg.ny;
+    cudaError_t e = cudaSuccess;
+    const double* d[4];
+    const double* src[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k) {
+        d[k] = stage_in(h, src[k], k * n, n, on_device, &e);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    }
+    // The scatter writes every stored entry that a pull reads (including
+    // ghost copies); clear first so the unread corners are defined too.
+    const size_t bytes = (size_t)18 * h->L.geo.plane * h->esize;
+    CK(cudaMemsetAsync(h->buf[0], 0, bytes, h->stream));
+    CK(launch_init(h->storage, h->L, d[0], d[1], d[2], d[3], h->buf[0], h->stream));
+    h->cur = 0;
+    return check_status(h);
+}
+
+int lbm_set_populations(lbm_handle* h, const double* f, const double* g) {
+    if (!h || !f || !g) return fail(LBM_ERR_ARG, "null argument");
+    const size_t n = (size_t)h->cfg.nx * h->cfg.ny;
+    CK(cudaMemcpyAsync(h->scratch, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->scratch + 9 * n, g, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const size_t bytes = (size_t)18 * h->L.geo.plane * h->esize;
+    CK(cudaMemsetAsync(h->buf[0], 0, bytes, h->stream));
+    CK(launch_set_pops(h->storage, h->L, h->scratch, h->scratch + 9 * n, h->buf[0], h->stream));
+    h->cur = 0;
+    return check_status(h);
+}
+
+int lbm_get_populations(lbm_handle* h, double* f, double* g) {
+    if (!h || !f || !g) return fail(LBM_ERR_ARG, "null argument");
+    const size_t n = (size_t)h->cfg.nx * h->cfg.ny;
+    CK(launch_get_pops(h->storage, h->L, h->buf[h->cur], h->scratch, h->scratch + 9 * n, h->stream));
+    CK(cudaMemcpyAsync(f, h->scratch, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(g, h->scratch + 9 * n, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_status(h);
+}
+
+static cudaError_t step_once(lbm_handle* h, int from) {
+    return launch_step(h->storage, h->L, &h->tmf[from], &h->tmg[from], h->buf[1 - from], h->partials, h->stats,
+                       h->counter, h->status, h->stream);
+}
+
+static int build_graph(lbm_handle* h) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < lbm_handle::GRAPH_STEPS && e == cudaSuccess; ++k) e = step_once(h, k & 1);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "step launch during capture");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, int n) {
+    if (!h) return fail(LBM_ERR_ARG, "null handle");
+    if (n < 0) return fail(LBM_ERR_ARG, "negative step count");
+    while (n > 0) {
+        if (h->cur == 0 && n >= lbm_handle::GRAPH_STEPS) {
+            if (!h->graph) {
+                int rc = build_graph(h);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(h->graph, h->stream));
+            h->steps += lbm_handle::GRAPH_STEPS;
+            n -= lbm_handle::GRAPH_STEPS;
+            continue;
+        }
+        CK(step_once(h, h->cur));
+        h->cur = 1 - h->cur;
+        h->steps += 1;
+        n -= 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, double* T, int on_device) {
+    if (!h) return fail(LBM_ERR_ARG, "null handle");
+    const size_t n = (size_t)h->cfg.nx * h->cfg.ny;
+    double* outs[4] = {rho, ux, uy, T};
+    double* d[4];
+    for (int k = 0; k < 4; ++k) d[k] = outs[k] ? (on_device ? outs[k] : h->scratch + (1 + k) * n) : nullptr;
+    CK(launch_moments(h->storage, h->L, h->buf[h->cur], h->scratch, d[0], d[1], d[2], d[3], nullptr, nullptr,
+                      nullptr, h->stream));
+    if (!on_device)
+        for (int k = 0; k < 4; ++k)
+            if (outs[k]) CK(cudaMemcpyAsync(outs[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_status(h);
+}
+
+int lbm_conservation(lbm_handle* h, double out[6]) {
+    if (!h || !out) return fail(LBM_ERR_ARG, "null argument");
+    CK(launch_moments(h->storage, h->L, h->buf[h->cur], h->scratch, nullptr, nullptr, nullptr, nullptr,
+                      h->partials, h->stats + NQ, h->counter + 1, h->stream));
+    double s[NQ];
+    CK(cudaMemcpyAsync(s, h->stats + NQ, NQ * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int rc = check_status(h);
+    if (rc) return rc;
+    for (int k = 0; k < 6; ++k) out[k] = s[k];
+    if (s[6] > 0) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density");
+    return LBM_OK;
+}
+
+int lbm_step_stats(lbm_handle* h, double out[8]) {
+    if (!h || !out) return fail(LBM_ERR_ARG, "null argument");
+    double s[NQ];
+    CK(cudaMemcpyAsync(s, h->stats, NQ * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int rc = check_status(h);
+    for (int k = 0; k < 8; ++k) out[k] = s[k];
+    return rc;
+}
+
+int64_t lbm_step_count(const lbm_handle* h) { return h ? h->steps : -1; }
+
+double lbm_bytes_per_step(const lbm_handle* h) {
+    if (!h) return 0.0;
+    return 2.0 * 18.0 * (double)h->esize * (double)h->cfg.nx * (double)h->cfg.ny;
+}
+
+// Checkpoint layout: magic, version, nx, ny, precision, walls, steps, then
+// the raw stored buffer (18 ghost-padded planes).
+static const uint64_t CK_MAGIC = 0x4c424d4c56434b31ull;  // "LBMLVCK1"
+
+int lbm_save(lbm_handle* h, const char* path) {
+    if (!h || !path) return fail(LBM_ERR_ARG, "null argument");
+    int rc = check_status(h);
+    if (rc) return rc;
+    const size_t bytes = (size_t)18 * h->L.geo.plane * h->esize;
+    std::vector<unsigned char> host(bytes);
+    CK(cudaMemcpy(host.data(), h->buf[h->cur], bytes, cudaMemcpyDeviceToHost));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    int32_t hdr[4] = {h->cfg.nx, h->cfg.ny, h->cfg.precision, h->cfg.walls};
+    bool ok = std::fwrite(&CK_MAGIC, 8, 1, fp) == 1 && std::fwrite(hdr, sizeof hdr, 1, fp) == 1 &&
+              std::fwrite(&h->steps, 8, 1, fp) == 1 && std::fwrite(host.data(), 1, bytes, fp) == bytes;
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(LBM_ERR_IO, std::string("write failed: ") + path);
+}
+
+int lbm_load(lbm_handle* h, const char* path) {
+    if (!h || !path) return fail(LBM_ERR_ARG, "null argument");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    uint64_t magic = 0;
+    int32_t hdr[4];
+    int64_t steps = 0;
+    const size_t bytes = (size_t)18 * h->L.geo.plane * h->esize;
+    std::vector<unsigned char> host(bytes);
+    bool ok = std::fread(&magic, 8, 1, fp) == 1 && std::fread(hdr, sizeof hdr, 1, fp) == 1 &&
+              std::fread(&steps, 8, 1, fp) == 1;
+    if (ok && (magic != CK_MAGIC || hdr[0] != h->cfg.nx || hdr[1] != h->cfg.ny || hdr[2] != h->cfg.precision ||
+               hdr[3] != h->cfg.walls)) {
+        std::fclose(fp);
+        return fail(LBM_ERR_ARG, "checkpoint does not match this handle's lattice");
+    }
+    ok = ok && std::fread(host.data(), 1, bytes, fp) == bytes;
+    std::fclose(fp);
+    if (!ok) return fail(LBM_ERR_IO, std::string("read failed: ") + path);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(h->buf[0], host.data(), bytes, cudaMemcpyHostToDevice));
+    h->cur = 0;
+    h->steps = steps;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle* h) {
+    if (!h) return LBM_OK;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Internal declarations shared by the host runtime and the kernels of liblbm.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Device status word bits (set by kernels, read and cleared by the host).
+enum : int { ST_TIMEOUT = 1, ST_NONFINITE = 2 };
+
+// Number of FP64 quantities in one conservation record.
+constexpr int NQ = 8;
+
+// Physical and model scalars in the kernel's compute type. Everything the
+// collision needs is precomputed here so that a node update does no
+// parameter arithmetic.
+template <class C>
+struct KC {
+    C c, c2, dt, half_dt;
+    C G2c;           // G^2 / c   (F^ = F / c)
+    C axc, ayc;      // a / c
+    C a, half_kappa; // Eq. 16 a and kappa / 2 (total-energy diagnostic)
+    C cs2_inv;       // 1 / c_s^2
+    C RK, aK_eff, b4;   // p_BE = RK rho T Z(b4 rho) + aK_eff rho^2
+    C inv_cv, cv, Cref;
+    C g1, g2, beta, kS, hS, bS;
+    C se, seps, sq, sp, sige, sigeps, sigp;
+    C tauj_v, dtauj, rho_v, inv_drho;
+    C qc;            // G^2 dt^2 / 12 of SM Eq. S6a (dx = 1)
+    C T_bottom, T_top, T_hot;
+    C rest[18];      // shifted-storage rest populations (f 0..8, g 9..17)
+};
+
+struct Geometry {
+    int nx, ny, walls, HX;
+    int pitch;       // padded row length in elements (multiple of HX)
+    int nyp;         // padded number of rows (ny + 4 at least)
+    long long plane; // elements per plane
+    int hot_x0, hot_len;
+    int sms;         // persistent grid size (one CTA per SM)
+};
+
+struct Launch {
+    Geometry geo;
+    KC<float> kf;
+    KC<double> kd;
+};
+
+// Storage kinds
+enum { S_F64 = 0, S_F32 = 1, S_F16 = 2, S_BF16 = 3 };
+
+// Host-side launchers (lbm_kernels.cu). All return cudaError_t of the launch.
+cudaError_t launch_step(int storage, const Launch& L, const CUtensorMap* tmf, const CUtensorMap* tmg,
+                        void* out, double* partials, double* stats, unsigned* counter, int* status,
+                        cudaStream_t s);
+void step_tile(int storage, int* bx, int* by, int* hx);
+int step_blocks(int storage, const Geometry& g);
+size_t step_smem_bytes(int storage);
+cudaError_t prepare_step(int storage);  // per-device kernel attributes; call before capture
+
+cudaError_t launch_init(int storage, const Launch& L, const double* rho, const double* ux,
+                        const double* uy, const double* T, void* buf, cudaStream_t s);
+cudaError_t launch_set_pops(int storage, const Launch& L, const double* f, const double* g, void* buf,
+                            cudaStream_t s);
+cudaError_t launch_get_pops(int storage, const Launch& L, const void* buf, double* f, double* g,
+                            cudaStream_t s);
+cudaError_t launch_moments(int storage, const Launch& L, const void* buf, double* rho_scratch,
+                           double* rho, double* ux, double* uy, double* T, double* partials,
+                           double* stats, unsigned* counter, cudaStream_t s);
+int moments_blocks(const Geometry& g);
+
+}  // namespace lbm

@@ -1,0 +1,411 @@
+// Fused f+g time step of the liquid-vapor LB model (Eq. 12a-c, 13, 14):
+// one persistent CTA per SM walks BX x BY tiles of the lattice.
+//
+//  1. One elected thread issues two 3-D TMA tile loads (all nine f planes of
+//     the tile plus a 2-row / HX-column halo; all nine g planes plus a
+//     1-row / HX-column halo) from the ghost-padded state into shared
+//     memory, completing on an mbarrier (bounded wait). Two stages: the
+//     next tile's copies are in flight while the current tile computes.
+//  2. The density of the tile and its one-node ring is formed from the
+//     pulled f populations in shared memory (pull streaming, Eq. 12a).
+//  3. Each node pulls its 18 populations, evaluates the pair force on the
+//     shared density tile (Eq. 13), the moments (Eq. 14), the EOS (Eq. 17),
+//     collides f and g (Eq. 12b, 12c), and stores the post-collision
+//     populations at its own node: coalesced row stores, plus copies into
+//     the periodic ghost cells or the reflected value into a wall ghost row.
+//  4. The conservation sums of the state entering the step are reduced in
+//     FP64 (warp shuffles, then a fixed-order last-block pass), so the
+//     result is deterministic.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int NT = 512;  // threads per CTA (one persistent CTA per SM)
+
+// D2Q9 directions (SM Eq. S1), e_i / c
+__host__ __device__ constexpr int EXf(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int EYf(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bound on any wait for an mbarrier phase: 2 s of wall time.
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+template <class S>
+struct Tile;
+template <>
+struct Tile<double> { static constexpr int BX = 32, BY = 16, HX = 2; };
+template <>
+struct Tile<float> { static constexpr int BX = 64, BY = 16, HX = 4; };
+template <>
+struct Tile<__half> { static constexpr int BX = 64, BY = 32, HX = 8; };
+template <>
+struct Tile<__nv_bfloat16> { static constexpr int BX = 64, BY = 32, HX = 8; };
+
+template <class S, class C>
+struct Smem {
+    static constexpr int BX = Tile<S>::BX, BY = Tile<S>::BY, HX = Tile<S>::HX;
+    static constexpr int WX = BX + 2 * HX;       // row width of a staged plane
+    static constexpr int FR = BY + 4;            // staged f rows
+    static constexpr int GR = BY + 2;            // staged g rows
+    static constexpr int F_BYTES = 9 * FR * WX * (int)sizeof(S);
+    static constexpr int G_BYTES = 9 * GR * WX * (int)sizeof(S);
+    static constexpr int STAGE = ((F_BYTES + 127) / 128) * 128 + ((G_BYTES + 127) / 128) * 128;
+    static constexpr int G_OFF = ((F_BYTES + 127) / 128) * 128;  // within a stage
+    static constexpr int RX = BX + 2, RY = BY + 2;               // density tile with ring
+    static constexpr int R_OFF = 2 * STAGE;
+    static constexpr int BYTES = R_OFF + (int)sizeof(C) * RX * RY + 128;  // + alignment slack
+};
+
+// Wall ghost-row stores of a node next to a wall: the populations leaving
+// through the wall come back reversed at the next pull (half-way bounce-back
+// of f; of g adiabatic, or anti-bounce-back on a fixed-temperature segment).
+template <class S, class C>
+__device__ __noinline__ void wall_store(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
+                                        const C* f, const C* g, C rho, const C* rest) {
+    const bool bottom = (y == 0);
+    const int yg = bottom ? -1 : G.ny;
+    const C Tw = bottom ? k.T_bottom : k.T_top;
+    for (int j = 0; j < 3; ++j) {
+        // leaving directions (4, 7, 8) at the bottom, (2, 5, 6) at the top
+        const int i = bottom ? (j == 0 ? 4 : (j == 1 ? 7 : 8)) : (j == 0 ? 2 : (j == 1 ? 5 : 6));
+        const int opp = (i == 2) ? 4 : (i == 4) ? 2 : (i == 5) ? 7 : (i == 6) ? 8 : (i == 7) ? 5 : 6;
+        const int ex = (i == 5 || i == 8) ? 1 : ((i == 6 || i == 7) ? -1 : 0);
+        int xg = x + ex;
+        xg = xg < 0 ? xg + G.nx : (xg >= G.nx ? xg - G.nx : xg);
+        C T_link = Tw;
+        if (bottom && G.hot_len > 0) {
+            int dxh = (xg - G.hot_x0) % G.nx;
+            if (dxh < 0) dxh += G.nx;
+            if (dxh < G.hot_len) T_link = k.T_hot;
+        }
+        C gv = g[i];
+        if (T_link > C(0)) {
+            C ga, gd;
+            g_rest_wall(k, rho, T_link, ga, gd);
+            gv = C(2) * (j == 0 ? ga : gd) - g[i];
+        }
+        put<S>(out, G, opp, xg, yg, Store<S, C>::st(f[i], rest[opp]));
+        put<S>(out, G, 9 + opp, xg, yg, Store<S, C>::st(gv, rest[9 + opp]));
+    }
+}
+
+template <class C>
+__device__ __forceinline__ C fast_div(C a, C b) { return a / b; }
+template <>
+__device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
+
+// Per-thread partial sums stay in the compute type (FP64 is a narrow pipe on
+// this GPU); they are widened to FP64 once per CTA.
+template <class C>
+struct Acc {
+    C mass, mx, my, ek, et, u2max, bad;
+};
+
+template <class S, class C>
+__global__ void __launch_bounds__(NT, 1)
+    k_step(const __grid_constant__ CUtensorMap tmf, const __grid_constant__ CUtensorMap tmg,
+           S* __restrict__ out, const __grid_constant__ Launch L, double* __restrict__ partials,
+           double* __restrict__ stats, unsigned* __restrict__ counter, int* __restrict__ status) {
+    using SM = Smem<S, C>;
+    constexpr int BX = SM::BX, BY = SM::BY, HX = SM::HX, WX = SM::WX;
+    constexpr int FR = SM::FR, GR = SM::GR, RX = SM::RX, RY = SM::RY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ C red[NT / 32][7];
+    __shared__ bool last;
+    // TMA destinations start on a 128-byte boundary (the launch adds 128 bytes)
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+
+    const Geometry& G = L.geo;
+    const KC<C>& k = kc<C>(L);
+    C* srho = reinterpret_cast<C*>(smem + SM::R_OFF);
+    const int tid = threadIdx.x;
+    const int ntx = (G.nx + BX - 1) / BX, nty = (G.ny + BY - 1) / BY;
+    const int ntiles = ntx * nty;
+
+    auto issue = [&](int tile, int stage) {
+        const int tx0 = (tile % ntx) * BX, ty0 = (tile / ntx) * BY;
+        unsigned char* st = smem + stage * SM::STAGE;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[stage], (uint32_t)(SM::F_BYTES + SM::G_BYTES));
+        // padded coordinates: x_p = x + HX, y_p = y + 2
+        tma_load_3d(st, &tmf, tx0, ty0, 0, &bar[stage]);                 // rows ty0-2 .. ty0+BY+1
+        tma_load_3d(st + SM::G_OFF, &tmg, tx0, ty0 + 1, 9, &bar[stage]);  // rows ty0-1 .. ty0+BY
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+
+    const C* rest = k.rest;
+    Acc<C> acc = {0, 0, 0, 0, 0, 0, 0};
+    bool ok = true;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int stage = it & 1;
+        const int next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles) issue(next, stage ^ 1);
+        bool timed_out = false;
+        {
+            const uint32_t parity = (it >> 1) & 1;
+            const uint64_t t0 = globaltimer_ns();
+            while (!mbar_try_wait(&bar[stage], parity)) {
+                if (globaltimer_ns() - t0 > WAIT_NS) { timed_out = true; break; }
+            }
+        }
+        if (__syncthreads_or(timed_out)) { ok = false; break; }
+
+        const S* sf = reinterpret_cast<const S*>(smem + stage * SM::STAGE);
+        const S* sg = reinterpret_cast<const S*>(smem + stage * SM::STAGE + SM::G_OFF);
+        const int tx0 = (tile % ntx) * BX, ty0 = (tile / ntx) * BY;
+
+        // ---- density on tile + ring (pull sums from staged f) --------------
+        for (int idx = tid; idx < RX * RY; idx += NT) {
+            const int rx = idx % RX, ry = idx / RX;
+            const int gy = ty0 + ry - 1;
+            int sy = ry + 1;  // staged row of this node: y - (ty0 - 2)
+            if (G.walls) {    // density beyond a wall = adjacent fluid node's
+                if (gy < 0) sy -= gy;
+                else if (gy >= G.ny) sy -= gy - (G.ny - 1);
+            }
+            const S* p = sf + sy * WX + rx - 1 + HX;
+            C r = C(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) r += Store<S, C>::ld(p[i * FR * WX - EYf(i) * WX - EXf(i)], rest[i]);
+            srho[idx] = r;
+        }
+        __syncthreads();
+
+        const int lx = tid % BX;
+        const int x = tx0 + lx;
+        for (int ly = tid / BX; ly < BY; ly += NT / BX) {
+            const int y = ty0 + ly;
+            if (x >= G.nx || y >= G.ny) continue;
+            C f[9], g[9], rn[9];
+            const S* pf = sf + (ly + 2) * WX + lx + HX;
+            const S* pg = sg + (ly + 1) * WX + lx + HX;
+            const C* pr = srho + (ly + 1) * RX + lx + 1;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                f[i] = Store<S, C>::ld(pf[i * FR * WX - EYf(i) * WX - EXf(i)], rest[i]);
+                g[i] = Store<S, C>::ld(pg[i * GR * WX - EYf(i) * WX - EXf(i)], rest[9 + i]);
+                rn[i] = pr[EYf(i) * RX + EXf(i)];
+            }
+            NodeMacro<C> s;
+            node_macro(k, f, g, rn, s);
+            {   // conservation record of the entering state
+                const C rho = s.rho;
+                acc.mass += rho;
+                acc.mx += rho * s.uhx;
+                acc.my += rho * s.uhy;
+                acc.ek += s.rek;
+                const C third = C(1.0 / 3.0), twelfth = C(1.0 / 12.0);
+                const C lap = C(2) * (third * ((rn[1] + rn[2]) + (rn[3] + rn[4])) +
+                                      twelfth * ((rn[5] + rn[6]) + (rn[7] + rn[8])) - C(5.0 / 3.0) * s.rho);
+                acc.et += s.rek - k.a * s.rho * s.rho - k.half_kappa * s.rho * lap;
+                const C u2 = s.uhx * s.uhx + s.uhy * s.uhy;
+                acc.u2max = u2 > acc.u2max ? u2 : acc.u2max;
+                if (!(rho > C(0)) || !isfinite(rho) || !isfinite(u2)) acc.bad += C(1);
+            }
+            collide(k, f, g, s);
+
+            // ---- store at own node (pull scheme) ----------------------------
+            const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
+            if (interior) {
+                S* o = out + (long long)(y + 2) * G.pitch + HX + x;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    o[i * G.plane] = Store<S, C>::st(f[i], rest[i]);
+                    o[(9 + i) * G.plane] = Store<S, C>::st(g[i], rest[9 + i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    put<S>(out, G, i, x, y, Store<S, C>::st(f[i], rest[i]));
+                    put<S>(out, G, 9 + i, x, y, Store<S, C>::st(g[i], rest[9 + i]));
+                }
+            }
+            // ---- walls: a population leaving through a wall returns reversed
+            if (G.walls && (y == 0 || y == G.ny - 1)) wall_store<S, C>(out, G, k, x, y, f, g, s.rho, rest);
+        }
+        __syncthreads();  // stage and density tile free for reuse
+    }
+    if (!ok && tid == 0) {
+        atomicOr(status, ST_TIMEOUT);
+        // give the copies in flight (this iteration's and the next one's) a
+        // bounded chance to land before exiting
+        for (int j = it; j <= it + 1; ++j) {
+            const uint64_t t0 = globaltimer_ns();
+            while (!mbar_try_wait(&bar[j & 1], (j >> 1) & 1) && globaltimer_ns() - t0 < WAIT_NS) {}
+        }
+    }
+
+    // ---- block reduction: compute type within warps, FP64 across warps -----
+    C v[7] = {acc.mass, acc.mx, acc.my, acc.ek, acc.et, acc.u2max, acc.bad};
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const C w = __shfl_down_sync(0xffffffffu, v[q], o);
+            v[q] = (q == 5) ? (w > v[q] ? w : v[q]) : v[q] + w;
+        }
+    }
+    const int warp = tid / 32, lane = tid % 32;
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) red[warp][q] = v[q];
+    }
+    __syncthreads();
+    const unsigned nblocks = gridDim.x;
+    if (tid < 7) {
+        const int q = tid;
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t = (q == 5) ? fmax(t, (double)red[w][q]) : t + (double)red[w][q];
+        const double cc = (double)k.c;
+        if (q == 1 || q == 2) t *= cc;
+        if (q == 5) t *= cc * cc;
+        partials[(size_t)blockIdx.x * NQ + q] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == nblocks - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid < 7) {
+        const int q = tid;
+        double t = 0.0;
+        for (unsigned b = 0; b < nblocks; ++b) {
+            const double pv = ((volatile double*)partials)[(size_t)b * NQ + q];
+            t = (q == 5) ? fmax(t, pv) : t + pv;
+        }
+        stats[q] = (q == 5) ? sqrt(t) : t;
+        if (q == 6 && t > 0.0) atomicOr(status, ST_NONFINITE);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        stats[7] = stats[7] + 1.0;  // fused steps executed so far
+        *counter = 0u;
+    }
+}
+
+template <class S, class C>
+cudaError_t launch_t(const Launch& L, const CUtensorMap* tmf, const CUtensorMap* tmg, void* out,
+                     double* partials, double* stats, unsigned* counter, int* status, cudaStream_t s) {
+    using SM = Smem<S, C>;
+    const int ntiles = ((L.geo.nx + SM::BX - 1) / SM::BX) * ((L.geo.ny + SM::BY - 1) / SM::BY);
+    const int grid = ntiles < L.geo.sms ? ntiles : L.geo.sms;
+    k_step<S, C><<<grid, NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats, counter, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void step_tile(int storage, int* bx, int* by, int* hx) {
+    switch (storage) {
+        case S_F64: *bx = Tile<double>::BX; *by = Tile<double>::BY; *hx = Tile<double>::HX; break;
+        case S_F32: *bx = Tile<float>::BX; *by = Tile<float>::BY; *hx = Tile<float>::HX; break;
+        default: *bx = Tile<__half>::BX; *by = Tile<__half>::BY; *hx = Tile<__half>::HX; break;
+    }
+}
+
+int step_blocks(int storage, const Geometry& g) {
+    int bx, by, hx;
+    step_tile(storage, &bx, &by, &hx);
+    const int ntiles = ((g.nx + bx - 1) / bx) * ((g.ny + by - 1) / by);
+    return ntiles < g.sms ? ntiles : g.sms;
+}
+
+size_t step_smem_bytes(int storage) {
+    switch (storage) {
+        case S_F64: return Smem<double, double>::BYTES;
+        case S_F32: return Smem<float, float>::BYTES;
+        case S_F16: return Smem<__half, float>::BYTES;
+        default: return Smem<__nv_bfloat16, float>::BYTES;
+    }
+}
+
+cudaError_t prepare_step(int storage) {
+    const int smem = (int)step_smem_bytes(storage);
+    switch (storage) {
+        case S_F64: return cudaFuncSetAttribute(k_step<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case S_F32: return cudaFuncSetAttribute(k_step<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case S_F16: return cudaFuncSetAttribute(k_step<__half, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case S_BF16:
+            return cudaFuncSetAttribute(k_step<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(int storage, const Launch& L, const CUtensorMap* tmf, const CUtensorMap* tmg, void* out,
+                        double* partials, double* stats, unsigned* counter, int* status, cudaStream_t s) {
+    switch (storage) {
+        case S_F64: return launch_t<double, double>(L, tmf, tmg, out, partials, stats, counter, status, s);
+        case S_F32: return launch_t<float, float>(L, tmf, tmg, out, partials, stats, counter, status, s);
+        case S_F16: return launch_t<__half, float>(L, tmf, tmg, out, partials, stats, counter, status, s);
+        case S_BF16:
+            return launch_t<__nv_bfloat16, float>(L, tmf, tmg, out, partials, stats, counter, status, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

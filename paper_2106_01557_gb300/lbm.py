@@ -1,0 +1,221 @@
+"""Thin ctypes binding of liblbm (include/lbm.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module
+converts numpy arrays and torch tensors to pointers and status codes to
+exceptions. There is no fallback: if the shared library or a CUDA device is
+missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
+ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM", -4: "LBM_ERR_DIVERGED",
+          -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE", -7: "LBM_ERR_IO"}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class LbmConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("walls", ctypes.c_int32),
+        ("a_t", ctypes.c_double), ("b_t", ctypes.c_double), ("R", ctypes.c_double),
+        ("K_EOS", ctypes.c_double), ("K_INT", ctypes.c_double), ("Tr0", ctypes.c_double),
+        ("varpi", ctypes.c_double), ("gamma1", ctypes.c_double), ("gamma2", ctypes.c_double),
+        ("s_p", ctypes.c_double), ("s_eps", ctypes.c_double),
+        ("sig_e", ctypes.c_double), ("sig_eps", ctypes.c_double), ("sig_p", ctypes.c_double),
+        ("tau_j_v", ctypes.c_double), ("tau_j_l", ctypes.c_double),
+        ("c_v", ctypes.c_double), ("C_ref", ctypes.c_double),
+        ("accel_x", ctypes.c_double), ("accel_y", ctypes.c_double),
+        ("Tr_bottom", ctypes.c_double), ("Tr_top", ctypes.c_double), ("Tr_hot", ctypes.c_double),
+        ("hot_x0", ctypes.c_int32), ("hot_len", ctypes.c_int32),
+        ("rho_ref", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class LbmParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "Tc", "pc", "T0", "rho_v", "rho_l", "p_s", "cs", "c", "dt", "G2", "a", "kappa",
+        "cv", "Cref", "beta", "kS", "hS", "bS", "se", "sq")]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+SIGNATURES = {
+    "lbm_last_error": ([], ctypes.c_char_p),
+    "lbm_default_config": ([ctypes.POINTER(LbmConfig), ctypes.c_int32, ctypes.c_int32], None),
+    "lbm_init": ([ctypes.POINTER(LbmConfig), ctypes.POINTER(_H)], ctypes.c_int),
+    "lbm_get_params": ([_H, ctypes.POINTER(LbmParams)], ctypes.c_int),
+    "lbm_set_fields": ([_H, _DP, _DP, _DP, _DP, ctypes.c_int], ctypes.c_int),
+    "lbm_step": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_moments": ([_H, _DP, _DP, _DP, _DP, ctypes.c_int], ctypes.c_int),
+    "lbm_conservation": ([_H, _DP], ctypes.c_int),
+    "lbm_step_stats": ([_H, _DP], ctypes.c_int),
+    "lbm_get_populations": ([_H, _DP, _DP], ctypes.c_int),
+    "lbm_set_populations": ([_H, _DP, _DP], ctypes.c_int),
+    "lbm_save": ([_H, ctypes.c_char_p], ctypes.c_int),
+    "lbm_load": ([_H, ctypes.c_char_p], ctypes.c_int),
+    "lbm_synchronize": ([_H], ctypes.c_int),
+    "lbm_step_count": ([_H], ctypes.c_int64),
+    "lbm_bytes_per_step": ([_H], ctypes.c_double),
+    "lbm_destroy": ([_H], ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbm.so (building it in-tree with nvcc if absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"CUDA library not built: {path}")
+                _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise LbmError(rc, _lib.lbm_last_error().decode())
+
+
+def _host_ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+def _dev_ptr(t):
+    return ctypes.cast(ctypes.c_void_p(t.data_ptr()), _DP)
+
+
+def default_config(nx: int, ny: int, **overrides) -> LbmConfig:
+    lib = load()
+    cfg = LbmConfig()
+    lib.lbm_default_config(ctypes.byref(cfg), int(nx), int(ny))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Lattice:
+    """One case on the GPU. Fields are numpy (host) arrays or CUDA torch
+    tensors of float64, shape (ny, nx); populations (9, ny, nx)."""
+
+    def __init__(self, cfg: LbmConfig):
+        self.lib = load()
+        self.cfg = cfg
+        h = _H()
+        _check(self.lib.lbm_init(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self.nx, self.ny = cfg.nx, cfg.ny
+
+    @classmethod
+    def create(cls, nx, ny, **overrides):
+        return cls(default_config(nx, ny, **overrides))
+
+    def close(self):
+        if self.h:
+            self.lib.lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> dict:
+        p = LbmParams()
+        _check(self.lib.lbm_get_params(self.h, ctypes.byref(p)))
+        return {n: getattr(p, n) for n, _ in LbmParams._fields_}
+
+    def set_fields(self, rho, ux, uy, T):
+        arrs = (rho, ux, uy, T)
+        if hasattr(rho, "data_ptr"):
+            for a in arrs:
+                assert a.is_cuda and a.is_contiguous() and str(a.dtype) == "torch.float64"
+            _check(self.lib.lbm_set_fields(self.h, *(_dev_ptr(a) for a in arrs), 1))
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+            _check(self.lib.lbm_set_fields(self.h, *(_host_ptr(a) for a in arrs), 0))
+
+    def step(self, n: int = 1):
+        _check(self.lib.lbm_step(self.h, int(n)))
+
+    def synchronize(self):
+        _check(self.lib.lbm_synchronize(self.h))
+
+    def moments(self, out=None):
+        """dict rho, ux, uy, T as (ny, nx) float64 host arrays; or, with
+        out = dict of CUDA float64 tensors, filled on the device."""
+        if out is not None:
+            _check(self.lib.lbm_moments(self.h, *(_dev_ptr(out[k]) for k in ("rho", "ux", "uy", "T")), 1))
+            return out
+        res = {k: np.empty((self.ny, self.nx)) for k in ("rho", "ux", "uy", "T")}
+        _check(self.lib.lbm_moments(self.h, *(_host_ptr(res[k]) for k in ("rho", "ux", "uy", "T")), 0))
+        return res
+
+    def conservation(self) -> np.ndarray:
+        out = np.zeros(6)
+        _check(self.lib.lbm_conservation(self.h, _host_ptr(out)))
+        return out
+
+    def step_stats(self) -> np.ndarray:
+        out = np.zeros(8)
+        _check(self.lib.lbm_step_stats(self.h, _host_ptr(out)))
+        return out
+
+    def get_populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((9, self.ny, self.nx))
+        _check(self.lib.lbm_get_populations(self.h, _host_ptr(f), _host_ptr(g)))
+        return f, g
+
+    def set_populations(self, f, g):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        _check(self.lib.lbm_set_populations(self.h, _host_ptr(f), _host_ptr(g)))
+
+    def save(self, path: str):
+        _check(self.lib.lbm_save(self.h, path.encode()))
+
+    def load(self, path: str):
+        _check(self.lib.lbm_load(self.h, path.encode()))
+
+    @property
+    def steps(self) -> int:
+        return int(self.lib.lbm_step_count(self.h))
+
+    def bytes_per_step(self) -> float:
+        return float(self.lib.lbm_bytes_per_step(self.h))

@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/lbm.h declares, and its
+ctypes structures match the header's layout."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(lbm_[A-Za-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_01557_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_library_exports_every_declared_function(lib):
+    l, path = lib
+    names = declared_functions()
+    assert "lbm_init" in names and "lbm_step" in names and "lbm_moments" in names
+    for n in names:
+        assert hasattr(l, n), f"{n} declared in include/ but not exported"
+
+
+def test_binding_covers_header(lib):
+    from paper_2106_01557_gb300 import lbm
+    for n in declared_functions():
+        if n.startswith("lbm_batch") or n.startswith("lbm_surrogate"):
+            continue
+        assert n in lbm.SIGNATURES, n
+
+
+def test_struct_layout_matches_header():
+    # compile a tiny C program against the header and compare offsets
+    from paper_2106_01557_gb300 import lbm
+    src = r'''
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "lbm.h"
+    int main(void) {
+      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(lbm_config), offsetof(lbm_config, Tr_hot),
+             offsetof(lbm_config, rho_ref), offsetof(lbm_config, stream), sizeof(lbm_params),
+             offsetof(lbm_params, sq));
+      return 0;
+    }'''
+    tmp = os.path.join(ROOT, "paper_2106_01557_gb300", "_build")
+    os.makedirs(tmp, exist_ok=True)
+    c = os.path.join(tmp, "layout.c")
+    exe = os.path.join(tmp, "layout")
+    open(c, "w").write(src)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    C, P = lbm.LbmConfig, lbm.LbmParams
+    assert got == [ctypes.sizeof(C), C.Tr_hot.offset, C.rho_ref.offset, C.stream.offset,
+                   ctypes.sizeof(P), P.sq.offset]
+
+
+def test_default_config_and_argument_errors_without_gpu(lib):
+    from paper_2106_01557_gb300 import lbm
+    cfg = lbm.default_config(64, 32)
+    assert cfg.K_EOS == pytest.approx(0.479820) and cfg.K_INT == pytest.approx(2.294922)
+    assert cfg.varpi == pytest.approx(1 / 6) and cfg.gamma1 == -2 and cfg.gamma2 == 2
+    l = lbm.load()
+    bad = lbm.default_config(4, 32)
+    h = ctypes.c_void_p()
+    assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
+    assert b"nx" in l.lbm_last_error()
+    bad = lbm.default_config(64, 32, s_p=2.5)
+    assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad = lbm.default_config(64, 32, Tr0=1.2)
+    assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1

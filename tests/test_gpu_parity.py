@@ -1,0 +1,152 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs. Tolerances: FP64 storage 1e-12 and FP32 storage 1e-5,
+both as max |gpu - oracle| / max |oracle| per distribution function or
+field; velocity errors are measured against the lattice speed c."""
+import numpy as np
+import pytest
+
+from gpu_common import gpu_case, oracle_case, rel_err, slab_fields
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def _pair(nx, ny, prec, seed=0, **kw):
+    o = oracle_case(nx, ny, **kw)
+    fields = slab_fields(o, seed=seed)
+    o.init_fields(*fields)
+    g = gpu_case(nx, ny, prec, **kw)
+    g.set_fields(*fields)
+    return o, g
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_derived_parameters_match_oracle(gpu_lib, prec):
+    o = oracle_case(64, 64)
+    g = gpu_case(64, 64, prec)
+    p = g.params()
+    for k in ("Tc", "pc", "T0", "rho_v", "rho_l", "cs", "c", "dt", "G2", "a", "kappa", "Cref", "beta",
+              "kS", "hS", "bS", "se", "sq"):
+        assert p[k] == pytest.approx(getattr(o.p, k), rel=1e-13), k
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_init_populations_match_oracle(gpu_lib, prec):
+    o, g = _pair(100, 37, prec)
+    f, gg = g.get_populations()
+    tol = 1e-14 if prec == "f64" else 1e-7
+    assert rel_err(f, o.f) < tol
+    assert rel_err(gg, o.g) < tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("nsteps", [1, 10, 100])
+def test_periodic_steps_match_oracle(gpu_lib, prec, nsteps):
+    # 100 x 37: two tiles across (ragged tail), three tile rows (ragged)
+    o, g = _pair(100, 37, prec, seed=3)
+    o.step(nsteps)
+    g.step(nsteps)
+    f, gg = g.get_populations()
+    assert rel_err(f, o.f) < TOL[prec]
+    assert rel_err(gg, o.g) < TOL[prec]
+    m = g.moments()
+    mo = o.moments()
+    assert rel_err(m["rho"], mo["rho"]) < TOL[prec]
+    assert rel_err(m["T"], mo["T"]) < TOL[prec]
+    assert np.abs(m["ux"] - mo["ux"]).max() < TOL[prec] * o.p.c
+    assert np.abs(m["uy"] - mo["uy"]).max() < TOL[prec] * o.p.c
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_walls_body_force_hot_spot_match_oracle(gpu_lib, prec):
+    kw = dict(walls=1, accel_y=-1e-4, Tr_bottom=0.8, Tr_hot=0.95, hot_x0=90, hot_len=20, Tr_top=0.0)
+    o, g = _pair(100, 40, prec, seed=5, **kw)
+    o.step(25)
+    g.step(25)
+    f, gg = g.get_populations()
+    assert rel_err(f, o.f) < TOL[prec]
+    assert rel_err(gg, o.g) < TOL[prec]
+
+
+def test_rest_state_stays_at_rest(gpu_lib):
+    g = gpu_case(64, 64, "f64")
+    p = g.params()
+    n = (64, 64)
+    g.set_fields(np.full(n, p["rho_l"]), np.zeros(n), np.zeros(n), np.full(n, p["T0"]))
+    f0, g0 = g.get_populations()
+    g.step(40)
+    f1, g1 = g.get_populations()
+    assert rel_err(f1, f0) < 1e-14 and rel_err(g1, g0) < 1e-14
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_conservation_record_matches_oracle(gpu_lib, prec):
+    o, g = _pair(128, 64, prec, seed=7)
+    o.step(5)
+    g.step(5)
+    co = o.conservation()
+    cg = g.conservation()
+    tol = TOL[prec]
+    assert cg[0] == pytest.approx(co[0], rel=tol)
+    scale = co[0] * o.p.c
+    assert abs(cg[1] - co[1]) < tol * scale and abs(cg[2] - co[2]) < tol * scale
+    assert cg[3] == pytest.approx(co[3], rel=tol)
+    assert cg[4] == pytest.approx(co[4], rel=10 * tol)
+    assert cg[5] == pytest.approx(co[5], rel=1e-3)
+
+
+def test_fused_step_reduction_equals_state_record(gpu_lib):
+    # the in-kernel reduction of step n is the record of the state entering it
+    o, g = _pair(128, 64, "f64", seed=8)
+    g.step(3)
+    before = g.conservation()
+    g.step(1)
+    s = g.step_stats()
+    assert s[0] == pytest.approx(before[0], rel=1e-13)
+    assert s[3] == pytest.approx(before[3], rel=1e-13)
+    assert s[4] == pytest.approx(before[4], rel=1e-12)
+    assert s[6] == 0 and s[7] == 4
+
+
+def test_exact_conservation_on_gpu(gpu_lib):
+    o, g = _pair(128, 64, "f64", seed=9)
+    c0 = g.conservation()
+    g.step(200)
+    c1 = g.conservation()
+    assert c1[0] == pytest.approx(c0[0], rel=1e-13)
+    assert abs(c1[1] - c0[1]) < 1e-13 * c0[0] * o.p.c
+
+
+def test_checkpoint_resume_is_bitwise(gpu_lib, tmp_path):
+    for prec in ("f64", "f32", "f16s"):
+        o = oracle_case(72, 40)
+        fields = slab_fields(o, seed=11)
+        a = gpu_case(72, 40, prec)
+        a.set_fields(*fields)
+        a.step(7)
+        path = str(tmp_path / f"ck_{prec}.bin")
+        a.save(path)
+        a.step(13)
+        fa, ga = a.get_populations()
+        b = gpu_case(72, 40, prec)
+        b.load(path)
+        assert b.steps == 7
+        b.step(13)
+        fb, gb = b.get_populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_divergence_is_reported(gpu_lib):
+    from paper_2106_01557_gb300 import lbm
+    o = oracle_case(64, 64)
+    fields = slab_fields(o, seed=12)
+    g = gpu_case(64, 64, "f32")
+    g.set_fields(*fields)
+    f, gg = g.get_populations()
+    f[:, 10, 10] = -1.0  # negative density at one node: a host-made fault
+    g.set_populations(f, gg)
+    g.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        g.synchronize()
+    assert e.value.code == -4
