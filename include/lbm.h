@@ -179,6 +179,38 @@ double lbm_bytes_per_step(const lbm_handle* h);
 
 int lbm_destroy(lbm_handle* h);
 
+/* Largest lattice (nx * ny) lbm_conservation_noalloc accepts. */
+#define LBM_NOALLOC_MAX_NODES (1 << 20)
+
+/* The conservation record of lbm_conservation, for populations that live in
+ * caller-owned device memory, computed without allocating any memory and
+ * without a handle. It is for callers that cannot call cudaMalloc -- for
+ * example code running while another framework owns the device memory
+ * pool, or code on a path where an allocation is not allowed -- since
+ * lbm_init allocates. The paper has no counterpart: this is an interface
+ * of this library only.
+ *   cfg    case description as for lbm_init (nx, ny, walls, EOS and model
+ *          parameters, body force); its stream, device and precision
+ *          fields are ignored. nx * ny above LBM_NOALLOC_MAX_NODES returns
+ *          LBM_ERR_ARG with a message naming the limit.
+ *   f, g   device arrays [9][ny][nx] of double: post-streaming populations
+ *          (the layout of lbm_get_populations), read only.
+ *   out    device array of at least 7 doubles, written asynchronously:
+ *          out[0..5] as lbm_conservation, out[6] the number of nodes with a
+ *          non-finite or non-positive density.
+ *   stream cudaStream_t to run on (NULL: the legacy default stream); the
+ *          work runs on the calling thread's current device.
+ * Scratch: a fixed device array inside the library (about 8.3 MiB on every
+ * GPU that loads it, held until the process exits) replaces allocations.
+ * The first call on each device looks up that array's device address, so
+ * make it before any stream capture. All calls share the array and it keeps
+ * the previous call's contents (the completion counter is cleared at the
+ * start of each call): calls that can overlap on the GPU -- on different
+ * streams, or from several threads -- race on it and must be serialised by
+ * the caller. */
+int lbm_conservation_noalloc(const lbm_config* cfg, const double* f, const double* g,
+                             double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

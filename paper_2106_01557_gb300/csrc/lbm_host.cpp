@@ -656,4 +656,22 @@ int lbm_destroy(lbm_handle* h) {
     return LBM_OK;
 }
 
+int lbm_conservation_noalloc(const lbm_config* cfg, const double* f, const double* g, double* out,
+                             void* stream) {
+    if (!cfg || !f || !g || !out) return fail(LBM_ERR_ARG, "null argument");
+    const long long n = (long long)cfg->nx * (long long)cfg->ny;
+    if (n > noalloc_max_nodes())
+        return fail(LBM_ERR_ARG, "lattice of " + std::to_string(n) +
+                                     " nodes exceeds LBM_NOALLOC_MAX_NODES = " +
+                                     std::to_string(noalloc_max_nodes()) + " of the no-allocation scratch");
+    lbm_params prm;
+    Launch L;
+    std::memset(&L, 0, sizeof L);
+    int rc = derive(*cfg, prm, L);
+    if (rc) return rc;
+    cudaError_t e = launch_record_noalloc(L, f, g, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "conservation record without allocation");
+    return LBM_OK;
+}
+
 }  // extern "C"

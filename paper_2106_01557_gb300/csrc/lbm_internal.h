@@ -71,4 +71,10 @@ cudaError_t launch_moments(int storage, const Launch& L, const void* buf, double
                            double* stats, unsigned* counter, cudaStream_t s);
 int moments_blocks(const Geometry& g);
 
+// Conservation record of caller-owned [9][ny][nx] FP64 populations with all
+// scratch in a fixed device array (lbm_noalloc.cu); allocates nothing.
+long long noalloc_max_nodes();
+cudaError_t launch_record_noalloc(const Launch& L, const double* f, const double* g, double* out,
+                                  cudaStream_t s);
+
 }  // namespace lbm

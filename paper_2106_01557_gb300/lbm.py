@@ -77,6 +77,8 @@ SIGNATURES = {
     "lbm_step_count": ([_H], ctypes.c_int64),
     "lbm_bytes_per_step": ([_H], ctypes.c_double),
     "lbm_destroy": ([_H], ctypes.c_int),
+    "lbm_conservation_noalloc": ([ctypes.POINTER(LbmConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p], ctypes.c_int),
 }
 
 
@@ -126,6 +128,22 @@ def default_config(nx: int, ny: int, **overrides) -> LbmConfig:
             v = PRECISIONS[v]
         setattr(cfg, k, v)
     return cfg
+
+
+NOALLOC_MAX_NODES = 1 << 20
+
+
+def conservation_noalloc(cfg: LbmConfig, f, g, out, stream=None):
+    """lbm_conservation_noalloc: f, g CUDA float64 tensors (9, ny, nx), out a
+    CUDA float64 tensor of >= 7 entries; asynchronous on `stream` (a
+    torch.cuda.Stream or None for the legacy default stream). Allocates
+    nothing, for callers that cannot allocate device memory."""
+    lib = load()
+    for t in (f, g, out):
+        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"
+    s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(lib.lbm_conservation_noalloc(ctypes.byref(cfg), ctypes.c_void_p(f.data_ptr()),
+                                        ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(out.data_ptr()), s))
 
 
 class Lattice:
