@@ -34,6 +34,11 @@ struct Store<__nv_bfloat16, float> {
     static __device__ __forceinline__ __nv_bfloat16 st(float v, float rest) { return __float2bfloat16_rn(v - rest); }
 };
 
+// Reciprocal: IEEE in FP64; in FP32 the hardware approximation (relative
+// error ~1e-7, far below the FP32 path's 1e-5 parity bound).
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+
 template <class C>
 __device__ __forceinline__ const KC<C>& kc(const Launch& L);
 template <>
@@ -101,7 +106,7 @@ __device__ __forceinline__ void node_macro(const KC<C>& k, const C f[9], const C
     s.gx = third * (rn[1] - rn[3]) + twelfth * ((rn[5] - rn[7]) + (rn[8] - rn[6]));
     s.gy = third * (rn[2] - rn[4]) + twelfth * ((rn[5] - rn[7]) + (rn[6] - rn[8]));
     s.rho = rho;
-    s.inv_rho = C(1) / rho;
+    s.inv_rho = recip(rho);
     s.Fhx = k.G2c * rho * s.gx + rho * k.axc;
     s.Fhy = k.G2c * rho * s.gy + rho * k.ayc;
     const C jx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
@@ -122,7 +127,7 @@ template <class C>
 __device__ __forceinline__ C p_BE(const KC<C>& k, C rho, C T) {
     const C th = k.b4 * rho;
     const C om = C(1) - th;
-    const C z = (C(1) + th * (C(1) + th * (C(1) - th))) / (om * om * om);
+    const C z = (C(1) + th * (C(1) + th * (C(1) - th))) * recip(om * om * om);
     return k.RK * rho * T * z + k.aK_eff * rho * rho;
 }
 
@@ -246,7 +251,7 @@ __device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const No
     // sigma_j(rho): tau_j linear in rho between rho_v and rho_l; sigma_q = sigma_j
     C wl = (rho - k.rho_v) * k.inv_drho;
     wl = wl < C(0) ? C(0) : (wl > C(1) ? C(1) : wl);
-    const C sj = C(1) / (k.tauj_v + k.dtauj * wl + C(0.5));
+    const C sj = recip(k.tauj_v + k.dtauj * wl + C(0.5));
     const C sq = sj;
     const C wj = C(0.5) * sj - C(1);
     // c^2 Y d of SM Eq. S6b

@@ -27,7 +27,7 @@ namespace lbm {
 
 namespace {
 
-constexpr int NT = 512;  // threads per CTA (one persistent CTA per SM)
+// one persistent CTA per SM; its thread count is a per-precision trait (Tile::NT)
 
 // D2Q9 directions (SM Eq. S1), e_i / c
 __host__ __device__ constexpr int EXf(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
@@ -86,13 +86,13 @@ constexpr uint64_t WAIT_NS = 2000000000ull;
 template <class S>
 struct Tile;
 template <>
-struct Tile<double> { static constexpr int BX = 32, BY = 16, HX = 2; };
+struct Tile<double> { static constexpr int BX = 32, BY = 16, HX = 2, NT = 512; };
 template <>
-struct Tile<float> { static constexpr int BX = 64, BY = 16, HX = 4; };
+struct Tile<float> { static constexpr int BX = 64, BY = 16, HX = 4, NT = 512; };
 template <>
-struct Tile<__half> { static constexpr int BX = 64, BY = 32, HX = 8; };
+struct Tile<__half> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512; };
 template <>
-struct Tile<__nv_bfloat16> { static constexpr int BX = 64, BY = 32, HX = 8; };
+struct Tile<__nv_bfloat16> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512; };
 
 template <class S, class C>
 struct Smem {
@@ -112,17 +112,21 @@ struct Smem {
 // Wall ghost-row stores of a node next to a wall: the populations leaving
 // through the wall come back reversed at the next pull (half-way bounce-back
 // of f; of g adiabatic, or anti-bounce-back on a fixed-temperature segment).
+// fo[j], go[j] are the post-collision populations of the three directions
+// that leave through the wall: (4, 7, 8) at the bottom, (2, 5, 6) at the top.
 template <class S, class C>
 __device__ __noinline__ void wall_store(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
-                                        const C* f, const C* g, C rho, const C* rest) {
+                                        C fo0, C fo1, C fo2, C go0, C go1, C go2, C rho) {
     const bool bottom = (y == 0);
     const int yg = bottom ? -1 : G.ny;
     const C Tw = bottom ? k.T_bottom : k.T_top;
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
-        // leaving directions (4, 7, 8) at the bottom, (2, 5, 6) at the top
-        const int i = bottom ? (j == 0 ? 4 : (j == 1 ? 7 : 8)) : (j == 0 ? 2 : (j == 1 ? 5 : 6));
-        const int opp = (i == 2) ? 4 : (i == 4) ? 2 : (i == 5) ? 7 : (i == 6) ? 8 : (i == 7) ? 5 : 6;
-        const int ex = (i == 5 || i == 8) ? 1 : ((i == 6 || i == 7) ? -1 : 0);
+        const int opp = bottom ? (j == 0 ? 2 : (j == 1 ? 5 : 6)) : (j == 0 ? 4 : (j == 1 ? 7 : 8));
+        // x step of the leaving direction: 0 for 4/2; 7 and 6 go left, 8 and 5 right
+        const int ex = j == 0 ? 0 : (bottom ? (j == 1 ? -1 : 1) : (j == 1 ? 1 : -1));
+        const C fv = j == 0 ? fo0 : (j == 1 ? fo1 : fo2);
+        C gv = j == 0 ? go0 : (j == 1 ? go1 : go2);
         int xg = x + ex;
         xg = xg < 0 ? xg + G.nx : (xg >= G.nx ? xg - G.nx : xg);
         C T_link = Tw;
@@ -131,21 +135,15 @@ __device__ __noinline__ void wall_store(S* __restrict__ out, const Geometry& G, 
             if (dxh < 0) dxh += G.nx;
             if (dxh < G.hot_len) T_link = k.T_hot;
         }
-        C gv = g[i];
         if (T_link > C(0)) {
             C ga, gd;
             g_rest_wall(k, rho, T_link, ga, gd);
-            gv = C(2) * (j == 0 ? ga : gd) - g[i];
+            gv = C(2) * (j == 0 ? ga : gd) - gv;
         }
-        put<S>(out, G, opp, xg, yg, Store<S, C>::st(f[i], rest[opp]));
-        put<S>(out, G, 9 + opp, xg, yg, Store<S, C>::st(gv, rest[9 + opp]));
+        put<S>(out, G, opp, xg, yg, Store<S, C>::st(fv, k.rest[opp]));
+        put<S>(out, G, 9 + opp, xg, yg, Store<S, C>::st(gv, k.rest[9 + opp]));
     }
 }
-
-template <class C>
-__device__ __forceinline__ C fast_div(C a, C b) { return a / b; }
-template <>
-__device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
 
 // Per-thread partial sums stay in the compute type (FP64 is a narrow pipe on
 // this GPU); they are widened to FP64 once per CTA.
@@ -155,13 +153,15 @@ struct Acc {
 };
 
 template <class S, class C>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(Tile<S>::NT, 1)
     k_step(const __grid_constant__ CUtensorMap tmf, const __grid_constant__ CUtensorMap tmg,
            S* __restrict__ out, const __grid_constant__ Launch L, double* __restrict__ partials,
            double* __restrict__ stats, unsigned* __restrict__ counter, int* __restrict__ status) {
     using SM = Smem<S, C>;
     constexpr int BX = SM::BX, BY = SM::BY, HX = SM::HX, WX = SM::WX;
     constexpr int FR = SM::FR, GR = SM::GR, RX = SM::RX, RY = SM::RY;
+    constexpr int NT = Tile<S>::NT;
+    static_assert(NT % BX == 0, "whole tile rows per thread sweep");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ C red[NT / 32][7];
@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(NT, 1)
         const int tx0 = (tile % ntx) * BX, ty0 = (tile / ntx) * BY;
 
         // ---- density on tile + ring (pull sums from staged f) --------------
+#pragma unroll 1
         for (int idx = tid; idx < RX * RY; idx += NT) {
             const int rx = idx % RX, ry = idx / RX;
             const int gy = ty0 + ry - 1;
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(NT, 1)
 
         const int lx = tid % BX;
         const int x = tx0 + lx;
+#pragma unroll 1
         for (int ly = tid / BX; ly < BY; ly += NT / BX) {
             const int y = ty0 + ly;
             if (x >= G.nx || y >= G.ny) continue;
@@ -283,7 +285,10 @@ __global__ void __launch_bounds__(NT, 1)
                 }
             }
             // ---- walls: a population leaving through a wall returns reversed
-            if (G.walls && (y == 0 || y == G.ny - 1)) wall_store<S, C>(out, G, k, x, y, f, g, s.rho, rest);
+            if (G.walls && (y == 0 || y == G.ny - 1)) {
+                if (y == 0) wall_store<S, C>(out, G, k, x, y, f[4], f[7], f[8], g[4], g[7], g[8], s.rho);
+                else wall_store<S, C>(out, G, k, x, y, f[2], f[5], f[6], g[2], g[5], g[6], s.rho);
+            }
         }
         __syncthreads();  // stage and density tile free for reuse
     }
@@ -354,7 +359,7 @@ cudaError_t launch_t(const Launch& L, const CUtensorMap* tmf, const CUtensorMap*
     using SM = Smem<S, C>;
     const int ntiles = ((L.geo.nx + SM::BX - 1) / SM::BX) * ((L.geo.ny + SM::BY - 1) / SM::BY);
     const int grid = ntiles < L.geo.sms ? ntiles : L.geo.sms;
-    k_step<S, C><<<grid, NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats, counter, status);
+    k_step<S, C><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats, counter, status);
     return cudaGetLastError();
 }
 
