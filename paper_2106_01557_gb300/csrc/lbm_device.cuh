@@ -87,7 +87,8 @@ __device__ __forceinline__ void populations9(const C m[9], C l[9]) {
 }
 
 // Per-node macroscopic state (Eq. 13, 14) from the pulled populations and
-// the densities of the eight neighbours rn[1..8] (rn[i] = rho(x + e_i)).
+// the density field around the node: rn[i] = rho(x + e_i), rn[0] = rho(x),
+// which every caller has already formed as sum_i f_i (Eq. 14).
 template <class C>
 struct NodeMacro {
     C rho, inv_rho;
@@ -100,7 +101,7 @@ struct NodeMacro {
 template <class C>
 __device__ __forceinline__ void node_macro(const KC<C>& k, const C f[9], const C g[9], const C rn[9],
                                            NodeMacro<C>& s) {
-    C rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const C rho = rn[0];
     // Eq. 13 weights: 1/3 on the axes, 1/12 on the diagonals
     const C third = C(1.0 / 3.0), twelfth = C(1.0 / 12.0);
     s.gx = third * (rn[1] - rn[3]) + twelfth * ((rn[5] - rn[7]) + (rn[8] - rn[6]));

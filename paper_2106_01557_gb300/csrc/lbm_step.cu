@@ -105,8 +105,9 @@ struct Smem {
     static constexpr int STAGE = ((F_BYTES + 127) / 128) * 128 + ((G_BYTES + 127) / 128) * 128;
     static constexpr int G_OFF = ((F_BYTES + 127) / 128) * 128;  // within a stage
     static constexpr int RX = BX + 2, RY = BY + 2;               // density tile with ring
-    static constexpr int R_OFF = 2 * STAGE;
-    static constexpr int BYTES = R_OFF + (int)sizeof(C) * RX * RY + 128;  // + alignment slack
+    static constexpr int R_OFF = 2 * STAGE;                      // two density tiles
+    static constexpr int R_BYTES = (((int)sizeof(C) * RX * RY + 127) / 128) * 128;
+    static constexpr int BYTES = R_OFF + 2 * R_BYTES + 128;      // + alignment slack
 };
 
 // Wall ghost-row stores of a node next to a wall: the populations leaving
@@ -171,7 +172,6 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
 
     const Geometry& G = L.geo;
     const KC<C>& k = kc<C>(L);
-    C* srho = reinterpret_cast<C*>(smem + SM::R_OFF);
     const int tid = threadIdx.x;
     const int ntx = (G.nx + BX - 1) / BX, nty = (G.ny + BY - 1) / BY;
     const int ntiles = ntx * nty;
@@ -192,16 +192,20 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    if (tid == 0) {
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if ((int)blockIdx.x + (int)gridDim.x < ntiles) issue(blockIdx.x + gridDim.x, 1);
+    }
 
     const C* rest = k.rest;
     Acc<C> acc = {0, 0, 0, 0, 0, 0, 0};
     bool ok = true;
     int it = 0;
+    // One block barrier per tile. At the barrier after the density pass of
+    // tile `it`, every thread has finished tile it-1, so its stage is
+    // refilled with tile it+1 and the other density buffer is free.
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int stage = it & 1;
-        const int next = tile + gridDim.x;
-        if (tid == 0 && next < ntiles) issue(next, stage ^ 1);
         bool timed_out = false;
         {
             const uint32_t parity = (it >> 1) & 1;
@@ -210,13 +214,14 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
                 if (globaltimer_ns() - t0 > WAIT_NS) { timed_out = true; break; }
             }
         }
-        if (__syncthreads_or(timed_out)) { ok = false; break; }
-
         const S* sf = reinterpret_cast<const S*>(smem + stage * SM::STAGE);
         const S* sg = reinterpret_cast<const S*>(smem + stage * SM::STAGE + SM::G_OFF);
+        C* srho = reinterpret_cast<C*>(smem + SM::R_OFF + stage * SM::R_BYTES);
         const int tx0 = (tile % ntx) * BX, ty0 = (tile / ntx) * BY;
 
         // ---- density on tile + ring (pull sums from staged f) --------------
+        // (after a timed-out wait these reads see stale data; the pass is
+        // discarded at the barrier below)
 #pragma unroll 1
         for (int idx = tid; idx < RX * RY; idx += NT) {
             const int rx = idx % RX, ry = idx / RX;
@@ -232,7 +237,11 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
             for (int i = 0; i < 9; ++i) r += Store<S, C>::ld(p[i * FR * WX - EYf(i) * WX - EXf(i)], rest[i]);
             srho[idx] = r;
         }
-        __syncthreads();
+        if (__syncthreads_or(timed_out)) { ok = false; break; }
+        if (tid == 0) {
+            const int ahead = tile + gridDim.x;  // tile it+1 goes into the stage tile it-1 used
+            if (it > 0 && ahead < ntiles) issue(ahead, stage ^ 1);
+        }
 
         const int lx = tid % BX;
         const int x = tx0 + lx;
@@ -290,7 +299,6 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
                 else wall_store<S, C>(out, G, k, x, y, f[2], f[5], f[6], g[2], g[5], g[6], s.rho);
             }
         }
-        __syncthreads();  // stage and density tile free for reuse
     }
     if (!ok && tid == 0) {
         atomicOr(status, ST_TIMEOUT);
