@@ -186,28 +186,46 @@ def run_ours(args, rank, world):
 
     variants = {}
     if rank == 0 and not args.no_variants:
-        for vp in ("f64", "f16s", "bf16s"):
-            variants[vp] = variant_rate(lbm, torch, vp, min(args.steps, 50))
+        variants = precision_variants(lbm, torch, args.variant_steps)
     return {"ms_step": ms_step, "mlups": mlups, "bytes_step": bytes_step, "clocks": clk.summary(),
             "e2e": e2e, "stats": stats.tolist(), "variants": variants}
 
 
-def variant_rate(lbm, torch, prec, steps):
-    stream = torch.cuda.Stream()
-    lat, fields = boiling_case(lbm, NX, NY, prec, stream_ptr=stream.cuda_stream)
-    lat.set_fields(*fields)
-    lat.step(3)
-    lat.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    lat.step(steps)
-    ev1.record(stream)
-    ev1.synchronize()
-    lat.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
-    out = {"mlups": NX * NY / (ms * 1e-3) / 1e6, "ms_per_step": ms,
-           "bytes_per_lu": lat.bytes_per_step() / (NX * NY)}
-    lat.close()
+def precision_variants(lbm, torch, nsteps):
+    """The other storage formats on the same workload: MLUPS over `nsteps`
+    steps, and the per-field error of FP32 / FP16S / BF16S against the FP64
+    run (the FP64 GPU path matches the FP64 oracle to 1e-12): max |x - x64| /
+    max |x64| for rho and T, max |u - u64| / c for velocity."""
+    out, ref = {}, None
+    for prec in ("f64", "f32", "f16s", "bf16s"):
+        stream = torch.cuda.Stream()
+        lat, fields = boiling_case(lbm, NX, NY, prec, stream_ptr=stream.cuda_stream)
+        lat.set_fields(*fields)
+        lat.step(3)
+        lat.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lat.step(nsteps - 3)
+        ev1.record(stream)
+        ev1.synchronize()
+        lat.synchronize()
+        ms = ev0.elapsed_time(ev1) / (nsteps - 3)
+        m = lat.moments()
+        c = lat.params()["c"]
+        rec = {"mlups": NX * NY / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+               "bytes_per_lu": lat.bytes_per_step() / (NX * NY)}
+        if prec == "f64":
+            ref = m
+        else:
+            rec["err_vs_f64_after_steps"] = nsteps
+            rec["err_rho"] = float(np.abs(m["rho"] - ref["rho"]).max() / np.abs(ref["rho"]).max())
+            rec["err_T"] = float(np.abs(m["T"] - ref["T"]).max() / np.abs(ref["T"]).max())
+            rec["err_u_over_c"] = float(max(np.abs(m["ux"] - ref["ux"]).max(), np.abs(m["uy"] - ref["uy"]).max()) / c)
+        out[prec] = rec
+        lat.close()
+    base = out["f32"]["mlups"]
+    for prec in out:
+        out[prec]["speedup_vs_f32"] = out[prec]["mlups"] / base
     return out
 
 
@@ -242,6 +260,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant-steps", type=int, default=1000,
+                    help="steps of each storage format for the error-vs-FP64 comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=NX, help="smaller lattice for profiling captures")
     ap.add_argument("--ny", type=int, default=NY)

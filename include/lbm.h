@@ -91,7 +91,7 @@ typedef struct lbm_config {
     double Tr_bottom, Tr_top;     /* fixed wall reduced temperatures; <= 0: adiabatic */
     double Tr_hot;                /* reduced temperature of a hot segment of the bottom wall */
     int32_t hot_x0, hot_len;      /* hot segment: x in [hot_x0, hot_x0 + hot_len) mod nx */
-    double rho_ref;        /* shifted storage reference density; <= 0: (rho_v + rho_l)/2 */
+    double rho_ref;        /* shifted storage reference density; <= 0: rho_v(Tr0) */
     void* stream;          /* cudaStream_t to issue work on; NULL: own stream */
     int32_t device;        /* CUDA device ordinal */
     int32_t reserved;
@@ -178,6 +178,48 @@ int64_t lbm_step_count(const lbm_handle* h);
 double lbm_bytes_per_step(const lbm_handle* h);
 
 int lbm_destroy(lbm_handle* h);
+
+/* ---- Batched cases -------------------------------------------------------
+ * Many independent cases (each its own lattice size, temperature and
+ * droplet) advanced together: one persistent launch per time step walks a
+ * work list of (case, tile) items, with the cases' tensor maps and constants
+ * in device tables. The rows are the same model as lbm_step; a case in a
+ * batch gives the same populations as that case on its own handle with the
+ * same precision, up to floating-point rounding (the two kernels are
+ * compiled separately). Extension of the paper's method for
+ * parameter sweeps (the paper runs single cases). Requirements: every
+ * cfgs[i] periodic (walls = 0), one precision for all (LBM_F32, LBM_F16S or
+ * LBM_BF16S), the stream and device of cfgs[0] are used. */
+typedef struct lbm_batch lbm_batch;
+
+int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out);
+/* As lbm_set_fields, for case i. */
+int lbm_batch_set_fields(lbm_batch* b, int32_t i, const double* rho, const double* ux,
+                         const double* uy, const double* T, int on_device);
+/* Advance every case n steps (CUDA-graph replay), asynchronously. */
+int lbm_batch_step(lbm_batch* b, int n);
+/* As lbm_moments / lbm_conservation / lbm_get_populations, for case i. */
+int lbm_batch_moments(lbm_batch* b, int32_t i, double* rho, double* ux, double* uy,
+                      double* T, int on_device);
+int lbm_batch_conservation(lbm_batch* b, int32_t i, double out[6]);
+int lbm_batch_get_populations(lbm_batch* b, int32_t i, double* f, double* g);
+/* Case i's conservation record as reduced inside the most recent step
+ * (per-tile FP32 partial sums, summed per case in FP64): layout of
+ * lbm_step_stats out[0..6]. Synchronous. */
+int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[7]);
+/* Autotuner: times every candidate (tile shape x work-list order) for
+ * trial_steps steps on the current state and keeps the fastest; the trial
+ * steps are real steps of every case (the state advances). choice[0] =
+ * tile shape index, choice[1] = order index (0 case-major, 1 largest case
+ * first, 2 round-robin over cases); ms[k] (may be NULL, >= 6 entries) =
+ * the time per step of candidate k = 3 * shape + order. Synchronous. */
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int32_t choice[2], double* ms);
+/* Select a candidate directly (tile shape, order). */
+int lbm_batch_select(lbm_batch* b, int32_t shape, int32_t order);
+int lbm_batch_synchronize(lbm_batch* b);
+int64_t lbm_batch_nodes(const lbm_batch* b);
+double lbm_batch_bytes_per_step(const lbm_batch* b);
+int lbm_batch_destroy(lbm_batch* b);
 
 /* Largest lattice (nx * ny) lbm_conservation_noalloc accepts. */
 #define LBM_NOALLOC_MAX_NODES (1 << 20)

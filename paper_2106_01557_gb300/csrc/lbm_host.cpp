@@ -7,12 +7,14 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "lbm_batch.h"
 #include "lbm_internal.h"
 
 using namespace lbm;
@@ -317,10 +319,13 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     if (c.hot_len > 0 && !(c.Tr_hot > 0)) return fail(LBM_ERR_ARG, "hot segment needs Tr_hot > 0");
 
     // Rest populations of the shifted formats: M^-1 m^eq and M^-1 n^eq at
-    // (rho_ref, T0, u = 0), evaluated in FP64 then rounded to FP32 once.
+    // (rho_ref, T0, u = 0), evaluated in FP64 then rounded to FP32 once. The
+    // default rho_ref = rho_v keeps the stored deviations of vapour nodes
+    // near zero; liquid nodes then carry deviations of their own size, so
+    // both phases keep the format's relative precision.
     for (int i = 0; i < 18; ++i) { L.kf.rest[i] = 0.0f; L.kd.rest[i] = 0.0; }
     if (storage == S_F16 || storage == S_BF16) {
-        const double rho = c.rho_ref > 0 ? c.rho_ref : 0.5 * (p.rho_v + p.rho_l);
+        const double rho = c.rho_ref > 0 ? c.rho_ref : p.rho_v;
         const double T = p.T0;
         const double th = 0.25 * c.b_t * rho, om = 1.0 - th;
         const double pbe = c.R * c.K_EOS * rho * T * (1.0 + th + th * th - th * th * th) / (om * om * om) +
@@ -653,6 +658,406 @@ int lbm_destroy(lbm_handle* h) {
     cudaStreamSynchronize(h->stream);
     release(h);
     delete h;
+    return LBM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched cases
+// ---------------------------------------------------------------------------
+struct lbm_batch {
+    int n = 0;
+    int storage = 0;
+    size_t esize = 0;
+    std::vector<lbm_config> cfg;
+    std::vector<lbm_params> prm;
+    std::vector<Launch> L;
+    std::vector<long long> off;  // element offsets of each case in an arena buffer
+    long long arena_elems = 0;
+    void* arena[2] = {nullptr, nullptr};
+    int cur = 0;
+    BatchCase* d_cases[2] = {nullptr, nullptr};  // per tile shape (ntx differs)
+    KC<float>* d_kcs = nullptr;
+    CUtensorMap* d_maps[2] = {nullptr, nullptr};
+    BatchItem* d_items = nullptr;
+    int max_items = 0;
+    std::vector<BatchItem> items[2][3];  // [shape][order]
+    float* d_partials = nullptr;
+    int* d_status = nullptr;
+    double* d_rec = nullptr;     // 8 (case record) + 8 (conservation)
+    double* scratch = nullptr;   // 18 x largest case
+    double* aux_partials = nullptr;
+    unsigned* aux_counter = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int shape = 0, order = 1;
+    int sms = 0;
+    cudaGraphExec_t graph = nullptr;
+    int64_t steps = 0;
+    static constexpr int GRAPH_STEPS = 20;
+};
+
+static BatchLaunch batch_launch(lbm_batch* b) {
+    BatchLaunch B;
+    B.items = b->d_items;
+    B.nitems = (int)b->items[b->shape][b->order].size();
+    B.cases = b->d_cases[b->shape];
+    B.kcs = b->d_kcs;
+    B.maps = b->d_maps[b->shape];
+    B.partials = b->d_partials;
+    B.status = b->d_status;
+    B.sms = b->sms;
+    return B;
+}
+
+static void batch_release(lbm_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    void* ptrs[] = {b->arena[0], b->arena[1], b->d_cases[0], b->d_cases[1], b->d_kcs, b->d_maps[0], b->d_maps[1],
+                    b->d_items, b->d_partials, b->d_status, b->d_rec, b->scratch, b->aux_partials, b->aux_counter};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+static int batch_upload_items(lbm_batch* b) {
+    const std::vector<BatchItem>& v = b->items[b->shape][b->order];
+    CK(cudaMemcpyAsync(b->d_items, v.data(), v.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out) {
+    if (!cfgs || !out || ncases <= 0) return fail(LBM_ERR_ARG, "null argument or no cases");
+    *out = nullptr;
+    const int prec = cfgs[0].precision;
+    if (prec != LBM_F32 && prec != LBM_F16S && prec != LBM_BF16S)
+        return fail(LBM_ERR_ARG, "batch precision must be LBM_F32, LBM_F16S or LBM_BF16S");
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return fail(LBM_ERR_OOM, "host allocation failed");
+    b->n = ncases;
+    b->storage = storage_of(prec);
+    b->esize = elem_size(b->storage);
+    b->cfg.assign(cfgs, cfgs + ncases);
+    b->prm.resize(ncases);
+    b->L.resize(ncases);
+    b->off.resize(ncases);
+    long long total = 0;
+    size_t max_n = 0;
+    for (int i = 0; i < ncases; ++i) {
+        if (cfgs[i].precision != prec) { delete b; return fail(LBM_ERR_ARG, "all batch cases need one precision"); }
+        if (cfgs[i].walls != 0) { delete b; return fail(LBM_ERR_ARG, "batch cases must be periodic (walls = 0)"); }
+        std::memset(&b->L[i], 0, sizeof(Launch));
+        int rc = derive(cfgs[i], b->prm[i], b->L[i]);
+        if (rc) { delete b; return rc; }
+        b->off[i] = total;
+        total += ((18 * b->L[i].geo.plane + 127) / 128) * 128;  // 256-byte aligned case starts
+        max_n = std::max(max_n, (size_t)cfgs[i].nx * cfgs[i].ny);
+    }
+    b->arena_elems = total;
+    cudaError_t e = cudaSetDevice(cfgs[0].device);
+    if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaSetDevice"); }
+    e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, cfgs[0].device);
+    if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    for (int i = 0; i < ncases; ++i) b->L[i].geo.sms = b->sms;
+    if (cfgs[0].stream) {
+        b->stream = static_cast<cudaStream_t>(cfgs[0].stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }
+        b->own_stream = true;
+    }
+    // work lists for both tile shapes and the three orders
+    std::vector<int> by_size(ncases);
+    for (int i = 0; i < ncases; ++i) by_size[i] = i;
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int a, int c) {
+        return (long long)cfgs[a].nx * cfgs[a].ny > (long long)cfgs[c].nx * cfgs[c].ny;
+    });
+    std::vector<BatchCase> hc[2];
+    for (int v = 0; v < 2; ++v) {
+        int bx, by;
+        batch_tile(b->storage, v, &bx, &by);
+        hc[v].resize(ncases);
+        std::vector<int> nt(ncases);
+        for (int i = 0; i < ncases; ++i) {
+            BatchCase& c = hc[v][i];
+            std::memset(&c, 0, sizeof c);
+            c.geo = b->L[i].geo;
+            c.off = b->off[i];
+            c.ntx = (cfgs[i].nx + bx - 1) / bx;
+            c.ntiles = c.ntx * ((cfgs[i].ny + by - 1) / by);
+            float rs = 0.f;
+            for (int q = 0; q < 9; ++q) rs += b->L[i].kf.rest[q];
+            c.rest_sum = rs;
+            nt[i] = c.ntiles;
+        }
+        for (int i = 0; i < ncases; ++i)
+            for (int t = 0; t < nt[i]; ++t) b->items[v][0].push_back({i, t});
+        for (int i : by_size)
+            for (int t = 0; t < nt[i]; ++t) b->items[v][1].push_back({i, t});
+        int maxt = *std::max_element(nt.begin(), nt.end());
+        for (int t = 0; t < maxt; ++t)
+            for (int i = 0; i < ncases; ++i)
+                if (t < nt[i]) b->items[v][2].push_back({i, t});
+        b->max_items = std::max(b->max_items, (int)b->items[v][0].size());
+    }
+    const size_t abytes = (size_t)total * b->esize;
+    const size_t nb_aux = 4096;
+    bool ok = cudaMalloc(&b->arena[0], abytes) == cudaSuccess && cudaMalloc(&b->arena[1], abytes) == cudaSuccess &&
+              cudaMalloc(&b->d_cases[0], ncases * sizeof(BatchCase)) == cudaSuccess &&
+              cudaMalloc(&b->d_cases[1], ncases * sizeof(BatchCase)) == cudaSuccess &&
+              cudaMalloc(&b->d_kcs, ncases * sizeof(KC<float>)) == cudaSuccess &&
+              cudaMalloc(&b->d_maps[0], (size_t)ncases * 4 * sizeof(CUtensorMap)) == cudaSuccess &&
+              cudaMalloc(&b->d_maps[1], (size_t)ncases * 4 * sizeof(CUtensorMap)) == cudaSuccess &&
+              cudaMalloc(&b->d_items, (size_t)b->max_items * sizeof(BatchItem)) == cudaSuccess &&
+              cudaMalloc(&b->d_partials, (size_t)b->max_items * 8 * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&b->d_status, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_rec, 16 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&b->scratch, 18 * max_n * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&b->aux_partials, nb_aux * NQ * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&b->aux_counter, sizeof(unsigned)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        batch_release(b);
+        delete b;
+        return fail(LBM_ERR_OOM, "device allocation failed");
+    }
+    // tensor maps: [case][buffer][f, g] per tile shape
+    EncodeTiled enc = get_encoder();
+    if (!enc) { batch_release(b); delete b; return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"); }
+    CUtensorMapDataType dt = b->storage == S_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : b->storage == S_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    for (int v = 0; v < 2; ++v) {
+        int bx, by;
+        batch_tile(b->storage, v, &bx, &by);
+        std::vector<CUtensorMap> maps((size_t)ncases * 4);
+        for (int i = 0; i < ncases; ++i) {
+            const Geometry& G = b->L[i].geo;
+            cuuint64_t dims[3] = {(cuuint64_t)G.pitch, (cuuint64_t)G.nyp, 18};
+            cuuint64_t strides[2] = {(cuuint64_t)G.pitch * b->esize, (cuuint64_t)G.plane * b->esize};
+            cuuint32_t estr[3] = {1, 1, 1};
+            cuuint32_t boxf[3] = {(cuuint32_t)(bx + 2 * G.HX), (cuuint32_t)(by + 4), 9};
+            cuuint32_t boxg[3] = {(cuuint32_t)(bx + 2 * G.HX), (cuuint32_t)(by + 2), 9};
+            for (int buf = 0; buf < 2; ++buf) {
+                void* base = static_cast<unsigned char*>(b->arena[buf]) + (size_t)b->off[i] * b->esize;
+                CUresult r1 = enc(&maps[(i * 2 + buf) * 2], dt, 3, base, dims, strides, boxf, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                CUresult r2 = enc(&maps[(i * 2 + buf) * 2 + 1], dt, 3, base, dims, strides, boxg, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+                    batch_release(b);
+                    delete b;
+                    return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed for a batch case");
+                }
+            }
+        }
+        e = cudaMemcpy(b->d_maps[v], maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_cases[v], hc[v].data(), ncases * sizeof(BatchCase), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { batch_release(b); delete b; return cuda_fail(e, "cudaMemcpy"); }
+    }
+    std::vector<KC<float>> kk(ncases);
+    for (int i = 0; i < ncases; ++i) kk[i] = b->L[i].kf;
+    ok = cudaMemcpy(b->d_kcs, kk.data(), ncases * sizeof(KC<float>), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(b->arena[0], 0, abytes) == cudaSuccess && cudaMemset(b->arena[1], 0, abytes) == cudaSuccess &&
+         cudaMemset(b->d_status, 0, sizeof(int)) == cudaSuccess &&
+         cudaMemset(b->d_partials, 0, (size_t)b->max_items * 8 * sizeof(float)) == cudaSuccess &&
+         cudaMemset(b->aux_counter, 0, sizeof(unsigned)) == cudaSuccess;
+    if (!ok) { batch_release(b); delete b; return fail(LBM_ERR_CUDA, "device initialisation failed"); }
+    e = batch_prepare(b->storage);
+    if (e == cudaSuccess) e = prepare_step(b->storage);
+    if (e != cudaSuccess) { batch_release(b); delete b; return cuda_fail(e, "cudaFuncSetAttribute"); }
+    int rc = batch_upload_items(b);
+    if (rc) { batch_release(b); delete b; return rc; }
+    *out = b;
+    return LBM_OK;
+}
+
+static int batch_check(lbm_batch* b) {
+    CK(cudaStreamSynchronize(b->stream));
+    int st = 0;
+    CK(cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(cudaMemset(b->d_status, 0, sizeof(int)));
+        if (st & ST_TIMEOUT) return fail(LBM_ERR_TIMEOUT, "a device-side wait exceeded its bound");
+        if (st & ST_NONFINITE) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density in a batch case");
+    }
+    return LBM_OK;
+}
+
+static void* case_buf(lbm_batch* b, int i, int which) {
+    return static_cast<unsigned char*>(b->arena[which]) + (size_t)b->off[i] * b->esize;
+}
+
+int lbm_batch_set_fields(lbm_batch* b, int32_t i, const double* rho, const double* ux, const double* uy,
+                         const double* T, int on_device) {
+    if (!b || i < 0 || i >= b->n || !rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "bad argument");
+    const size_t n = (size_t)b->cfg[i].nx * b->cfg[i].ny;
+    const double* src[4] = {rho, ux, uy, T};
+    const double* d[4];
+    for (int k = 0; k < 4; ++k) {
+        if (on_device) { d[k] = src[k]; continue; }
+        CK(cudaMemcpyAsync(b->scratch + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+        d[k] = b->scratch + k * n;
+    }
+    CK(cudaMemsetAsync(case_buf(b, i, b->cur), 0, (size_t)18 * b->L[i].geo.plane * b->esize, b->stream));
+    CK(launch_init(b->storage, b->L[i], d[0], d[1], d[2], d[3], case_buf(b, i, b->cur), b->stream));
+    return batch_check(b);
+}
+
+static int batch_build_graph(lbm_batch* b) {
+    cudaGraph_t g;
+    const BatchLaunch B = batch_launch(b);
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < lbm_batch::GRAPH_STEPS && e == cudaSuccess; ++k)
+        e = launch_batch_step(b->storage, b->shape, B, k & 1, b->arena[1 - (k & 1)], b->stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "batch step launch during capture");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int n) {
+    if (!b || n < 0) return fail(LBM_ERR_ARG, "bad argument");
+    const BatchLaunch B = batch_launch(b);
+    while (n > 0) {
+        if (b->cur == 0 && n >= lbm_batch::GRAPH_STEPS) {
+            if (!b->graph) {
+                int rc = batch_build_graph(b);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(b->graph, b->stream));
+            b->steps += lbm_batch::GRAPH_STEPS;
+            n -= lbm_batch::GRAPH_STEPS;
+            continue;
+        }
+        CK(launch_batch_step(b->storage, b->shape, B, b->cur, b->arena[1 - b->cur], b->stream));
+        b->cur = 1 - b->cur;
+        b->steps += 1;
+        n -= 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_moments(lbm_batch* b, int32_t i, double* rho, double* ux, double* uy, double* T, int on_device) {
+    if (!b || i < 0 || i >= b->n) return fail(LBM_ERR_ARG, "bad argument");
+    const size_t n = (size_t)b->cfg[i].nx * b->cfg[i].ny;
+    double* outs[4] = {rho, ux, uy, T};
+    double* d[4];
+    for (int k = 0; k < 4; ++k) d[k] = outs[k] ? (on_device ? outs[k] : b->scratch + (1 + k) * n) : nullptr;
+    CK(launch_moments(b->storage, b->L[i], case_buf(b, i, b->cur), b->scratch, d[0], d[1], d[2], d[3], nullptr,
+                      nullptr, nullptr, b->stream));
+    if (!on_device)
+        for (int k = 0; k < 4; ++k)
+            if (outs[k]) CK(cudaMemcpyAsync(outs[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    return batch_check(b);
+}
+
+int lbm_batch_conservation(lbm_batch* b, int32_t i, double out[6]) {
+    if (!b || i < 0 || i >= b->n || !out) return fail(LBM_ERR_ARG, "bad argument");
+    CK(launch_moments(b->storage, b->L[i], case_buf(b, i, b->cur), b->scratch, nullptr, nullptr, nullptr, nullptr,
+                      b->aux_partials, b->d_rec + 8, b->aux_counter, b->stream));
+    double s[8];
+    CK(cudaMemcpyAsync(s, b->d_rec + 8, 8 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    int rc = batch_check(b);
+    if (rc) return rc;
+    for (int k = 0; k < 6; ++k) out[k] = s[k];
+    return LBM_OK;
+}
+
+int lbm_batch_get_populations(lbm_batch* b, int32_t i, double* f, double* g) {
+    if (!b || i < 0 || i >= b->n || !f || !g) return fail(LBM_ERR_ARG, "bad argument");
+    const size_t n = (size_t)b->cfg[i].nx * b->cfg[i].ny;
+    CK(launch_get_pops(b->storage, b->L[i], case_buf(b, i, b->cur), b->scratch, b->scratch + 9 * n, b->stream));
+    CK(cudaMemcpyAsync(f, b->scratch, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(g, b->scratch + 9 * n, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    return batch_check(b);
+}
+
+int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[7]) {
+    if (!b || i < 0 || i >= b->n || !out) return fail(LBM_ERR_ARG, "bad argument");
+    CK(launch_batch_case_record(batch_launch(b), i, b->d_rec, b->stream));
+    double s[8];
+    CK(cudaMemcpyAsync(s, b->d_rec, 8 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    int rc = batch_check(b);
+    for (int k = 0; k < 7; ++k) out[k] = s[k];
+    return rc;
+}
+
+int lbm_batch_select(lbm_batch* b, int32_t shape, int32_t order) {
+    if (!b || shape < 0 || shape > 1 || order < 0 || order > 2) return fail(LBM_ERR_ARG, "bad candidate");
+    b->shape = shape;
+    b->order = order;
+    return batch_upload_items(b);
+}
+
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int32_t choice[2], double* ms) {
+    if (!b || trial_steps < 2) return fail(LBM_ERR_ARG, "need at least 2 trial steps");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bs = 0, bo = 0;
+    for (int v = 0; v < 2; ++v)
+        for (int o = 0; o < 3; ++o) {
+            int rc = lbm_batch_select(b, v, o);
+            if (rc) return rc;
+            const BatchLaunch B = batch_launch(b);
+            CK(launch_batch_step(b->storage, b->shape, B, b->cur, b->arena[1 - b->cur], b->stream));  // warm-up
+            b->cur = 1 - b->cur;
+            CK(cudaEventRecord(e0, b->stream));
+            for (int k = 0; k < trial_steps; ++k) {
+                CK(launch_batch_step(b->storage, b->shape, B, b->cur, b->arena[1 - b->cur], b->stream));
+                b->cur = 1 - b->cur;
+            }
+            CK(cudaEventRecord(e1, b->stream));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            const double per = t / trial_steps;
+            if (ms) ms[3 * v + o] = per;
+            b->steps += trial_steps + 1;
+            if (per < best) { best = per; bs = v; bo = o; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (choice) { choice[0] = bs; choice[1] = bo; }
+    int rc = lbm_batch_select(b, bs, bo);
+    if (rc) return rc;
+    return batch_check(b);
+}
+
+int lbm_batch_synchronize(lbm_batch* b) {
+    if (!b) return fail(LBM_ERR_ARG, "null batch");
+    return batch_check(b);
+}
+
+int64_t lbm_batch_nodes(const lbm_batch* b) {
+    if (!b) return 0;
+    int64_t s = 0;
+    for (int i = 0; i < b->n; ++i) s += (int64_t)b->cfg[i].nx * b->cfg[i].ny;
+    return s;
+}
+
+double lbm_batch_bytes_per_step(const lbm_batch* b) {
+    return b ? 2.0 * 18.0 * (double)b->esize * (double)lbm_batch_nodes(b) : 0.0;
+}
+
+int lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    delete b;
     return LBM_OK;
 }
 

@@ -77,6 +77,19 @@ SIGNATURES = {
     "lbm_step_count": ([_H], ctypes.c_int64),
     "lbm_bytes_per_step": ([_H], ctypes.c_double),
     "lbm_destroy": ([_H], ctypes.c_int),
+    "lbm_batch_init": ([ctypes.POINTER(LbmConfig), ctypes.c_int32, ctypes.POINTER(_H)], ctypes.c_int),
+    "lbm_batch_set_fields": ([_H, ctypes.c_int32, _DP, _DP, _DP, _DP, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_step": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_moments": ([_H, ctypes.c_int32, _DP, _DP, _DP, _DP, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_conservation": ([_H, ctypes.c_int32, _DP], ctypes.c_int),
+    "lbm_batch_get_populations": ([_H, ctypes.c_int32, _DP, _DP], ctypes.c_int),
+    "lbm_batch_step_stats": ([_H, ctypes.c_int32, _DP], ctypes.c_int),
+    "lbm_batch_autotune": ([_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), _DP], ctypes.c_int),
+    "lbm_batch_select": ([_H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "lbm_batch_synchronize": ([_H], ctypes.c_int),
+    "lbm_batch_nodes": ([_H], ctypes.c_int64),
+    "lbm_batch_bytes_per_step": ([_H], ctypes.c_double),
+    "lbm_batch_destroy": ([_H], ctypes.c_int),
     "lbm_conservation_noalloc": ([ctypes.POINTER(LbmConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p], ctypes.c_int),
 }
@@ -237,3 +250,81 @@ class Lattice:
 
     def bytes_per_step(self) -> float:
         return float(self.lib.lbm_bytes_per_step(self.h))
+
+
+class Batch:
+    """Many independent periodic cases advanced together (lbm_batch_*).
+    cfgs: list of LbmConfig, one precision for all (f32, f16s or bf16s)."""
+
+    ORDERS = ("case-major", "largest-first", "round-robin")
+
+    def __init__(self, cfgs):
+        self.lib = load()
+        self.cfgs = list(cfgs)
+        arr = (LbmConfig * len(self.cfgs))(*self.cfgs)
+        h = _H()
+        _check(self.lib.lbm_batch_init(arr, len(self.cfgs), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.cfgs)
+
+    def set_fields(self, i, rho, ux, uy, T):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy, T)]
+        _check(self.lib.lbm_batch_set_fields(self.h, int(i), *(_host_ptr(a) for a in arrs), 0))
+
+    def step(self, n=1):
+        _check(self.lib.lbm_batch_step(self.h, int(n)))
+
+    def synchronize(self):
+        _check(self.lib.lbm_batch_synchronize(self.h))
+
+    def moments(self, i):
+        c = self.cfgs[i]
+        res = {k: np.empty((c.ny, c.nx)) for k in ("rho", "ux", "uy", "T")}
+        _check(self.lib.lbm_batch_moments(self.h, int(i), *(_host_ptr(res[k]) for k in ("rho", "ux", "uy", "T")), 0))
+        return res
+
+    def conservation(self, i):
+        out = np.zeros(6)
+        _check(self.lib.lbm_batch_conservation(self.h, int(i), _host_ptr(out)))
+        return out
+
+    def get_populations(self, i):
+        c = self.cfgs[i]
+        f = np.empty((9, c.ny, c.nx))
+        g = np.empty((9, c.ny, c.nx))
+        _check(self.lib.lbm_batch_get_populations(self.h, int(i), _host_ptr(f), _host_ptr(g)))
+        return f, g
+
+    def step_stats(self, i):
+        out = np.zeros(7)
+        _check(self.lib.lbm_batch_step_stats(self.h, int(i), _host_ptr(out)))
+        return out
+
+    def autotune(self, trial_steps=10):
+        choice = (ctypes.c_int32 * 2)()
+        ms = np.zeros(6)
+        _check(self.lib.lbm_batch_autotune(self.h, int(trial_steps), choice, _host_ptr(ms)))
+        return (int(choice[0]), int(choice[1])), ms
+
+    def select(self, shape, order):
+        _check(self.lib.lbm_batch_select(self.h, int(shape), int(order)))
+
+    @property
+    def nodes(self):
+        return int(self.lib.lbm_batch_nodes(self.h))
+
+    def bytes_per_step(self):
+        return float(self.lib.lbm_batch_bytes_per_step(self.h))

@@ -1,0 +1,79 @@
+"""Reduced-precision storage (FP16 / BF16 shifted populations, FP32 collision)
+against the FP64 oracle, and the GPU path's physics on the flat-interface
+check. The shifted formats store l_i - l_i^rest; their error bounds per field
+are stated here and in the design notes (max |gpu - oracle| / max |oracle|,
+velocity against the lattice speed c)."""
+import numpy as np
+import pytest
+
+from gpu_common import gpu_case, oracle_case, rel_err, slab_fields
+
+pytestmark = pytest.mark.gpu
+
+# stated per-field bounds after 100 steps of the perturbed slab
+# (measured: FP16 rho 1.9e-3, T 3.6e-3, u/c 1.8e-4; BF16 rho 2.0e-2,
+# T 4.8e-2, u/c 2.0e-3)
+BOUNDS = {"f16s": {"rho": 5e-3, "T": 8e-3, "u": 5e-4},
+          "bf16s": {"rho": 4e-2, "T": 8e-2, "u": 4e-3}}
+
+
+@pytest.mark.parametrize("prec", ["f16s", "bf16s"])
+def test_shifted_storage_error_bounds(gpu_lib, prec):
+    o = oracle_case(100, 37)
+    fields = slab_fields(o, seed=21)
+    o.init_fields(*fields)
+    g = gpu_case(100, 37, prec)
+    g.set_fields(*fields)
+    o.step(100)
+    g.step(100)
+    m, mo = g.moments(), o.moments()
+    b = BOUNDS[prec]
+    e_rho = rel_err(m["rho"], mo["rho"])
+    e_T = rel_err(m["T"], mo["T"])
+    e_u = max(np.abs(m["ux"] - mo["ux"]).max(), np.abs(m["uy"] - mo["uy"]).max()) / o.p.c
+    print(f"{prec}: rho {e_rho:.3e} T {e_T:.3e} u/c {e_u:.3e}")
+    assert e_rho < b["rho"], e_rho
+    assert e_T < b["T"], e_T
+    assert e_u < b["u"], e_u
+    # mass is still conserved to the storage precision of one population
+    c0 = fields[0].sum()
+    assert abs(g.conservation()[0] / c0 - 1) < (1e-3 if prec == "f16s" else 1e-2)
+
+
+def test_shifted_storage_roundtrip_is_bounded(gpu_lib):
+    # set/get populations through the shifted format rounds each value once
+    o = oracle_case(72, 40)
+    o.init_fields(*slab_fields(o, seed=22))
+    for prec, tol in (("f16s", 2 ** -11), ("bf16s", 2 ** -8)):
+        g = gpu_case(72, 40, prec)
+        g.set_populations(o.f, o.g)
+        f, gg = g.get_populations()
+        # error relative to the largest population of each DF
+        assert rel_err(f, o.f) < 2 * tol
+        assert rel_err(gg, o.g) < 2 * tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gpu_flat_interface_coexistence(gpu_lib, prec):
+    # the oracle's thermodynamic-consistency pin, on the GPU path: a slab from
+    # the square-gradient equilibrium profile keeps the Maxwell densities
+    # (within 1%) and W = 10 (within 2%) over 10,000 steps
+    from oracle import thermo
+    N = 128
+    o = oracle_case(N, 8)
+    p = o.p
+    x = np.arange(N, dtype=float)
+    z = np.minimum(x - N / 4, 3 * N / 4 - x)
+    r1 = thermo.planar_profile(p.T0, 1.0, 4.0, 1.0, o.cfg.K_EOS, o.cfg.K_INT, z)
+    rho = np.repeat(r1[None, :], 8, axis=0)
+    g = gpu_case(N, 8, prec)
+    g.set_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+    g.step(10000)
+    m = g.moments()
+    r, T = m["rho"][0], m["T"][0]
+    Mv, _, _ = thermo.maxwell(T[0], 1.0, 4.0, 1.0)
+    _, Ml, _ = thermo.maxwell(T[N // 2], 1.0, 4.0, 1.0)
+    assert abs(r[0] / Mv - 1) < 0.01 and abs(r[N // 2] / Ml - 1) < 0.01
+    xs = np.arange(N // 4 - 20, N // 4 + 20)
+    lvl = lambda fr: np.interp(r[0] + fr * (r[N // 2] - r[0]), r[xs], xs)
+    assert lvl(0.95) - lvl(0.05) == pytest.approx(10.0, rel=0.02)
