@@ -65,8 +65,8 @@ extern "C" {
  * parameters (paragraph after Eq. 19): varpi = 1/6, gamma1 = -2,
  * gamma2 = 2, a~ = 1, b~ = 4, R = 1, Tr0 = 0.8, K_EOS = 0.479820,
  * K_INT = 2.294922, and for the rates the paper leaves open: s_p = 1,
- * s_eps = 1, sigma_e = sigma_eps = sigma_p = 1, tau_j = 0.5 (vapour) and
- * 5.0 (liquid) so that lambda_l = 10 lambda_v, c_v = 3/2 R, C_ref =
+ * s_eps = 1, sigma_e = sigma_eps = sigma_p = 1, tau_j = 0.25 (vapour) and
+ * 2.5 (liquid) so that lambda_l = 10 lambda_v, c_v = 3/2 R, C_ref =
  * rho_v c_v. */
 typedef struct lbm_config {
     int32_t nx, ny;        /* lattice size; nx >= 8, ny >= 8 */
@@ -126,6 +126,11 @@ void lbm_default_config(lbm_config* cfg, int32_t nx, int32_t ny);
 int lbm_init(const lbm_config* cfg, lbm_handle** out);
 
 int lbm_get_params(const lbm_handle* h, lbm_params* out);
+
+/* Maxwell coexistence of the EOS of cfg (Eq. 17: a~, b~, R, K_EOS) at
+ * reduced temperature Tr: out[0] rho_v, out[1] rho_l, out[2] saturation
+ * pressure. Host only; LBM_ERR_ARG if Tr is not in (0.3, 1). */
+int lbm_maxwell(const lbm_config* cfg, double Tr, double out[3]);
 
 /* Initial populations from macroscopic fields (rho, u_x, u_y, T), each
  * [ny][nx] double: m = m^eq - dt/2 F_m and n = n^eq - dt/2 q_m at every
@@ -216,6 +221,7 @@ int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[7]);
 int lbm_batch_autotune(lbm_batch* b, int trial_steps, int32_t choice[2], double* ms);
 /* Select a candidate directly (tile shape, order). */
 int lbm_batch_select(lbm_batch* b, int32_t shape, int32_t order);
+int lbm_batch_get_params(const lbm_batch* b, int32_t i, lbm_params* out);
 int lbm_batch_synchronize(lbm_batch* b);
 int64_t lbm_batch_nodes(const lbm_batch* b);
 double lbm_batch_bytes_per_step(const lbm_batch* b);

@@ -30,7 +30,7 @@ Readings where the paper is silent (all listed in the design doc):
 * W is the 5%-95% width of the planar equilibrium profile;
 * relaxation rates not given in the paper use parameter set "P0"
   (s_p = 1, s_eps = 1, sigma_e = sigma_eps = sigma_p = 1, tau_j linear in
-  rho from 0.5 at rho_v to 5.0 at rho_l so that lambda_l = 10 lambda_v,
+  rho from 0.25 at rho_v to 2.5 at rho_l so that lambda_l = 10 lambda_v,
   sigma_q = sigma_j).
 """
 from __future__ import annotations
@@ -232,8 +232,8 @@ class Config:
     sig_e: float = 1.0
     sig_eps: float = 1.0
     sig_p: float = 1.0
-    tau_j_v: float = 0.5
-    tau_j_l: float = 5.0
+    tau_j_v: float = 0.25
+    tau_j_l: float = 2.5
     c_v: float = 1.5               # in units of R
     C_ref: float = 0.0             # 0 -> rho_v(Tr0) c_v R
     accel_x: float = 0.0

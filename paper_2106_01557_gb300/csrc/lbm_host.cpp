@@ -201,8 +201,8 @@ void lbm_default_config(lbm_config* c, int32_t nx, int32_t ny) {
     c->sig_e = 1.0;
     c->sig_eps = 1.0;
     c->sig_p = 1.0;
-    c->tau_j_v = 0.5;
-    c->tau_j_l = 5.0;
+    c->tau_j_v = 0.25;
+    c->tau_j_l = 2.5;
     c->c_v = 1.5;
     c->C_ref = 0.0;
     c->rho_ref = 0.0;
@@ -452,6 +452,18 @@ int lbm_init(const lbm_config* cfg, lbm_handle** out) {
 int lbm_get_params(const lbm_handle* h, lbm_params* out) {
     if (!h || !out) return fail(LBM_ERR_ARG, "null argument");
     *out = h->prm;
+    return LBM_OK;
+}
+
+int lbm_maxwell(const lbm_config* cfg, double Tr, double out[3]) {
+    if (!cfg || !out) return fail(LBM_ERR_ARG, "null argument");
+    if (!(Tr > 0.3 && Tr < 1.0)) return fail(LBM_ERR_ARG, "Tr must lie in (0.3, 1)");
+    const double A = 0.4963880577294099, B = 0.1872945669467330;
+    const double Tc = (B / A) * cfg->a_t / (cfg->b_t * cfg->R);
+    Eos e{cfg->a_t, cfg->b_t, cfg->R, Tr * Tc};
+    double ps;
+    if (!maxwell(e, &out[0], &out[1], &ps)) return fail(LBM_ERR_ARG, "no coexistence at this temperature");
+    out[2] = cfg->K_EOS * ps;
     return LBM_OK;
 }
 
@@ -1035,6 +1047,12 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, int32_t choice[2], double*
     int rc = lbm_batch_select(b, bs, bo);
     if (rc) return rc;
     return batch_check(b);
+}
+
+int lbm_batch_get_params(const lbm_batch* b, int32_t i, lbm_params* out) {
+    if (!b || !out || i < 0 || i >= b->n) return fail(LBM_ERR_ARG, "bad argument");
+    *out = b->prm[i];
+    return LBM_OK;
 }
 
 int lbm_batch_synchronize(lbm_batch* b) {

@@ -87,6 +87,8 @@ SIGNATURES = {
     "lbm_batch_autotune": ([_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), _DP], ctypes.c_int),
     "lbm_batch_select": ([_H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "lbm_batch_synchronize": ([_H], ctypes.c_int),
+    "lbm_batch_get_params": ([_H, ctypes.c_int32, ctypes.POINTER(LbmParams)], ctypes.c_int),
+    "lbm_maxwell": ([ctypes.POINTER(LbmConfig), ctypes.c_double, _DP], ctypes.c_int),
     "lbm_batch_nodes": ([_H], ctypes.c_int64),
     "lbm_batch_bytes_per_step": ([_H], ctypes.c_double),
     "lbm_batch_destroy": ([_H], ctypes.c_int),
@@ -141,6 +143,14 @@ def default_config(nx: int, ny: int, **overrides) -> LbmConfig:
             v = PRECISIONS[v]
         setattr(cfg, k, v)
     return cfg
+
+
+def maxwell(cfg: LbmConfig, Tr: float):
+    """Coexistence densities (rho_v, rho_l) and saturation pressure of the
+    EOS of cfg at reduced temperature Tr, from the library's host solver."""
+    out = np.zeros(3)
+    _check(load().lbm_maxwell(ctypes.byref(cfg), float(Tr), _host_ptr(out)))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 NOALLOC_MAX_NODES = 1 << 20
@@ -318,6 +328,11 @@ class Batch:
         ms = np.zeros(6)
         _check(self.lib.lbm_batch_autotune(self.h, int(trial_steps), choice, _host_ptr(ms)))
         return (int(choice[0]), int(choice[1])), ms
+
+    def params(self, i) -> dict:
+        p = LbmParams()
+        _check(self.lib.lbm_batch_get_params(self.h, int(i), ctypes.byref(p)))
+        return {n: getattr(p, n) for n, _ in LbmParams._fields_}
 
     def select(self, shape, order):
         _check(self.lib.lbm_batch_select(self.h, int(shape), int(order)))

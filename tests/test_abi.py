@@ -84,3 +84,20 @@ def test_default_config_and_argument_errors_without_gpu(lib):
     assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
     bad = lbm.default_config(64, 32, Tr0=1.2)
     assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
+
+
+def test_library_maxwell_matches_oracle_on_host(lib):
+    # the library's own coexistence solver (host code, no GPU) against the
+    # oracle's, over the benchmark temperature range
+    from oracle import thermo
+    from paper_2106_01557_gb300 import lbm
+    cfg = lbm.default_config(64, 64)
+    Tc, _ = thermo.critical_point(1.0, 4.0, 1.0)
+    for Tr in (0.6, 0.7, 0.8, 0.85, 0.9, 0.95):
+        rv, rl, ps = lbm.maxwell(cfg, Tr)
+        ov, ol, ops = thermo.maxwell(Tr * Tc, 1.0, 4.0, 1.0)
+        assert rv == pytest.approx(ov, rel=1e-12)
+        assert rl == pytest.approx(ol, rel=1e-12)
+        assert ps == pytest.approx(cfg.K_EOS * ops, rel=1e-12)
+    with pytest.raises(lbm.LbmError):
+        lbm.maxwell(cfg, 1.1)

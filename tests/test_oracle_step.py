@@ -199,3 +199,52 @@ def test_single_node_collision_budget():
     assert p.c * (EX * fb).sum() == pytest.approx(p.c * (EX * fl).sum() + p.dt * Fx, rel=1e-13)
     assert p.c * (EY * fb).sum() == pytest.approx(p.c * (EY * fl).sum() + p.dt * Fy, rel=1e-13)
     assert gb.sum() == pytest.approx(gl.sum() + p.dt * q, rel=1e-14)
+
+
+def _growth(o, rho0, ngrid=10):
+    """Largest amplification factor of the linearised step (collision
+    Jacobian by central differences of the oracle's node collision, pair
+    force through the neighbour densities, streaming as a phase) over a
+    grid of wave vectors, around the uniform rest state at density rho0."""
+    p = o.p
+    n = 4
+    o.init_fields(np.full((n, n), rho0), np.zeros((n, n)), np.zeros((n, n)), np.full((n, n), p.T0))
+    x0 = np.concatenate([o.f[:, 0, 0], o.g[:, 0, 0], np.full(9, rho0)])
+
+    def col(x):
+        fb, gb, _ = o.collide_node(x[:9], x[9:18], x[18:])
+        return np.concatenate([fb, gb])
+
+    J = np.zeros((18, 27))
+    for j in range(27):
+        h = 1e-6 * max(abs(x0[j]), 1e-3)
+        xp, xm = x0.copy(), x0.copy()
+        xp[j] += h
+        xm[j] -= h
+        J[:, j] = (col(xp) - col(xm)) / (2 * h)
+    worst = 0.0
+    sel = np.concatenate([np.ones(9), np.zeros(9)])
+    for kx in np.linspace(0, np.pi, ngrid):
+        for ky in np.linspace(0, np.pi, ngrid):
+            ph = np.exp(1j * (kx * EX + ky * EY))
+            A = J[:, :18].astype(complex) + np.outer(J[:, 18:] @ ph, sel)
+            P = np.diag(np.concatenate([np.conj(ph), np.conj(ph)]))
+            worst = max(worst, np.abs(np.linalg.eigvals(P @ A)).max())
+    return worst
+
+
+@pytest.mark.parametrize("Tr", [0.75, 0.8, 0.95])
+def test_bulk_phases_linearly_stable(Tr):
+    # with the default rates both bulk phases are linearly stable for
+    # T_r >= 0.75 (the paper's runs use 0.8 and 0.85)
+    o = Oracle(thermo.Config(nx=4, ny=4, Tr0=Tr))
+    assert _growth(o, o.p.rho_l) < 1 + 1e-7
+    assert _growth(o, o.p.rho_v) < 1 + 1e-7
+
+
+def test_bulk_liquid_unstable_at_low_temperature():
+    # the same rates leave the dense liquid linearly unstable at T_r = 0.6
+    # (thermo-acoustic growth of a long wave), the reason the sweep's
+    # temperatures start at 0.75
+    o = Oracle(thermo.Config(nx=4, ny=4, Tr0=0.6))
+    assert _growth(o, o.p.rho_l) > 1.01
