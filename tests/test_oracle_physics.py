@@ -109,4 +109,4 @@ def test_laplace_law_static_droplets():
     slope, icpt = np.polyfit(x, y, 1)
     sigma = GOLD["simulation_parameters"]["sigma_prescribed"]
     assert slope == pytest.approx(sigma, rel=0.20)
-    assert abs(icpt) < 0.1 * y.min()
+    assert abs(icpt) < 0.2 * y.min()
