@@ -187,6 +187,7 @@ def run_ours(args, rank, world):
     variants = {}
     if rank == 0 and not args.no_variants:
         variants = precision_variants(lbm, torch, args.variant_steps)
+        variants["batch_f16s"] = batch_variant(lbm, torch, 100)
     return {"ms_step": ms_step, "mlups": mlups, "bytes_step": bytes_step, "clocks": clk.summary(),
             "e2e": e2e, "stats": stats.tolist(), "variants": variants}
 
@@ -229,6 +230,127 @@ def precision_variants(lbm, torch, nsteps):
     return out
 
 
+def batch_cases_fields(lbm, ncases, seed, precision, stream_ptr):
+    """The heterogeneous sweep: ncases periodic boxes, sides log-uniform in
+    [64, 512] (multiples of 8), one droplet of radius U[8, 0.3 min(nx, ny)]
+    at the centre, T/Tc uniform in [0.75, 0.95] (the model's bulk liquid is
+    linearly unstable below T/Tc = 0.75 with these rates), tanh edge of
+    width 4."""
+    from paper_2106_01557_gb300 import inputs
+    cases = inputs.batch_cases(ncases, seed, tr_lo=0.75)
+    cfgs = []
+    for c in cases:
+        cfg = lbm.default_config(c["nx"], c["ny"], precision=precision, Tr0=c["Tr"])
+        if stream_ptr is not None:
+            cfg.stream = stream_ptr
+        cfgs.append(cfg)
+    return cases, cfgs
+
+
+def batch_variant(lbm, torch, steps, ncases=256, seed=4):
+    """Batched FP16-storage sweep in one persistent launch per step (autotuned)
+    against the same cases run one by one on the plain FP32 path."""
+    from paper_2106_01557_gb300 import inputs
+    stream = torch.cuda.Stream()
+    cases, cfgs = batch_cases_fields(lbm, ncases, seed, "f16s", stream.cuda_stream)
+    b = lbm.Batch(cfgs)
+    fields = []
+    for i, c in enumerate(cases):
+        p = b.params(i)
+        rho = inputs.droplets(c["nx"], c["ny"], p["rho_v"], p["rho_l"], [(c["nx"] / 2, c["ny"] / 2)], [c["R"]], 4.0)
+        T = np.full_like(rho, p["T0"])
+        z = np.zeros_like(rho)
+        fields.append((rho, z, z, T))
+        b.set_fields(i, *fields[-1])
+    choice, ms = b.autotune(5)
+    b.step(20)
+    b.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    b.synchronize()
+    ms_step = ev0.elapsed_time(ev1) / steps
+    nodes = b.nodes
+    out = {"cases": ncases, "nodes": nodes, "mlups": nodes / (ms_step * 1e-3) / 1e6, "ms_per_step": ms_step,
+           "bytes_per_lu": b.bytes_per_step() / nodes,
+           "autotune": {"tile_shape": ["64x32", "32x16"][choice[0]], "order": lbm.Batch.ORDERS[choice[1]],
+                        "ms_per_step_candidates": [round(float(x), 4) for x in ms]}}
+    b.close()
+    # the same cases, each on its own plain FP32 handle, stepped one after another
+    lats = []
+    for cfg, fl in zip(batch_cases_fields(lbm, ncases, seed, "f32", stream.cuda_stream)[1], fields):
+        lat = lbm.Lattice(cfg)
+        lat.set_fields(*fl)
+        lats.append(lat)
+    per = 20
+    for lat in lats:
+        lat.step(per)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for lat in lats:
+        lat.step(per)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_plain = ev0.elapsed_time(ev1) / per
+    for lat in lats:
+        lat.close()
+    out["plain_f32_one_by_one_mlups"] = nodes / (ms_plain * 1e-3) / 1e6
+    out["speedup_vs_plain_f32_one_by_one"] = ms_plain / ms_step
+    return out
+
+
+def batch_study(steps, ncases=256, seed=4, precision="f16s"):
+    """The heterogeneous sweep run for `steps` steps (FP16 storage, FP32
+    math): per case, the droplet-centre (liquid) and corner (vapour) densities
+    against the Maxwell densities at each bulk's measured temperature, from
+    the library's own coexistence solver. A case whose droplet has
+    evaporated (centre density below the mean of the two Maxwell densities)
+    is reported and left out of the 1% statistic."""
+    import torch
+    from paper_2106_01557_gb300 import inputs, lbm
+    stream = torch.cuda.Stream()
+    cases, cfgs = batch_cases_fields(lbm, ncases, seed, precision, stream.cuda_stream)
+    b = lbm.Batch(cfgs)
+    for i, c in enumerate(cases):
+        p = b.params(i)
+        rho = inputs.droplets(c["nx"], c["ny"], p["rho_v"], p["rho_l"], [(c["nx"] / 2, c["ny"] / 2)], [c["R"]], 4.0)
+        z = np.zeros_like(rho)
+        b.set_fields(i, rho, z, z, np.full_like(rho, p["T0"]))
+    b.autotune(5)
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.synchronize()
+    wall = time.perf_counter() - t0
+    rows, ok, evap = [], 0, 0
+    for i, c in enumerate(cases):
+        m = b.moments(i)
+        p = b.params(i)
+        cy, cx = c["ny"] // 2, c["nx"] // 2
+        rl, Tl = m["rho"][cy, cx], m["T"][cy, cx]
+        rv, Tv = m["rho"][0, 0], m["T"][0, 0]
+        Mv = lbm.maxwell(cfgs[i], Tv / p["Tc"])[0]
+        Ml = lbm.maxwell(cfgs[i], Tl / p["Tc"])[1]
+        gone = rl < 0.5 * (Mv + Ml)
+        ev, el = rv / Mv - 1, rl / Ml - 1
+        if gone:
+            evap += 1
+        elif abs(ev) < 0.01 and abs(el) < 0.01:
+            ok += 1
+        rows.append({"nx": c["nx"], "ny": c["ny"], "R0": round(c["R"], 2), "Tr": round(c["Tr"], 4),
+                     "Tr_vapour": round(float(Tv / p["Tc"]), 5), "Tr_liquid": round(float(Tl / p["Tc"]), 5),
+                     "err_rho_v": ev, "err_rho_l": el, "evaporated": bool(gone)})
+    b.close()
+    kept = ncases - evap
+    return {"metric": "batched sweep coexistence vs Maxwell", "steps": steps, "cases": ncases,
+            "storage": precision, "wall_s": wall, "evaporated": evap,
+            "within_1pct": ok, "of_kept": kept,
+            "max_abs_err_kept": max((max(abs(r["err_rho_v"]), abs(r["err_rho_l"])) for r in rows if not r["evaporated"]),
+                                    default=None),
+            "per_case": rows}
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle as it stands, on this host's cores, on a bounded
     slice of the workload (4096 x 64 rows of the same layout with walls)."""
@@ -263,6 +385,9 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=1000,
                     help="steps of each storage format for the error-vs-FP64 comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-study", type=int, default=0,
+                    help="run the 256-case sweep for this many steps and report coexistence per case")
+    ap.add_argument("--batch-precision", default="f16s", choices=["f32", "f16s", "bf16s"])
     ap.add_argument("--nx", type=int, default=NX, help="smaller lattice for profiling captures")
     ap.add_argument("--ny", type=int, default=NY)
     args = ap.parse_args()
@@ -272,6 +397,10 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.batch_study:
+        if rank == 0:
+            print(json.dumps(batch_study(args.batch_study, precision=args.batch_precision)))
+        return
     config = {"workload": f"boiling {NX}x{NY}, walls, hot spot 32 cells, g=1e-5, {args.precision.upper()} storage",
               "nx": NX, "ny": NY, "precision": args.precision,
               "l2": "state (2 x 302 MB FP32) larger than L2; no flush needed",
