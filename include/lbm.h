@@ -227,6 +227,62 @@ int64_t lbm_batch_nodes(const lbm_batch* b);
 double lbm_batch_bytes_per_step(const lbm_batch* b);
 int lbm_batch_destroy(lbm_batch* b);
 
+/* ---- Learned surrogate ---------------------------------------------------
+ * A convolutional neural operator that advances the macroscopic fields
+ * (rho, u_x, u_y, T) of a periodic case by K lattice steps in one jump, with
+ * the LB step as its fallback and judge. Not in the paper: an extension of
+ * the method for faster time-to-solution. Network (3x3 convolutions,
+ * periodic padding, bias; BF16 tensor-core kernels, FP32 accumulation):
+ *   h0 = lift(x); h_{b+1} = h_b + conv_b2(relu(conv_b1(relu(h_b))));
+ *   y  = x + proj(relu(h_B)),
+ * on normalised fields x_c = (field_c - off[c]) / scale[c]. Parameters in
+ * lbm_surrogate_set_params order: lift weight [9][C][4], lift bias [C], for
+ * each block w1 [9][C][C], b1 [C], w2 [9][C][C], b2 [C], proj weight
+ * [9][4][C], proj bias [4] (weight index [tap][out][in], tap = 3 (dy + 1) +
+ * (dx + 1) reading input pixel (y + dy, x + dx)). Field arrays: device
+ * double, 4 planes [4][N][H][W] (rho, u_x, u_y, T); W a multiple of 16. */
+typedef struct lbm_surrogate lbm_surrogate;
+
+typedef struct lbm_surrogate_config {
+    int32_t channels;    /* C: 64 */
+    int32_t blocks;      /* B: 6 */
+    int32_t K;           /* lattice steps per jump */
+    int32_t reserved;
+    double norm_off[4];  /* normalisation offsets of rho, u_x, u_y, T */
+    double norm_scale[4];
+    void* stream;        /* cudaStream_t; NULL: own stream */
+    int32_t device;
+    int32_t pad;
+} lbm_surrogate_config;
+
+int lbm_surrogate_create(const lbm_surrogate_config* cfg, lbm_surrogate** out);
+int64_t lbm_surrogate_num_params(const lbm_surrogate* s);
+/* Host FP32 arrays of lbm_surrogate_num_params values, in the order above. */
+int lbm_surrogate_set_params(lbm_surrogate* s, const float* params);
+int lbm_surrogate_get_params(lbm_surrogate* s, float* params);
+/* One jump for N fields: out = network(in) (device arrays). Synchronous. */
+int lbm_surrogate_forward(lbm_surrogate* s, const double* in, int32_t N, int32_t H, int32_t W, double* out);
+/* Loss (mean squared error of the normalised fields) and, if grads is not
+ * NULL, its gradient in parameter order (host FP32). Synchronous. */
+int lbm_surrogate_loss_grad(lbm_surrogate* s, const double* in, const double* target, int32_t N, int32_t H,
+                            int32_t W, double* loss, float* grads);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a minibatch;
+ * returns the minibatch loss before the step. Synchronous. */
+int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* target, int32_t N, int32_t H,
+                             int32_t W, double lr, double* loss);
+/* Rollout on a periodic FP32/FP64 case: njumps times, snapshot the state,
+ * predict K steps ahead, re-initialise the populations from the predicted
+ * fields (the LB continues from the surrogate state), and compare mass and
+ * energy (sum rho e_k) before and after; an unphysical prediction
+ * (non-finite, rho <= 0 or T <= 0), a relative change above drift_tol, or a
+ * liquid area (rho above (rho_v + rho_l)/2) changing by more than drift_tol
+ * relative, restores the snapshot and runs K LB steps instead.
+ * stats (may be NULL, >= 6): [0] jumps accepted, [1] fallbacks,
+ * [2] ms in surrogate jumps, [3] ms in fallback LB steps, [4] largest
+ * accepted mass drift, [5] largest accepted energy drift. Synchronous. */
+int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, double drift_tol, double* stats);
+int lbm_surrogate_destroy(lbm_surrogate* s);
+
 /* Largest lattice (nx * ny) lbm_conservation_noalloc accepts. */
 #define LBM_NOALLOC_MAX_NODES (1 << 20)
 

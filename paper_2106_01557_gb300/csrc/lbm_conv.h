@@ -1,0 +1,46 @@
+// Launchers of the surrogate's BF16 tensor-core kernels (lbm_conv.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// x_norm = (x - off) * inv_scale per field (rho, u_x, u_y, T)
+struct NormConsts {
+    double off[4];
+    double scale[4];
+    double inv_scale[4];
+};
+
+struct ConvArgs {
+    const __nv_bfloat16* in;      // [N][H][W][cin]
+    const __nv_bfloat16* w;       // [9][cout][cin]
+    const float* bias;            // [cout] or null
+    int N, H, W;                  // W a multiple of 16
+    int in_relu;                  // apply max(0, .) to the input
+    const __nv_bfloat16* mask;    // [P][cout]: zero where mask <= 0 (or null)
+    const __nv_bfloat16* res16;   // [P][cout] added (or null)
+    const float* res32;           // [P][res32_c] added to the first res32_c channels (or null)
+    int res32_c;
+    __nv_bfloat16* out16;         // [P][cout] BF16 output, or
+    float* out32;                 // [P][cout] FP32 output
+};
+
+size_t conv_smem_bytes(int cin, int cout);
+cudaError_t launch_conv(int cin, int cout, const ConvArgs& a, cudaStream_t s, int sms);
+cudaError_t launch_wgrad(int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W,
+                         int in_relu, float* dw, cudaStream_t s, int sms);
+cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, cudaStream_t s);
+cudaError_t launch_mse(const float* out, const float* target, long long P, __nv_bfloat16* dout, double* loss,
+                       cudaStream_t s);
+cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float b1, float b2, float eps,
+                        float c1, float c2, cudaStream_t s);
+cudaError_t launch_refresh(const float* w, int cin, int cout, int cin_real, int cout_real, __nv_bfloat16* w16,
+                           __nv_bfloat16* wflip, cudaStream_t s);
+cudaError_t launch_pack(const double* rho, const double* ux, const double* uy, const double* T, long long P,
+                        const NormConsts& nc, __nv_bfloat16* x16, float* x32, cudaStream_t s);
+cudaError_t launch_unpack(const float* y, long long P, const NormConsts& nc, double* rho, double* ux, double* uy,
+                          double* T, cudaStream_t s);
+
+}  // namespace lbm

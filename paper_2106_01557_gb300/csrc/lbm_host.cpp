@@ -1079,6 +1079,33 @@ int lbm_batch_destroy(lbm_batch* b) {
     return LBM_OK;
 }
 
+}  // extern "C"
+
+int lbm_internal_fail(int code, const char* msg) { return fail(code, msg); }
+
+size_t lbm_internal_state_bytes(const lbm_handle* h) { return (size_t)18 * h->L.geo.plane * h->esize; }
+
+int lbm_internal_snapshot(lbm_handle* h, void* dst) {
+    CK(cudaMemcpyAsync(dst, h->buf[h->cur], lbm_internal_state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    return LBM_OK;
+}
+
+int lbm_internal_restore(lbm_handle* h, const void* src) {
+    CK(cudaMemcpyAsync(h->buf[h->cur], src, lbm_internal_state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    return LBM_OK;
+}
+
+cudaStream_t lbm_internal_stream(const lbm_handle* h) { return h->stream; }
+
+void lbm_internal_rho_bounds(const lbm_handle* h, double* rho_v, double* rho_l, int* nx, int* ny) {
+    *rho_v = h->prm.rho_v;
+    *rho_l = h->prm.rho_l;
+    *nx = h->cfg.nx;
+    *ny = h->cfg.ny;
+}
+
+extern "C" {
+
 int lbm_conservation_noalloc(const lbm_config* cfg, const double* f, const double* g, double* out,
                              void* stream) {
     if (!cfg || !f || !g || !out) return fail(LBM_ERR_ARG, "null argument");

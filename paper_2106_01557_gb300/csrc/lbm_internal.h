@@ -78,3 +78,12 @@ cudaError_t launch_record_noalloc(const Launch& L, const double* f, const double
                                   cudaStream_t s);
 
 }  // namespace lbm
+
+// Access the surrogate's host code needs to a single-case handle (lbm_host.cpp).
+struct lbm_handle;
+int lbm_internal_fail(int code, const char* msg);
+size_t lbm_internal_state_bytes(const lbm_handle* h);
+int lbm_internal_snapshot(lbm_handle* h, void* dst);       // device copy of the current state
+int lbm_internal_restore(lbm_handle* h, const void* src);  // and back
+cudaStream_t lbm_internal_stream(const lbm_handle* h);
+void lbm_internal_rho_bounds(const lbm_handle* h, double* rho_v, double* rho_l, int* nx, int* ny);

@@ -92,6 +92,18 @@ SIGNATURES = {
     "lbm_batch_nodes": ([_H], ctypes.c_int64),
     "lbm_batch_bytes_per_step": ([_H], ctypes.c_double),
     "lbm_batch_destroy": ([_H], ctypes.c_int),
+    "lbm_surrogate_create": ([ctypes.c_void_p, ctypes.POINTER(_H)], ctypes.c_int),
+    "lbm_surrogate_num_params": ([_H], ctypes.c_int64),
+    "lbm_surrogate_set_params": ([_H, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "lbm_surrogate_get_params": ([_H, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "lbm_surrogate_forward": ([_H, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p],
+                              ctypes.c_int),
+    "lbm_surrogate_loss_grad": ([_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                 _DP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "lbm_surrogate_train_step": ([_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_int32, ctypes.c_double, _DP], ctypes.c_int),
+    "lbm_surrogate_rollout": ([_H, _H, ctypes.c_int32, ctypes.c_double, _DP], ctypes.c_int),
+    "lbm_surrogate_destroy": ([_H], ctypes.c_int),
     "lbm_conservation_noalloc": ([ctypes.POINTER(LbmConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p], ctypes.c_int),
 }
@@ -343,3 +355,99 @@ class Batch:
 
     def bytes_per_step(self):
         return float(self.lib.lbm_batch_bytes_per_step(self.h))
+
+
+class SurrogateConfig(ctypes.Structure):
+    _fields_ = [("channels", ctypes.c_int32), ("blocks", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("norm_off", ctypes.c_double * 4),
+                ("norm_scale", ctypes.c_double * 4), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class Surrogate:
+    """The learned surrogate (lbm_surrogate_*). Fields are CUDA float64
+    tensors of shape (4, N, H, W) = (rho, u_x, u_y, T); parameters are a flat
+    float32 numpy array in the library's order."""
+
+    def __init__(self, norm_off, norm_scale, K=50, channels=64, blocks=6, stream=None):
+        self.lib = load()
+        cfg = SurrogateConfig()
+        cfg.channels, cfg.blocks, cfg.K = channels, blocks, K
+        for i in range(4):
+            cfg.norm_off[i] = float(norm_off[i])
+            cfg.norm_scale[i] = float(norm_scale[i])
+        cfg.stream = None if stream is None else stream.cuda_stream
+        self.cfg = cfg
+        h = _H()
+        _check(self.lib.lbm_surrogate_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self.K = K
+
+    def close(self):
+        if self.h:
+            self.lib.lbm_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return int(self.lib.lbm_surrogate_num_params(self.h))
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.num_params
+        _check(self.lib.lbm_surrogate_set_params(self.h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def get_params(self):
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(self.lib.lbm_surrogate_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    @staticmethod
+    def _dims(t):
+        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64" and t.shape[0] == 4
+        return int(t.shape[1]), int(t.shape[2]), int(t.shape[3])
+
+    def forward(self, fields, out):
+        N, H, W = self._dims(fields)
+        _check(self.lib.lbm_surrogate_forward(self.h, ctypes.c_void_p(fields.data_ptr()), N, H, W,
+                                              ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def loss_grad(self, fields, target, grads=True):
+        N, H, W = self._dims(fields)
+        loss = ctypes.c_double()
+        g = np.empty(self.num_params, dtype=np.float32) if grads else None
+        _check(self.lib.lbm_surrogate_loss_grad(self.h, ctypes.c_void_p(fields.data_ptr()),
+                                                ctypes.c_void_p(target.data_ptr()), N, H, W, ctypes.byref(loss),
+                                                g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if grads else None))
+        return loss.value, g
+
+    def train_step(self, fields, target, lr):
+        N, H, W = self._dims(fields)
+        loss = ctypes.c_double()
+        _check(self.lib.lbm_surrogate_train_step(self.h, ctypes.c_void_p(fields.data_ptr()),
+                                                 ctypes.c_void_p(target.data_ptr()), N, H, W, float(lr),
+                                                 ctypes.byref(loss)))
+        return loss.value
+
+    def rollout(self, lattice, njumps, drift_tol=1e-3):
+        stats = np.zeros(6)
+        _check(self.lib.lbm_surrogate_rollout(self.h, lattice.h, int(njumps), float(drift_tol), _host_ptr(stats)))
+        return {"accepted": int(stats[0]), "fallbacks": int(stats[1]), "ms_surrogate": stats[2],
+                "ms_fallback_lb": stats[3], "max_mass_drift": stats[4], "max_energy_drift": stats[5]}
+
+
+def surrogate_params_from_oracle_layout(p):
+    """Flatten a parameter dict laid out as {'lift': (w, b), 'blocks': [((w1, b1), (w2, b2)), ...],
+    'proj': (w, b)} with weights (9, Cout, Cin) into the library's order."""
+    parts = [p["lift"][0], p["lift"][1]]
+    for (w1, b1), (w2, b2) in p["blocks"]:
+        parts += [w1, b1, w2, b2]
+    parts += [p["proj"][0], p["proj"][1]]
+    return np.concatenate([np.asarray(a, dtype=np.float32).reshape(-1) for a in parts])

@@ -1,0 +1,109 @@
+"""The learned surrogate's BF16 tensor-core kernels against its FP64 oracle
+network: forward pass, loss and every parameter gradient; then training and
+the rollout with LB fallback."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _make(channels=64, blocks=2, seed=0, K=10):
+    from oracle import surrogate as S
+    from paper_2106_01557_gb300 import lbm
+    p = S.init_params(channels=channels, blocks=blocks, seed=seed)
+    # a projection large enough that the network output differs from its input
+    rng = np.random.default_rng(seed + 100)
+    p["proj"] = (rng.normal(0, 0.05, p["proj"][0].shape), rng.normal(0, 0.05, p["proj"][1].shape))
+    s = lbm.Surrogate([0, 0, 0, 0], [1, 1, 1, 1], K=K, channels=channels, blocks=blocks)
+    s.set_params(lbm.surrogate_params_from_oracle_layout(p))
+    return S, p, s
+
+
+def _fields(N, H, W, seed):
+    rng = np.random.default_rng(seed)
+    # smooth-ish normalised fields
+    x = rng.normal(size=(N, H, W, 4))
+    x = 0.5 * (x + np.roll(x, 1, axis=2))
+    return x
+
+
+def _to_dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.moveaxis(x, -1, 0))).cuda()
+
+
+def test_forward_matches_oracle(gpu_lib):
+    import torch
+    S, p, s = _make()
+    x = _fields(2, 8, 32, 1)
+    y_ref, _ = S.forward(p, x)
+    out = torch.empty((4, 2, 8, 32), dtype=torch.float64, device="cuda")
+    s.forward(_to_dev(x), out)
+    y = np.moveaxis(out.cpu().numpy(), 0, -1)
+    # the network's change of the fields, compared at BF16 precision
+    d_ref, d = y_ref - x, y - x
+    assert np.abs(d - d_ref).max() < 2e-2 * np.abs(d_ref).max()
+    assert np.corrcoef(d.ravel(), d_ref.ravel())[0, 1] > 0.999
+
+
+def test_gradients_match_oracle(gpu_lib):
+    S, p, s = _make(seed=3)
+    x = _fields(2, 8, 32, 4)
+    t = x + 0.3 * _fields(2, 8, 32, 5)
+    y_ref, cache = S.forward(p, x)
+    g_ref = S.flatten(S.backward(p, cache, y_ref, t))
+    loss, g = s.loss_grad(_to_dev(x), _to_dev(t))
+    assert loss == pytest.approx(S.loss(y_ref, t), rel=2e-2)
+    off = 0
+    for gr in g_ref:
+        n = gr.size
+        gg = g[off:off + n].astype(np.float64)
+        gr = gr.reshape(-1)
+        off += n
+        err = np.linalg.norm(gg - gr) / max(np.linalg.norm(gr), 1e-30)
+        assert err < 0.05, (off, err)
+    assert off == g.size
+
+
+def test_training_reduces_loss(gpu_lib):
+    # learn a fixed smooth map of the fields: loss falls by an order of magnitude
+    import torch
+    S, p, s = _make(blocks=2, seed=7)
+    rng = np.random.default_rng(8)
+    xs = [_fields(4, 16, 32, 20 + k) for k in range(4)]
+    ts = [x + 0.2 * np.roll(x, 1, axis=1) - 0.2 * np.roll(x, -1, axis=2) for x in xs]
+    dev = [(_to_dev(x), _to_dev(t)) for x, t in zip(xs, ts)]
+    first = [s.loss_grad(a, b, grads=False)[0] for a, b in dev]
+    for it in range(200):
+        a, b = dev[it % 4]
+        s.train_step(a, b, lr=2e-3)
+    last = [s.loss_grad(a, b, grads=False)[0] for a, b in dev]
+    assert np.mean(last) < 0.1 * np.mean(first)
+
+
+def test_rollout_falls_back_and_accepts(gpu_lib):
+    from oracle import Oracle, thermo
+    from paper_2106_01557_gb300 import inputs, lbm
+    nx = ny = 64
+    o = Oracle(thermo.Config(nx=nx, ny=ny))
+    pp = o.p
+    rho = inputs.droplets(nx, ny, pp.rho_v, pp.rho_l, [(32, 32)], [14], 4.0)
+    z = np.zeros_like(rho)
+    off = [pp.rho_v, 0.0, 0.0, pp.T0]
+    scale = [pp.rho_l - pp.rho_v, 0.01 * pp.c, 0.01 * pp.c, 0.05 * pp.Tc]
+    # an untrained network with a large projection moves the fields: rejected
+    S, p, _ = _make(blocks=2, seed=11)
+    p["proj"] = (p["proj"][0] * 20, p["proj"][1] * 20)
+    s = lbm.Surrogate(off, scale, K=10, blocks=2)
+    s.set_params(lbm.surrogate_params_from_oracle_layout(p))
+    lat = lbm.Lattice.create(nx, ny, precision="f32")
+    lat.set_fields(rho, z, z, np.full_like(rho, pp.T0))
+    st = s.rollout(lat, 3, drift_tol=1e-3)
+    assert st["fallbacks"] == 3 and st["accepted"] == 0
+    assert lat.steps == 30
+    # a network whose projection is zero is the identity: every jump is accepted
+    p["proj"] = (0 * p["proj"][0], 0 * p["proj"][1])
+    s.set_params(lbm.surrogate_params_from_oracle_layout(p))
+    st = s.rollout(lat, 3, drift_tol=1e-3)
+    assert st["accepted"] == 3 and st["fallbacks"] == 0
+    assert st["max_mass_drift"] < 1e-6
