@@ -188,6 +188,9 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.no_variants:
         variants = precision_variants(lbm, torch, args.variant_steps)
         variants["batch_f16s"] = batch_variant(lbm, torch, 100)
+        if args.surrogate_iters:
+            from paper_2106_01557_gb300 import surrogate as sur_mod
+            variants["surrogate"] = sur_mod.study(iters=args.surrogate_iters)
     return {"ms_step": ms_step, "mlups": mlups, "bytes_step": bytes_step, "clocks": clk.summary(),
             "e2e": e2e, "stats": stats.tolist(), "variants": variants}
 
@@ -388,6 +391,8 @@ def main():
     ap.add_argument("--batch-study", type=int, default=0,
                     help="run the 256-case sweep for this many steps and report coexistence per case")
     ap.add_argument("--batch-precision", default="f16s", choices=["f32", "f16s", "bf16s"])
+    ap.add_argument("--surrogate-iters", type=int, default=600,
+                    help="training iterations of the surrogate study in the default run (0: skip)")
     ap.add_argument("--nx", type=int, default=NX, help="smaller lattice for profiling captures")
     ap.add_argument("--ny", type=int, default=NY)
     args = ap.parse_args()

@@ -277,9 +277,11 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
  * (non-finite, rho <= 0 or T <= 0), a relative change above drift_tol, or a
  * liquid area (rho above (rho_v + rho_l)/2) changing by more than drift_tol
  * relative, restores the snapshot and runs K LB steps instead.
- * stats (may be NULL, >= 6): [0] jumps accepted, [1] fallbacks,
+ * stats (may be NULL, >= 10): [0] jumps accepted, [1] fallbacks,
  * [2] ms in surrogate jumps, [3] ms in fallback LB steps, [4] largest
- * accepted mass drift, [5] largest accepted energy drift. Synchronous. */
+ * accepted mass drift, [5] largest accepted energy drift, [6..8] largest
+ * mass, energy and liquid-area drift over all jumps, [9] jumps with an
+ * unphysical prediction. Synchronous. */
 int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, double drift_tol, double* stats);
 int lbm_surrogate_destroy(lbm_surrogate* s);
 

@@ -183,27 +183,34 @@ __global__ void __launch_bounds__(WT)
     for (long long ch = blockIdx.y; ch < nchunks; ch += gridDim.y) {
         const long long p0 = ch * WCH;
         __syncthreads();
-        for (int e = tid; e < WCH * (16 + CIN); e += WT) {
-            const int px = e % WCH;
-            const int c = e / WCH;
+        // 16-byte coalesced loads (8 channels of one pixel), scattered into
+        // the transposed [channel][pixel] tiles
+        constexpr int C8 = (16 + CIN) / 8;  // 8-channel groups per pixel: 2 of dOut, CIN/8 of input
+        for (int e = tid; e < WCH * C8; e += WT) {
+            const int grp = e % C8, px = e / C8;
             const long long p = p0 + px;
-            __nv_bfloat16 v = __float2bfloat16(0.f);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (p < P) {
-                if (c < 16) {
-                    v = dout[p * COUT + cot * 16 + c];
+                if (grp < 2) {
+                    v = *reinterpret_cast<const uint4*>(dout + p * COUT + cot * 16 + grp * 8);
                 } else {
-                    const int ci = c - 16;
                     const int n = (int)(p / ((long long)H * W));
                     const int rem = (int)(p % ((long long)H * W));
                     int yy = rem / W + dy, xx = rem % W + dx;
                     yy = (yy % H + H) % H;
                     xx = (xx % W + W) % W;
-                    v = in[(((size_t)n * H + yy) * W + xx) * CIN + ci];
-                    if (in_relu) v = relu_bf(v);
+                    v = *reinterpret_cast<const uint4*>(in + (((size_t)n * H + yy) * W + xx) * CIN + (grp - 2) * 8);
+                    if (in_relu) {
+                        __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&v);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) hh[j] = relu_bf(hh[j]);
+                    }
                 }
             }
-            if (c < 16) s_d[c * PP + px] = v;
-            else s_x[(c - 16) * PP + px] = v;
+            const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v);
+            __nv_bfloat16* dst = grp < 2 ? s_d + (grp * 8) * PP + px : s_x + ((grp - 2) * 8) * PP + px;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dst[j * PP] = hv[j];
         }
         __syncthreads();
         // warp w: pixels [16 w, 16 w + 16) as the k16 step; A = dOut^T (co x p), B = in (p x ci)
@@ -331,6 +338,26 @@ __global__ void k_unpack(const float* __restrict__ y, long long P, NormConsts nc
     }
 }
 
+// counts over a field set [4][P]: cnt[0] nodes with rho > mid, cnt[1] nodes
+// that are non-finite or have rho <= 0 or T <= 0
+__global__ void k_field_check(const double* __restrict__ f, long long P, double mid,
+                              unsigned long long* __restrict__ cnt) {
+    unsigned long long liq = 0, bad = 0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const double r = f[p], u = f[P + p], v = f[2 * P + p], T = f[3 * P + p];
+        liq += r > mid;
+        bad += !(isfinite(r) && isfinite(u) && isfinite(v) && isfinite(T) && r > 0.0 && T > 0.0);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        liq += __shfl_down_sync(0xffffffffu, liq, o);
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if (threadIdx.x % 32 == 0) {
+        atomicAdd(&cnt[0], liq);
+        atomicAdd(&cnt[1], bad);
+    }
+}
+
 template <int CIN, int COUT>
 cudaError_t conv_t(const ConvArgs& a, cudaStream_t s, int sms) {
     using SMc = ConvSmem<CIN, COUT>;
@@ -361,6 +388,15 @@ cudaError_t wgrad_t(const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, i
 }
 
 }  // namespace
+
+cudaError_t launch_field_check(const double* f, long long P, double mid, unsigned long long* cnt, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    long long g = (P + 255) / 256;
+    if (g > 2048) g = 2048;
+    k_field_check<<<(unsigned)g, 256, 0, s>>>(f, P, mid, cnt);
+    return cudaGetLastError();
+}
 
 size_t conv_smem_bytes(int cin, int cout) {
     if (cin == 16 && cout == 64) return ConvSmem<16, 64>::BYTES;

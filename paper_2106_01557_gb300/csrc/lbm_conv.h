@@ -43,4 +43,6 @@ cudaError_t launch_pack(const double* rho, const double* ux, const double* uy, c
 cudaError_t launch_unpack(const float* y, long long P, const NormConsts& nc, double* rho, double* ux, double* uy,
                           double* T, cudaStream_t s);
 
+cudaError_t launch_field_check(const double* f, long long P, double mid, unsigned long long* cnt, cudaStream_t s);
+
 }  // namespace lbm

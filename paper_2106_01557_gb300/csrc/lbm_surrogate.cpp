@@ -64,6 +64,7 @@ struct lbm_surrogate {
     __nv_bfloat16* g1 = nullptr;
     __nv_bfloat16* g2 = nullptr;
     double* d_loss = nullptr;
+    unsigned long long* d_cnt = nullptr;  // field checks
     double* fields = nullptr;        // 4 planes of the rollout case (device)
     double* pred = nullptr;
     void* snapshot = nullptr;
@@ -259,7 +260,8 @@ int lbm_surrogate_create(const lbm_surrogate_config* cfg, lbm_surrogate** out) {
             cudaMemset(L.w16, 0, nw * 2); cudaMemset(L.wflip, 0, nw * 2);
         }
     }
-    ok = ok && cudaMalloc(&s->d_loss, sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->d_loss, sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->d_cnt, 2 * sizeof(unsigned long long)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lbm_surrogate_destroy(s);
@@ -423,22 +425,25 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
         s->snapshot_bytes = sb;
     }
     double acc = 0, fb = 0, t_sur = 0, t_lb = 0, max_dm = 0, max_de = 0;
-    std::vector<double> rho(P), pred_host(4 * P);
-    auto liquid_area = [&](const double* r) {
-        long long a = 0;
-        const double mid = 0.5 * (rho_v + rho_l);
-        for (long long p = 0; p < P; ++p) a += r[p] > mid;
-        return (double)a;
+    double all_dm = 0, all_de = 0, all_da = 0, n_bad = 0;
+    const double mid = 0.5 * (rho_v + rho_l);
+    // device counts: cnt[0] liquid nodes, cnt[1] unphysical nodes
+    auto check = [&](const double* f, unsigned long long cnt[2]) {
+        SCK(launch_field_check(f, P, mid, s->d_cnt, s->stream));
+        SCK(cudaMemcpyAsync(cnt, s->d_cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
+        SCK(cudaStreamSynchronize(s->stream));
+        return LBM_OK;
     };
     cudaStream_t hs = lbm_internal_stream(h);
     for (int j = 0; j < njumps; ++j) {
         double c0[6], c1[6];
+        unsigned long long n0[2], n1[2];
         rc = lbm_conservation(h, c0);
         if (rc) return rc;
         rc = lbm_moments(h, s->fields, s->fields + P, s->fields + 2 * P, s->fields + 3 * P, 1);
         if (rc) return rc;
-        SCK(cudaMemcpy(rho.data(), s->fields, P * 8, cudaMemcpyDeviceToHost));
-        const double a0 = liquid_area(rho.data());
+        rc = check(s->fields, n0);
+        if (rc) return rc;
         rc = lbm_internal_snapshot(h, s->snapshot);
         if (rc) return rc;
         SCK(cudaStreamSynchronize(hs));
@@ -446,13 +451,9 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
         rc = lbm_surrogate_forward(s, s->fields, 1, ny, nx, s->pred);
         if (rc) return rc;
         // an unphysical prediction (non-finite, rho <= 0 or T <= 0) is a rejected jump
-        SCK(cudaMemcpy(pred_host.data(), s->pred, 4 * P * 8, cudaMemcpyDeviceToHost));
-        bool physical = true;
-        for (long long q = 0; q < P && physical; ++q) {
-            const double r = pred_host[q], T = pred_host[3 * P + q];
-            physical = std::isfinite(r) && std::isfinite(T) && std::isfinite(pred_host[P + q]) &&
-                       std::isfinite(pred_host[2 * P + q]) && r > 0 && T > 0;
-        }
+        rc = check(s->pred, n1);
+        if (rc) return rc;
+        const bool physical = n1[1] == 0;
         double dm = 0, de = 0, da = 0;
         if (physical) {
             rc = lbm_set_fields(h, s->pred, s->pred + P, s->pred + 2 * P, s->pred + 3 * P, 1);
@@ -465,9 +466,13 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
             if (rc) return rc;
             dm = std::fabs(c1[0] / c0[0] - 1.0);
             de = std::fabs(c1[3] / c0[3] - 1.0);
-            da = std::fabs(liquid_area(pred_host.data()) - a0) / std::max(a0, 1.0);
+            da = std::fabs((double)n1[0] - (double)n0[0]) / std::max((double)n0[0], 1.0);
         }
         const bool bad = !physical || !(dm <= drift_tol) || !(de <= drift_tol) || !(da <= drift_tol);
+        all_dm = std::max(all_dm, dm);
+        all_de = std::max(all_de, de);
+        all_da = std::max(all_da, da);
+        n_bad += physical ? 0.0 : 1.0;
         if (bad) {
             if (physical) {
                 rc = lbm_internal_restore(h, s->snapshot);
@@ -488,6 +493,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
     }
     if (stats) {
         stats[0] = acc; stats[1] = fb; stats[2] = t_sur; stats[3] = t_lb; stats[4] = max_dm; stats[5] = max_de;
+        stats[6] = all_dm; stats[7] = all_de; stats[8] = all_da; stats[9] = n_bad;
     }
     return LBM_OK;
 }
@@ -500,7 +506,7 @@ int lbm_surrogate_destroy(lbm_surrogate* s) {
         s_free(L.vb); s_free(L.w16); s_free(L.wflip);
     }
     release_acts(s);
-    s_free(s->d_loss); s_free(s->fields); s_free(s->pred); s_free(s->snapshot);
+    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->fields); s_free(s->pred); s_free(s->snapshot);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return LBM_OK;

@@ -176,6 +176,9 @@ def conservation_noalloc(cfg: LbmConfig, f, g, out, stream=None):
     lib = load()
     for t in (f, g, out):
         assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"
+    import torch
+    if stream is None:
+        torch.cuda.current_stream().synchronize()
     s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(lib.lbm_conservation_noalloc(ctypes.byref(cfg), ctypes.c_void_p(f.data_ptr()),
                                         ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(out.data_ptr()), s))
@@ -216,8 +219,11 @@ class Lattice:
     def set_fields(self, rho, ux, uy, T):
         arrs = (rho, ux, uy, T)
         if hasattr(rho, "data_ptr"):
+            import torch
             for a in arrs:
                 assert a.is_cuda and a.is_contiguous() and str(a.dtype) == "torch.float64"
+            # the handle's stream is not ordered after torch's: finish the producers
+            torch.cuda.current_stream().synchronize()
             _check(self.lib.lbm_set_fields(self.h, *(_dev_ptr(a) for a in arrs), 1))
         else:
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
@@ -233,6 +239,8 @@ class Lattice:
         """dict rho, ux, uy, T as (ny, nx) float64 host arrays; or, with
         out = dict of CUDA float64 tensors, filled on the device."""
         if out is not None:
+            import torch
+            torch.cuda.current_stream().synchronize()
             _check(self.lib.lbm_moments(self.h, *(_dev_ptr(out[k]) for k in ("rho", "ux", "uy", "T")), 1))
             return out
         res = {k: np.empty((self.ny, self.nx)) for k in ("rho", "ux", "uy", "T")}
@@ -370,6 +378,9 @@ class Surrogate:
     float32 numpy array in the library's order."""
 
     def __init__(self, norm_off, norm_scale, K=50, channels=64, blocks=6, stream=None):
+        """stream: a torch.cuda.Stream to issue the work on (None: a stream of
+        the library's own). Every call first waits for torch's current
+        stream, so that the tensors it reads are complete."""
         self.lib = load()
         cfg = SurrogateConfig()
         cfg.channels, cfg.blocks, cfg.K = channels, blocks, K
@@ -378,6 +389,8 @@ class Surrogate:
             cfg.norm_scale[i] = float(norm_scale[i])
         cfg.stream = None if stream is None else stream.cuda_stream
         self.cfg = cfg
+        self.norm_off = [float(v) for v in norm_off]
+        self.norm_scale = [float(v) for v in norm_scale]
         h = _H()
         _check(self.lib.lbm_surrogate_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h
@@ -410,7 +423,10 @@ class Surrogate:
 
     @staticmethod
     def _dims(t):
+        import torch
         assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64" and t.shape[0] == 4
+        # the library's stream is not ordered after torch's: finish the producers
+        torch.cuda.current_stream().synchronize()
         return int(t.shape[1]), int(t.shape[2]), int(t.shape[3])
 
     def forward(self, fields, out):
@@ -437,10 +453,14 @@ class Surrogate:
         return loss.value
 
     def rollout(self, lattice, njumps, drift_tol=1e-3):
-        stats = np.zeros(6)
+        import torch
+        torch.cuda.current_stream().synchronize()
+        stats = np.zeros(10)
         _check(self.lib.lbm_surrogate_rollout(self.h, lattice.h, int(njumps), float(drift_tol), _host_ptr(stats)))
         return {"accepted": int(stats[0]), "fallbacks": int(stats[1]), "ms_surrogate": stats[2],
-                "ms_fallback_lb": stats[3], "max_mass_drift": stats[4], "max_energy_drift": stats[5]}
+                "ms_fallback_lb": stats[3], "max_mass_drift": stats[4], "max_energy_drift": stats[5],
+                "max_mass_drift_all": stats[6], "max_energy_drift_all": stats[7], "max_area_drift_all": stats[8],
+                "unphysical": int(stats[9])}
 
 
 def surrogate_params_from_oracle_layout(p):

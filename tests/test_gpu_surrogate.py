@@ -107,3 +107,20 @@ def test_rollout_falls_back_and_accepts(gpu_lib):
     st = s.rollout(lat, 3, drift_tol=1e-3)
     assert st["accepted"] == 3 and st["fallbacks"] == 0
     assert st["max_mass_drift"] < 1e-6
+
+
+def test_trained_network_beats_no_change_on_held_out_runs(gpu_lib):
+    # the gain of the learned part over the method without it, on data the
+    # network never saw: LB snapshot pairs K = 50 steps apart from evaporating
+    # droplets; after a short training the network's loss on held-out runs is
+    # below the loss of predicting no change (what the plain method offers in
+    # the same single call)
+    from paper_2106_01557_gb300 import lbm, surrogate as S
+    snaps, p = S.generate_pairs(n_runs=10, pairs_per_run=20, K=50, size=256, seed=30)
+    off, scale = S.norm_consts(p)
+    sur = lbm.Surrogate(off, scale, K=50)
+    sur.set_params(S.init_params(seed=1))
+    losses, hold, _ = S.train(sur, snaps, iters=250, batch=8, lr=1e-3, seed=2, holdout_runs=2)
+    pers = S.persistence_loss(sur, snaps, holdout_runs=2)
+    assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:20])
+    assert hold < pers, (hold, pers)
