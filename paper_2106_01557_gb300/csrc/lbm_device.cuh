@@ -88,7 +88,8 @@ __device__ __forceinline__ void populations9(const C m[9], C l[9]) {
 
 // Per-node macroscopic state (Eq. 13, 14) from the pulled populations and
 // the density field around the node: rn[i] = rho(x + e_i), rn[0] = rho(x),
-// which every caller has already formed as sum_i f_i (Eq. 14).
+// which every caller has already formed as sum_i f_i (Eq. 14). The moments
+// m = M f and n = M g are kept for the collision.
 template <class C>
 struct NodeMacro {
     C rho, inv_rho;
@@ -96,11 +97,14 @@ struct NodeMacro {
     C Fhx, Fhy;    // F / c
     C uhx, uhy;    // u / c
     C q, rek, T;
+    C m[9], n[9];
 };
 
 template <class C>
 __device__ __forceinline__ void node_macro(const KC<C>& k, const C f[9], const C g[9], const C rn[9],
                                            NodeMacro<C>& s) {
+    moments9(f, s.m);
+    moments9(g, s.n);
     const C rho = rn[0];
     // Eq. 13 weights: 1/3 on the axes, 1/12 on the diagonals
     const C third = C(1.0 / 3.0), twelfth = C(1.0 / 12.0);
@@ -110,15 +114,12 @@ __device__ __forceinline__ void node_macro(const KC<C>& k, const C f[9], const C
     s.inv_rho = recip(rho);
     s.Fhx = k.G2c * rho * s.gx + rho * k.axc;
     s.Fhy = k.G2c * rho * s.gy + rho * k.ayc;
-    const C jx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
-    const C jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
-    // Eq. 14: rho u = sum e_i f_i + dt/2 F  ->  rho u^ = j^ + dt/2 F^
-    s.uhx = (jx + k.half_dt * s.Fhx) * s.inv_rho;
-    s.uhy = (jy + k.half_dt * s.Fhy) * s.inv_rho;
+    // Eq. 14: rho u = sum e_i f_i + dt/2 F  ->  rho u^ = m_3,5 + dt/2 F^
+    s.uhx = (s.m[3] + k.half_dt * s.Fhx) * s.inv_rho;
+    s.uhy = (s.m[5] + k.half_dt * s.Fhy) * s.inv_rho;
     // q = F . u = c^2 F^ . u^
     s.q = k.c2 * (s.Fhx * s.uhx + s.Fhy * s.uhy);
-    const C sg = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    s.rek = sg + k.half_dt * s.q;
+    s.rek = s.n[0] + k.half_dt * s.q;
     const C ke = C(0.5) * k.c2 * (s.uhx * s.uhx + s.uhy * s.uhy);
     s.T = (s.rek * s.inv_rho - ke) * k.inv_cv;
 }
@@ -183,10 +184,11 @@ __device__ __forceinline__ void equilibria(const KC<C>& k, const NodeMacro<C>& s
     qm[8] = C(0);
 }
 
-// The collision of both DFs at one node (Eq. 12b, 12c). On entry f, g hold
-// the pulled populations; on exit the post-collision ones. Rows 0, 3, 5 of
-// m - m^eq + dt/2 F_m and row 0 of n - n^eq + dt/2 q_m vanish by Eq. 14,
-// so s_0, s_j and sigma_0 never act and are not applied.
+// The collision of both DFs at one node (Eq. 12b, 12c). On entry s holds
+// the moments of the pulled populations; on exit f, g hold the post-
+// collision populations. Rows 0, 3, 5 of m - m^eq + dt/2 F_m and row 0 of
+// n - n^eq + dt/2 q_m vanish by Eq. 14, so s_0, s_j and sigma_0 never act
+// and are not applied.
 template <class C>
 __device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const NodeMacro<C>& s) {
     const C rho = s.rho, ux = s.uhx, uy = s.uhy;
@@ -196,18 +198,18 @@ __device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const No
     const C rhk = s.rek + pbe;
     const C Fx = s.Fhx, Fy = s.Fhy;
     const C FU = Fx * ux + Fy * uy;
+    const C* m = s.m;
+    const C* n = s.n;
 
     // ---- f: m_bar = m + dt F_m - S (m - m^eq + dt/2 F_m - Q_m) -----------
-    C m[9];
-    moments9(f, m);
-    const C meq1 = C(-2) * rho + C(2) * eta + C(3) * rho * u2;
-    const C meq2 = rho + k.beta * eta - C(3) * rho * u2;
+    const C r3u2 = C(3) * rho * u2;
+    const C meq1 = C(-2) * rho + C(2) * eta + r3u2;
+    const C meq2 = rho + k.beta * eta - r3u2;
     const C meq7 = rho * (ux * ux - uy * uy);
     const C meq8 = rho * ux * uy;
     const C Fm1 = C(6) * FU, Fm7 = C(2) * (Fx * ux - Fy * uy), Fm8 = Fx * uy + Fy * ux;
     // Q_m of SM Eq. S6a with grad rho = F_pair / (G^2 rho)
-    const C g2 = s.gx * s.gx + s.gy * s.gy;
-    const C Q1 = C(6) * k.qc * g2;
+    const C Q1 = k.six_qc * (s.gx * s.gx + s.gy * s.gy);
     const C Q7 = k.qc * (s.gx * s.gx - s.gy * s.gy);
     const C Q8 = k.qc * s.gx * s.gy;
     const C w1 = m[1] - meq1 + k.half_dt * Fm1 - Q1;
@@ -217,11 +219,10 @@ __device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const No
     const C w7 = m[7] - meq7 + k.half_dt * Fm7 - Q7;
     const C w8 = m[8] - meq8 + k.half_dt * Fm8 - Q8;
     // S of SM Eq. S5a; omega_e = s_e/2 - 1, omega_p = s_p/2 - 1
-    const C we = C(0.5) * k.se - C(1), wp = C(0.5) * k.sp - C(1);
     const C sqw4 = k.sq * w4, sqw6 = k.sq * w6;
-    const C Sw1 = k.se * w1 + we * (k.kS * k.seps * w2 + k.hS * (ux * sqw4 + uy * sqw6));
-    const C Sw7 = k.sp * w7 + k.bS * wp * C(2) * (ux * sqw4 - uy * sqw6);
-    const C Sw8 = k.sp * w8 + k.bS * wp * (uy * sqw4 + ux * sqw6);
+    const C Sw1 = k.se * w1 + k.we_kS_seps * w2 + k.we_hS * (ux * sqw4 + uy * sqw6);
+    const C Sw7 = k.sp * w7 + k.wp_bS * (C(2) * (ux * sqw4 - uy * sqw6));
+    const C Sw8 = k.sp * w8 + k.wp_bS * (uy * sqw4 + ux * sqw6);
     C mb[9];
     mb[0] = m[0];
     mb[1] = m[1] + k.dt * Fm1 - Sw1;
@@ -239,11 +240,9 @@ __device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const No
     populations9(mb, f);
 
     // ---- g: n_bar = n + dt q_m - L (n - n^eq + dt/2 q_m) + c^2 Y d -------
-    C n[9];
-    moments9(g, n);
-    const C E = s.rek, CT = k.Cref * s.T, q = s.q;
-    const C z1 = n[1] - (C(-4) * E + (C(4) + k.g1) * CT) + k.half_dt * k.g1 * q;
-    const C z2 = n[2] - (C(4) * E - (C(4) - k.g2) * CT) + k.half_dt * k.g2 * q;
+    const C E = s.rek, T = s.T, q = s.q;
+    const C z1 = n[1] + C(4) * E - k.c4g1_Cref * T + k.hdt_g1 * q;
+    const C z2 = n[2] - C(4) * E + k.c4g2_Cref * T + k.hdt_g2 * q;
     const C qux = q * ux, quy = q * uy;
     const C z3 = n[3] - rhk * ux + k.half_dt * qux;
     const C z4 = n[4] + rhk * ux - k.half_dt * qux;
@@ -253,19 +252,18 @@ __device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const No
     C wl = (rho - k.rho_v) * k.inv_drho;
     wl = wl < C(0) ? C(0) : (wl > C(1) ? C(1) : wl);
     const C sj = recip(k.tauj_v + k.dtauj * wl + C(0.5));
-    const C sq = sj;
-    const C wj = C(0.5) * sj - C(1);
+    const C sjwj = sj * (C(0.5) * sj - C(1));   // sigma_q omega_j with sigma_q = sigma_j
     // c^2 Y d of SM Eq. S6b
-    const C yx = k.c2 * (ux * (d1 * C(1.0 / 3.0) + d7) + C(2) * uy * d8);
-    const C yy = k.c2 * (uy * (d1 * C(1.0 / 3.0) - d7) + C(2) * ux * d8);
+    const C yx = k.c2_third * ux * d1 + k.c2 * (ux * d7 + C(2) * uy * d8);
+    const C yy = k.c2_third * uy * d1 + k.c2 * (C(2) * ux * d8 - uy * d7);
     C nb[9];
     nb[0] = n[0] + k.dt * q;
-    nb[1] = n[1] + k.dt * k.g1 * q - k.sige * z1;
-    nb[2] = n[2] + k.dt * k.g2 * q - k.sigeps * z2;
-    nb[3] = n[3] + k.dt * qux - (sj * z3 + sq * wj * z4) + yx;
-    nb[4] = n[4] - k.dt * qux - sq * z4 - yx;
-    nb[5] = n[5] + k.dt * quy - (sj * z5 + sq * wj * z6) + yy;
-    nb[6] = n[6] - k.dt * quy - sq * z6 - yy;
+    nb[1] = n[1] + k.dt_g1 * q - k.sige * z1;
+    nb[2] = n[2] + k.dt_g2 * q - k.sigeps * z2;
+    nb[3] = n[3] + k.dt * qux - (sj * z3 + sjwj * z4) + yx;
+    nb[4] = n[4] - k.dt * qux - sj * z4 - yx;
+    nb[5] = n[5] + k.dt * quy - (sj * z5 + sjwj * z6) + yy;
+    nb[6] = n[6] - k.dt * quy - sj * z6 - yy;
     nb[7] = n[7] - k.sigp * n[7];
     nb[8] = n[8] - k.sigp * n[8];
     populations9(nb, g);

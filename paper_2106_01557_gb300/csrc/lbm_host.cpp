@@ -310,6 +310,17 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
         k.rho_v = cast(p.rho_v);
         k.inv_drho = cast(1.0 / (p.rho_l - p.rho_v));
         k.qc = cast(p.G2 * p.dt * p.dt / 12.0);
+        k.we_kS_seps = cast((0.5 * p.se - 1.0) * p.kS * c.s_eps);
+        k.we_hS = cast((0.5 * p.se - 1.0) * p.hS);
+        k.wp_bS = cast((0.5 * c.s_p - 1.0) * p.bS);
+        k.six_qc = cast(6.0 * p.G2 * p.dt * p.dt / 12.0);
+        k.dt_g1 = cast(p.dt * c.gamma1);
+        k.dt_g2 = cast(p.dt * c.gamma2);
+        k.hdt_g1 = cast(0.5 * p.dt * c.gamma1);
+        k.hdt_g2 = cast(0.5 * p.dt * c.gamma2);
+        k.c4g1_Cref = cast((4.0 + c.gamma1) * p.Cref);
+        k.c4g2_Cref = cast((4.0 - c.gamma2) * p.Cref);
+        k.c2_third = cast(p.c * p.c / 3.0);
         k.T_bottom = cast(c.Tr_bottom > 0 ? c.Tr_bottom * p.Tc : 0.0);
         k.T_top = cast(c.Tr_top > 0 ? c.Tr_top * p.Tc : 0.0);
         k.T_hot = cast(c.Tr_hot > 0 ? c.Tr_hot * p.Tc : 0.0);

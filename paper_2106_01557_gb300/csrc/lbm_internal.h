@@ -29,6 +29,14 @@ struct KC {
     C se, seps, sq, sp, sige, sigeps, sigp;
     C tauj_v, dtauj, rho_v, inv_drho;
     C qc;            // G^2 dt^2 / 12 of SM Eq. S6a (dx = 1)
+    // products of the constants above, formed once on the host
+    C we_kS_seps;    // (s_e/2 - 1) k s_eps
+    C we_hS;         // (s_e/2 - 1) h
+    C wp_bS;         // (s_p/2 - 1) b
+    C six_qc;        // 6 qc
+    C dt_g1, dt_g2, hdt_g1, hdt_g2;  // dt gamma_1, dt gamma_2, dt/2 gamma_1, dt/2 gamma_2
+    C c4g1_Cref, c4g2_Cref;          // (4 + gamma_1) C_ref, (4 - gamma_2) C_ref
+    C c2_third;      // c^2 / 3
     C T_bottom, T_top, T_hot;
     C rest[18];      // shifted-storage rest populations (f 0..8, g 9..17)
 };

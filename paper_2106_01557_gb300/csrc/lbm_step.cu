@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
                 acc.et += s.rek - k.a * s.rho * s.rho - k.half_kappa * s.rho * lap;
                 const C u2 = s.uhx * s.uhx + s.uhy * s.uhy;
                 acc.u2max = u2 > acc.u2max ? u2 : acc.u2max;
-                if (!(rho > C(0)) || !isfinite(rho) || !isfinite(u2)) acc.bad += C(1);
+                if (!(rho > C(0) && rho < C(1e30) && u2 < C(1e30))) acc.bad += C(1);  // also catches NaN
             }
             collide(k, f, g, s);
 
