@@ -247,7 +247,10 @@ typedef struct lbm_surrogate_config {
     int32_t channels;    /* C: 64 */
     int32_t blocks;      /* B: 6 */
     int32_t K;           /* lattice steps per jump */
-    int32_t reserved;
+    int32_t conv_path;   /* 3x3 convolutions (forward and input gradient):
+                            0 tcgen05 MMAs with tensor-memory accumulators,
+                            1 warp-level mma.sync; weight gradients use
+                            mma.sync either way */
     double norm_off[4];  /* normalisation offsets of rho, u_x, u_y, T */
     double norm_scale[4];
     void* stream;        /* cudaStream_t; NULL: own stream */

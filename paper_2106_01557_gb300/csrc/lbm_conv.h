@@ -29,6 +29,10 @@ struct ConvArgs {
 
 size_t conv_smem_bytes(int cin, int cout);
 cudaError_t launch_conv(int cin, int cout, const ConvArgs& a, cudaStream_t s, int sms);
+// The same convolution on tcgen05 MMAs with tensor-memory accumulators
+// (lbm_conv_tc.cu); bit 0 of the device int *status is set if a wait for
+// the tensor cores ran out of time (the output is then incomplete).
+cudaError_t launch_conv_tc(int cin, int cout, const ConvArgs& a, cudaStream_t s, int sms, int* status);
 cudaError_t launch_wgrad(int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W,
                          int in_relu, float* dw, cudaStream_t s, int sms);
 cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, cudaStream_t s);

@@ -1,7 +1,8 @@
 // Host runtime of the learned surrogate: parameters (FP32 master copies,
 // Adam moments, BF16 forward and flipped copies), activation buffers, the
 // forward and backward passes built from the BF16 tensor-core kernels of
-// lbm_conv.cu, and the rollout with LB fallback.
+// lbm_conv_tc.cu (tcgen05) or lbm_conv.cu (mma.sync; weight gradients and
+// the elementwise kernels), and the rollout with LB fallback.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -65,6 +66,7 @@ struct lbm_surrogate {
     __nv_bfloat16* g2 = nullptr;
     double* d_loss = nullptr;
     unsigned long long* d_cnt = nullptr;  // field checks
+    int* d_status = nullptr;         // bit 0: a tensor-core wait ran out of time
     double* fields = nullptr;        // 4 planes of the rollout case (device)
     double* pred = nullptr;
     void* snapshot = nullptr;
@@ -134,13 +136,40 @@ static ConvArgs cargs(const __nv_bfloat16* in, const __nv_bfloat16* w, const flo
     return a;
 }
 
+// 3x3 convolution on the configured path
+static int conv(lbm_surrogate* s, int cin, int cout, const ConvArgs& a) {
+    if (s->cfg.conv_path == 0) {
+        SCK(launch_conv_tc(cin, cout, a, s->stream, s->sms, s->d_status));
+    } else {
+        SCK(launch_conv(cin, cout, a, s->stream, s->sms));
+    }
+    return LBM_OK;
+}
+
+#define CONV(cin, cout, a)                \
+    do {                                  \
+        int rc_ = conv(s, cin, cout, a);  \
+        if (rc_) return rc_;              \
+    } while (0)
+
+// after a stream synchronisation: fail if a tensor-core wait ran out of time
+static int check_status(lbm_surrogate* s) {
+    int st = 0;
+    SCK(cudaMemcpy(&st, s->d_status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st) {
+        SCK(cudaMemset(s->d_status, 0, sizeof st));
+        return sfail(LBM_ERR_CUDA, "a tensor-core completion wait ran out of time");
+    }
+    return LBM_OK;
+}
+
 // forward pass; with train = true every activation is kept for backward
 static int run_forward(lbm_surrogate* s, int N, int H, int W, bool train) {
     const int B = s->cfg.blocks, C = s->cfg.channels;
     const Layer& lift = s->layers[0];
     ConvArgs a = cargs(s->x16, lift.w16, lift.b, N, H, W, 0);
     a.out16 = s->h[0];
-    SCK(launch_conv(16, C, a, s->stream, s->sms));
+    CONV(16, C, a);
     for (int b = 0; b < B; ++b) {
         const Layer& L1 = s->layers[1 + 2 * b];
         const Layer& L2 = s->layers[2 + 2 * b];
@@ -149,18 +178,18 @@ static int run_forward(lbm_surrogate* s, int N, int H, int W, bool train) {
         __nv_bfloat16* z = train ? s->z1[b] : s->z1[0];
         a = cargs(hin, L1.w16, L1.b, N, H, W, 1);
         a.out16 = z;
-        SCK(launch_conv(C, C, a, s->stream, s->sms));
+        CONV(C, C, a);
         a = cargs(z, L2.w16, L2.b, N, H, W, 1);
         a.res16 = hin;
         a.out16 = hout;
-        SCK(launch_conv(C, C, a, s->stream, s->sms));
+        CONV(C, C, a);
     }
     const Layer& proj = s->layers.back();
     a = cargs(train ? s->h[B] : s->h[B & 1], proj.w16, proj.b, N, H, W, 1);
     a.res32 = s->x32;
     a.res32_c = 4;
     a.out32 = s->y32;
-    SCK(launch_conv(C, 16, a, s->stream, s->sms));
+    CONV(C, 16, a);
     return LBM_OK;
 }
 
@@ -178,7 +207,7 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
     ConvArgs a = cargs(s->dy16, proj.wflip, nullptr, N, H, W, 0);
     a.mask = s->h[B];
     a.out16 = s->g0;  // d h_B
-    SCK(launch_conv(16, C, a, s->stream, s->sms));
+    CONV(16, C, a);
     __nv_bfloat16* dh = s->g0;
     __nv_bfloat16* spare = s->g2;
     for (int b = B - 1; b >= 0; --b) {
@@ -190,14 +219,14 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
         a = cargs(dh, L2.wflip, nullptr, N, H, W, 0);
         a.mask = s->z1[b];
         a.out16 = s->g1;  // d z1
-        SCK(launch_conv(C, C, a, s->stream, s->sms));
+        CONV(C, C, a);
         SCK(launch_wgrad(C, C, s->h[b], s->g1, N, H, W, 1, L1.gw, s->stream, s->sms));
         SCK(launch_bgrad(s->g1, P, C, L1.gb, s->stream));
         a = cargs(s->g1, L1.wflip, nullptr, N, H, W, 0);
         a.mask = s->h[b];
         a.res16 = dh;
         a.out16 = spare;  // d h_b = d h_{b+1} + conv1^T(d z1) * [h_b > 0]
-        SCK(launch_conv(C, C, a, s->stream, s->sms));
+        CONV(C, C, a);
         std::swap(dh, spare);
     }
     Layer& lift = s->layers[0];
@@ -219,6 +248,7 @@ int lbm_surrogate_create(const lbm_surrogate_config* cfg, lbm_surrogate** out) {
     if (cfg->channels != 64) return sfail(LBM_ERR_ARG, "the tensor-core kernels are built for 64 channels");
     if (cfg->blocks < 1 || cfg->blocks > 64) return sfail(LBM_ERR_ARG, "blocks must lie in [1, 64]");
     if (cfg->K < 1) return sfail(LBM_ERR_ARG, "K must be positive");
+    if (cfg->conv_path != 0 && cfg->conv_path != 1) return sfail(LBM_ERR_ARG, "conv_path must be 0 (tcgen05) or 1 (mma.sync)");
     for (int c = 0; c < 4; ++c)
         if (!(cfg->norm_scale[c] > 0)) return sfail(LBM_ERR_ARG, "normalisation scales must be positive");
     lbm_surrogate* s = new (std::nothrow) lbm_surrogate();
@@ -261,7 +291,8 @@ int lbm_surrogate_create(const lbm_surrogate_config* cfg, lbm_surrogate** out) {
         }
     }
     ok = ok && cudaMalloc(&s->d_loss, sizeof(double)) == cudaSuccess &&
-         cudaMalloc(&s->d_cnt, 2 * sizeof(unsigned long long)) == cudaSuccess;
+         cudaMalloc(&s->d_cnt, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+         cudaMalloc(&s->d_status, sizeof(int)) == cudaSuccess && cudaMemset(s->d_status, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lbm_surrogate_destroy(s);
@@ -347,7 +378,7 @@ int lbm_surrogate_forward(lbm_surrogate* s, const double* in, int32_t N, int32_t
     if (rc) return rc;
     SCK(launch_unpack(s->y32, P, s->nc, out, out + P, out + 2 * P, out + 3 * P, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
-    return LBM_OK;
+    return check_status(s);
 }
 
 static int loss_and_backward(lbm_surrogate* s, const double* in, const double* target, int N, int H, int W,
@@ -369,7 +400,7 @@ static int loss_and_backward(lbm_surrogate* s, const double* in, const double* t
         SCK(cudaMemcpyAsync(loss, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     }
     SCK(cudaStreamSynchronize(s->stream));
-    return LBM_OK;
+    return check_status(s);
 }
 
 int lbm_surrogate_loss_grad(lbm_surrogate* s, const double* in, const double* target, int32_t N, int32_t H,
@@ -506,7 +537,7 @@ int lbm_surrogate_destroy(lbm_surrogate* s) {
         s_free(L.vb); s_free(L.w16); s_free(L.wflip);
     }
     release_acts(s);
-    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->fields); s_free(s->pred); s_free(s->snapshot);
+    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->d_status); s_free(s->fields); s_free(s->pred); s_free(s->snapshot);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return LBM_OK;

@@ -367,7 +367,7 @@ class Batch:
 
 class SurrogateConfig(ctypes.Structure):
     _fields_ = [("channels", ctypes.c_int32), ("blocks", ctypes.c_int32), ("K", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("norm_off", ctypes.c_double * 4),
+                ("conv_path", ctypes.c_int32), ("norm_off", ctypes.c_double * 4),
                 ("norm_scale", ctypes.c_double * 4), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
@@ -377,13 +377,18 @@ class Surrogate:
     tensors of shape (4, N, H, W) = (rho, u_x, u_y, T); parameters are a flat
     float32 numpy array in the library's order."""
 
-    def __init__(self, norm_off, norm_scale, K=50, channels=64, blocks=6, stream=None):
+    def __init__(self, norm_off, norm_scale, K=50, channels=64, blocks=6, stream=None, conv_path="tcgen05"):
         """stream: a torch.cuda.Stream to issue the work on (None: a stream of
         the library's own). Every call first waits for torch's current
-        stream, so that the tensors it reads are complete."""
+        stream, so that the tensors it reads are complete. conv_path:
+        "tcgen05" (tensor-memory accumulators) or "mma" (warp-level MMAs) for
+        the 3x3 convolutions."""
         self.lib = load()
         cfg = SurrogateConfig()
         cfg.channels, cfg.blocks, cfg.K = channels, blocks, K
+        if conv_path not in ("tcgen05", "mma"):
+            raise ValueError("conv_path must be 'tcgen05' or 'mma'")
+        cfg.conv_path = 0 if conv_path == "tcgen05" else 1
         for i in range(4):
             cfg.norm_off[i] = float(norm_off[i])
             cfg.norm_scale[i] = float(norm_scale[i])

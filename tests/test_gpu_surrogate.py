@@ -1,20 +1,25 @@
 """The learned surrogate's BF16 tensor-core kernels against its FP64 oracle
-network: forward pass, loss and every parameter gradient; then training and
-the rollout with LB fallback."""
+network: forward pass, loss and every parameter gradient, on both
+convolution paths (tcgen05 with tensor-memory accumulators, warp-level
+mma.sync); sampled windows of a full-size 1024 x 1024 forward pass; then
+training and the rollout with LB fallback."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 
-def _make(channels=64, blocks=2, seed=0, K=10):
+PATHS = ["tcgen05", "mma"]
+
+
+def _make(channels=64, blocks=2, seed=0, K=10, conv_path="tcgen05"):
     from oracle import surrogate as S
     from paper_2106_01557_gb300 import lbm
     p = S.init_params(channels=channels, blocks=blocks, seed=seed)
     # a projection large enough that the network output differs from its input
     rng = np.random.default_rng(seed + 100)
     p["proj"] = (rng.normal(0, 0.05, p["proj"][0].shape), rng.normal(0, 0.05, p["proj"][1].shape))
-    s = lbm.Surrogate([0, 0, 0, 0], [1, 1, 1, 1], K=K, channels=channels, blocks=blocks)
+    s = lbm.Surrogate([0, 0, 0, 0], [1, 1, 1, 1], K=K, channels=channels, blocks=blocks, conv_path=conv_path)
     s.set_params(lbm.surrogate_params_from_oracle_layout(p))
     return S, p, s
 
@@ -32,22 +37,54 @@ def _to_dev(x):
     return torch.from_numpy(np.ascontiguousarray(np.moveaxis(x, -1, 0))).cuda()
 
 
-def test_forward_matches_oracle(gpu_lib):
-    import torch
-    S, p, s = _make()
-    x = _fields(2, 8, 32, 1)
-    y_ref, _ = S.forward(p, x)
-    out = torch.empty((4, 2, 8, 32), dtype=torch.float64, device="cuda")
-    s.forward(_to_dev(x), out)
-    y = np.moveaxis(out.cpu().numpy(), 0, -1)
+def _close(d, d_ref):
     # the network's change of the fields, compared at BF16 precision
-    d_ref, d = y_ref - x, y - x
     assert np.abs(d - d_ref).max() < 2e-2 * np.abs(d_ref).max()
     assert np.corrcoef(d.ravel(), d_ref.ravel())[0, 1] > 0.999
 
 
-def test_gradients_match_oracle(gpu_lib):
-    S, p, s = _make(seed=3)
+# (N, H, W): one partial 128-pixel strip; several strips with a ragged 16-pixel
+# tail and more rows than CTAs, so runs of rows cross strip and image borders
+SHAPES = [(2, 8, 32), (3, 20, 272)]
+
+
+@pytest.mark.parametrize("conv_path", PATHS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_forward_matches_oracle(gpu_lib, conv_path, shape):
+    import torch
+    S, p, s = _make(conv_path=conv_path)
+    x = _fields(*shape, 1)
+    y_ref, _ = S.forward(p, x)
+    out = torch.empty((4,) + shape, dtype=torch.float64, device="cuda")
+    s.forward(_to_dev(x), out)
+    y = np.moveaxis(out.cpu().numpy(), 0, -1)
+    _close(y - x, y_ref - x)
+
+
+def test_forward_full_size_sampled_windows(gpu_lib):
+    # 1024 x 1024 (the rollout size): every CTA walks long runs of rows.
+    # The output at a pixel depends only on inputs within R = 2 B + 2 pixels
+    # (B blocks of two 3 x 3 convolutions, plus lift and projection), so the
+    # oracle on a crop of the periodic input, R pixels wider on each side,
+    # gives the exact output on the crop's centre.
+    import torch
+    S, p, s = _make(blocks=2, seed=5)
+    R, h = 2 * 2 + 2, 32
+    x = _fields(1, 1024, 1024, 6)
+    out = torch.empty((4, 1, 1024, 1024), dtype=torch.float64, device="cuda")
+    s.forward(_to_dev(x), out)
+    y = np.moveaxis(out.cpu().numpy(), 0, -1)
+    for (yc, xc) in [(0, 0), (500, 640), (1000, 1016)]:
+        crop = np.roll(x, (R - yc, R - xc), axis=(1, 2))[:, :h + 2 * R, :h + 2 * R]
+        y_ref, _ = S.forward(p, crop)
+        got = np.roll(y, (-yc, -xc), axis=(1, 2))[:, :h, :h]
+        ref = y_ref[:, R:R + h, R:R + h]
+        _close(got - crop[:, R:R + h, R:R + h], ref - crop[:, R:R + h, R:R + h])
+
+
+@pytest.mark.parametrize("conv_path", PATHS)
+def test_gradients_match_oracle(gpu_lib, conv_path):
+    S, p, s = _make(seed=3, conv_path=conv_path)
     x = _fields(2, 8, 32, 4)
     t = x + 0.3 * _fields(2, 8, 32, 5)
     y_ref, cache = S.forward(p, x)
