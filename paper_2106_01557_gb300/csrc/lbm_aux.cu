@@ -20,7 +20,7 @@ constexpr int AUX_NT = 256;
 
 template <class S>
 __device__ __forceinline__ double load_d(const S* buf, const Geometry& G, int p, int x, int y, double rest) {
-    const S v = buf[(long long)p * G.plane + (long long)(y + 2) * G.pitch + G.HX + x];
+    const S v = buf[(long long)p * G.plane + (long long)(y + 2) * G.pitch + G.PX + x];
     if constexpr (sizeof(S) == 2) return rest + (double)Store<S, float>::ld(v, 0.0f);
     else return (double)v;
 }

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(T::NT, 1)
             collide(k, f, g, s);
             const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
             if (interior) {
-                S* o = out + (long long)(y + 2) * G.pitch + HX + x;
+                S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     o[i * G.plane] = Store<S, C>::st(f[i], rest[i]);

@@ -39,6 +39,10 @@ struct Store<__nv_bfloat16, float> {
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 
+// clamp to [0, 1]
+__device__ __forceinline__ double clamp01(double w) { return w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w); }
+__device__ __forceinline__ float clamp01(float w) { return w < 0.f ? 0.f : (w > 1.f ? 1.f : w); }
+
 template <class C>
 __device__ __forceinline__ const KC<C>& kc(const Launch& L);
 template <>
@@ -100,8 +104,8 @@ struct NodeMacro {
     C m[9], n[9];
 };
 
-template <class C>
-__device__ __forceinline__ void node_macro(const KC<C>& k, const C f[9], const C g[9], const C rn[9],
+template <class C, class K>
+__device__ __forceinline__ void node_macro(const K& k, const C f[9], const C g[9], const C rn[9],
                                            NodeMacro<C>& s) {
     moments9(f, s.m);
     moments9(g, s.n);
@@ -125,8 +129,8 @@ __device__ __forceinline__ void node_macro(const KC<C>& k, const C f[9], const C
 }
 
 // p_BE = p_EOS + a rho^2 with Eq. 17
-template <class C>
-__device__ __forceinline__ C p_BE(const KC<C>& k, C rho, C T) {
+template <class C, class K>
+__device__ __forceinline__ C p_BE(const K& k, C rho, C T) {
     const C th = k.b4 * rho;
     const C om = C(1) - th;
     const C z = (C(1) + th * (C(1) + th * (C(1) - th))) * recip(om * om * om);
@@ -189,8 +193,8 @@ __device__ __forceinline__ void equilibria(const KC<C>& k, const NodeMacro<C>& s
 // collision populations. Rows 0, 3, 5 of m - m^eq + dt/2 F_m and row 0 of
 // n - n^eq + dt/2 q_m vanish by Eq. 14, so s_0, s_j and sigma_0 never act
 // and are not applied.
-template <class C>
-__device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const NodeMacro<C>& s) {
+template <class C, class K>
+__device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMacro<C>& s) {
     const C rho = s.rho, ux = s.uhx, uy = s.uhy;
     const C u2 = ux * ux + uy * uy;
     const C pbe = p_BE(k, rho, s.T);
@@ -249,8 +253,7 @@ __device__ __forceinline__ void collide(const KC<C>& k, C f[9], C g[9], const No
     const C z5 = n[5] - rhk * uy + k.half_dt * quy;
     const C z6 = n[6] + rhk * uy - k.half_dt * quy;
     // sigma_j(rho): tau_j linear in rho between rho_v and rho_l; sigma_q = sigma_j
-    C wl = (rho - k.rho_v) * k.inv_drho;
-    wl = wl < C(0) ? C(0) : (wl > C(1) ? C(1) : wl);
+    const C wl = clamp01((rho - k.rho_v) * k.inv_drho);
     const C sj = recip(k.tauj_v + k.dtauj * wl + C(0.5));
     const C sjwj = sj * (C(0.5) * sj - C(1));   // sigma_q omega_j with sigma_q = sigma_j
     // c^2 Y d of SM Eq. S6b
@@ -297,7 +300,7 @@ __device__ __forceinline__ void put(S* __restrict__ out, const Geometry& G, int 
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         if (r >= nr) break;
-        S* row = base + (long long)(rows[r] + 2) * G.pitch + HX;
+        S* row = base + (long long)(rows[r] + 2) * G.pitch + G.PX;
         row[x] = v;
         if (x < HX) row[x + G.nx] = v;
         if (x >= G.nx - HX) row[x - G.nx] = v;

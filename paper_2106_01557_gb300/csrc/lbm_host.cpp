@@ -267,8 +267,10 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     G.ny = c.ny;
     G.walls = c.walls;
     G.HX = hx;
-    int pitch = ((c.nx + 2 * hx + hx - 1) / hx) * hx;
-    if (pitch < bx + 2 * hx) pitch = bx + 2 * hx;
+    const int line = 128 / (int)elem_size(storage);  // elements per 128 bytes
+    G.PX = line;
+    int pitch = G.PX + (c.nx > bx ? c.nx : bx) + hx;
+    pitch = ((pitch + line - 1) / line) * line;
     G.pitch = pitch;
     G.nyp = c.ny + 4 > by + 4 ? c.ny + 4 : by + 4;
     G.plane = (long long)G.pitch * G.nyp;
@@ -374,16 +376,19 @@ static int make_maps(lbm_handle* h) {
                              : h->storage == S_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                              : h->storage == S_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    cuuint64_t dims[3] = {(cuuint64_t)G.pitch, (cuuint64_t)G.nyp, 18};
+    // map x = 0 is the first ghost column (row element PX - HX, 16-byte aligned)
+    const int x0 = G.PX - G.HX;
+    cuuint64_t dims[3] = {(cuuint64_t)(G.pitch - x0), (cuuint64_t)G.nyp, 18};
     cuuint64_t strides[2] = {(cuuint64_t)G.pitch * h->esize, (cuuint64_t)G.plane * h->esize};
     cuuint32_t estr[3] = {1, 1, 1};
     cuuint32_t boxf[3] = {(cuuint32_t)(bx + 2 * hx), (cuuint32_t)(by + 4), 9};
     cuuint32_t boxg[3] = {(cuuint32_t)(bx + 2 * hx), (cuuint32_t)(by + 2), 9};
     for (int b = 0; b < 2; ++b) {
-        CUresult r1 = enc(&h->tmf[b], dt, 3, h->buf[b], dims, strides, boxf, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        void* base = static_cast<unsigned char*>(h->buf[b]) + (size_t)x0 * h->esize;
+        CUresult r1 = enc(&h->tmf[b], dt, 3, base, dims, strides, boxf, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        CUresult r2 = enc(&h->tmg[b], dt, 3, h->buf[b], dims, strides, boxg, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CUresult r2 = enc(&h->tmg[b], dt, 3, base, dims, strides, boxg, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
@@ -860,13 +865,14 @@ int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out) {
         std::vector<CUtensorMap> maps((size_t)ncases * 4);
         for (int i = 0; i < ncases; ++i) {
             const Geometry& G = b->L[i].geo;
-            cuuint64_t dims[3] = {(cuuint64_t)G.pitch, (cuuint64_t)G.nyp, 18};
+            const int x0 = G.PX - G.HX;  // map x = 0: the first ghost column
+            cuuint64_t dims[3] = {(cuuint64_t)(G.pitch - x0), (cuuint64_t)G.nyp, 18};
             cuuint64_t strides[2] = {(cuuint64_t)G.pitch * b->esize, (cuuint64_t)G.plane * b->esize};
             cuuint32_t estr[3] = {1, 1, 1};
             cuuint32_t boxf[3] = {(cuuint32_t)(bx + 2 * G.HX), (cuuint32_t)(by + 4), 9};
             cuuint32_t boxg[3] = {(cuuint32_t)(bx + 2 * G.HX), (cuuint32_t)(by + 2), 9};
             for (int buf = 0; buf < 2; ++buf) {
-                void* base = static_cast<unsigned char*>(b->arena[buf]) + (size_t)b->off[i] * b->esize;
+                void* base = static_cast<unsigned char*>(b->arena[buf]) + ((size_t)b->off[i] + x0) * b->esize;
                 CUresult r1 = enc(&maps[(i * 2 + buf) * 2], dt, 3, base, dims, strides, boxf, estr,
                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

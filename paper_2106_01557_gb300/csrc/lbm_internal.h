@@ -42,8 +42,10 @@ struct KC {
 };
 
 struct Geometry {
-    int nx, ny, walls, HX;
-    int pitch;       // padded row length in elements (multiple of HX)
+    int nx, ny, walls, HX;  // HX: ghost columns on each side (16 bytes)
+    int PX;          // elements before column x = 0 of a row (128 bytes), so
+                     // that row stores start on a cache line
+    int pitch;       // padded row length in elements (a multiple of 128 bytes)
     int nyp;         // padded number of rows (ny + 4 at least)
     long long plane; // elements per plane
     int hot_x0, hot_len;

@@ -4,8 +4,8 @@
 //  1. One elected thread issues two 3-D TMA tile loads (all nine f planes of
 //     the tile plus a 2-row / HX-column halo; all nine g planes plus a
 //     1-row / HX-column halo) from the ghost-padded state into shared
-//     memory, completing on an mbarrier (bounded wait). Two stages: the
-//     next tile's copies are in flight while the current tile computes.
+//     memory, completing on an mbarrier (bounded wait). NS stages: the
+//     copies of the next NS - 1 tiles are in flight while one computes.
 //  2. The density of the tile and its one-node ring is formed from the
 //     pulled f populations in shared memory (pull streaming, Eq. 12a).
 //  3. Each node pulls its 18 populations, evaluates the pair force on the
@@ -35,16 +35,21 @@ __host__ __device__ constexpr int EXf(int i) { return (i == 1 || i == 5 || i == 
 __host__ __device__ constexpr int EYf(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
 
 
+// Tile shape per storage type: BX x BY nodes, HX staged halo columns (16
+// bytes), NT threads, NS staging buffers per CTA, CPS resident CTAs per SM.
+// With NS >= 2 the copies of the next NS - 1 tiles land while this one
+// computes; with NS = 1 and CPS = 2 the two CTAs of an SM cover each
+// other's waits.
 template <class S>
 struct Tile;
 template <>
-struct Tile<double> { static constexpr int BX = 32, BY = 16, HX = 2, NT = 512; };
+struct Tile<double> { static constexpr int BX = 32, BY = 16, HX = 2, NT = 512, NS = 2, CPS = 1; };
 template <>
-struct Tile<float> { static constexpr int BX = 64, BY = 16, HX = 4, NT = 512; };
+struct Tile<float> { static constexpr int BX = 64, BY = 16, HX = 4, NT = 512, NS = 2, CPS = 1; };
 template <>
-struct Tile<__half> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512; };
+struct Tile<__half> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512, NS = 2, CPS = 1; };
 template <>
-struct Tile<__nv_bfloat16> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512; };
+struct Tile<__nv_bfloat16> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512, NS = 2, CPS = 1; };
 
 template <class S, class C>
 struct Smem {
@@ -56,10 +61,13 @@ struct Smem {
     static constexpr int G_BYTES = 9 * GR * WX * (int)sizeof(S);
     static constexpr int STAGE = ((F_BYTES + 127) / 128) * 128 + ((G_BYTES + 127) / 128) * 128;
     static constexpr int G_OFF = ((F_BYTES + 127) / 128) * 128;  // within a stage
+    static constexpr int NS = Tile<S>::NS;                      // staging buffers
+    static constexpr int NR = NS == 1 ? 1 : 2;                   // density tiles
     static constexpr int RX = BX + 2, RY = BY + 2;               // density tile with ring
-    static constexpr int R_OFF = 2 * STAGE;                      // two density tiles
+    static constexpr int R_OFF = NS * STAGE;
     static constexpr int R_BYTES = (((int)sizeof(C) * RX * RY + 127) / 128) * 128;
-    static constexpr int BYTES = R_OFF + 2 * R_BYTES + 128;      // + alignment slack
+    static constexpr int BYTES = R_OFF + NR * R_BYTES + 128;     // + alignment slack
+    static_assert(NS >= 1 && NS <= 4, "one to four staging buffers");
 };
 
 // Wall ghost-row stores of a node next to a wall: the populations leaving
@@ -105,18 +113,47 @@ struct Acc {
     C mass, mx, my, ek, et, u2max, bad;
 };
 
+// Post-collision populations of node (x, y) into its own slot of the output
+// state (pull scheme), with the periodic ghost copies near the edges and the
+// wall reflections in the rows next to a wall.
 template <class S, class C>
-__global__ void __launch_bounds__(Tile<S>::NT, 1)
+__device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
+                                           const C f[9], const C g[9], C rho) {
+    const C* rest = k.rest;
+    const int HX = G.HX;
+    const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
+    if (interior) {
+        S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            o[i * G.plane] = Store<S, C>::st(f[i], rest[i]);
+            o[(9 + i) * G.plane] = Store<S, C>::st(g[i], rest[9 + i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            put<S>(out, G, i, x, y, Store<S, C>::st(f[i], rest[i]));
+            put<S>(out, G, 9 + i, x, y, Store<S, C>::st(g[i], rest[9 + i]));
+        }
+    }
+    if (G.walls && (y == 0 || y == G.ny - 1)) {
+        if (y == 0) wall_store<S, C>(out, G, k, x, y, f[4], f[7], f[8], g[4], g[7], g[8], rho);
+        else wall_store<S, C>(out, G, k, x, y, f[2], f[5], f[6], g[2], g[5], g[6], rho);
+    }
+}
+
+template <class S, class C>
+__global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     k_step(const __grid_constant__ CUtensorMap tmf, const __grid_constant__ CUtensorMap tmg,
            S* __restrict__ out, const __grid_constant__ Launch L, double* __restrict__ partials,
            double* __restrict__ stats, unsigned* __restrict__ counter, int* __restrict__ status) {
     using SM = Smem<S, C>;
     constexpr int BX = SM::BX, BY = SM::BY, HX = SM::HX, WX = SM::WX;
     constexpr int FR = SM::FR, GR = SM::GR, RX = SM::RX, RY = SM::RY;
-    constexpr int NT = Tile<S>::NT;
+    constexpr int NT = Tile<S>::NT, NS = SM::NS;
     static_assert(NT % BX == 0, "whole tile rows per thread sweep");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[SM::NS];
     __shared__ C red[NT / 32][7];
     __shared__ bool last;
     // TMA destinations start on a 128-byte boundary (the launch adds 128 bytes)
@@ -139,28 +176,28 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
     };
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int j = 0; j < NS; ++j) mbar_init(&bar[j], 1);
         fence_mbar_init();
     }
     __syncthreads();
     if (tid == 0) {
-        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-        if ((int)blockIdx.x + (int)gridDim.x < ntiles) issue(blockIdx.x + gridDim.x, 1);
+        for (int j = 0; j < NS; ++j)
+            if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) issue(blockIdx.x + j * gridDim.x, j);
     }
 
     const C* rest = k.rest;
     Acc<C> acc = {0, 0, 0, 0, 0, 0, 0};
     bool ok = true;
     int it = 0;
-    // One block barrier per tile. At the barrier after the density pass of
-    // tile `it`, every thread has finished tile it-1, so its stage is
-    // refilled with tile it+1 and the other density buffer is free.
+    // NS >= 2: one block barrier per tile. At the barrier after the density
+    // pass of tile `it`, every thread has finished tile it-1, so its stage is
+    // refilled with tile it+NS-1 and the other density buffer is free.
+    // NS = 1: a second barrier after the compute pass frees the one stage.
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int stage = it & 1;
+        const int stage = it % NS;
         bool timed_out = false;
         {
-            const uint32_t parity = (it >> 1) & 1;
+            const uint32_t parity = (uint32_t)(it / NS) & 1u;
             const uint64_t t0 = globaltimer_ns();
             while (!mbar_try_wait(&bar[stage], parity)) {
                 if (globaltimer_ns() - t0 > WAIT_NS) { timed_out = true; break; }
@@ -168,7 +205,7 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
         }
         const S* sf = reinterpret_cast<const S*>(smem + stage * SM::STAGE);
         const S* sg = reinterpret_cast<const S*>(smem + stage * SM::STAGE + SM::G_OFF);
-        C* srho = reinterpret_cast<C*>(smem + SM::R_OFF + stage * SM::R_BYTES);
+        C* srho = reinterpret_cast<C*>(smem + SM::R_OFF + (it % SM::NR) * SM::R_BYTES);
         const int tx0 = (tile % ntx) * BX, ty0 = (tile / ntx) * BY;
 
         // ---- density on tile + ring (pull sums from staged f) --------------
@@ -190,9 +227,9 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
             srho[idx] = r;
         }
         if (__syncthreads_or(timed_out)) { ok = false; break; }
-        if (tid == 0) {
-            const int ahead = tile + gridDim.x;  // tile it+1 goes into the stage tile it-1 used
-            if (it > 0 && ahead < ntiles) issue(ahead, stage ^ 1);
+        if (NS >= 2 && tid == 0) {
+            const int ahead = tile + (NS - 1) * gridDim.x;  // tile it+NS-1 goes into the stage tile it-1 used
+            if (it > 0 && ahead < ntiles) issue(ahead, (it - 1) % NS);
         }
 
         const int lx = tid % BX;
@@ -228,37 +265,22 @@ __global__ void __launch_bounds__(Tile<S>::NT, 1)
                 if (!(rho > C(0) && rho < C(1e30) && u2 < C(1e30))) acc.bad += C(1);  // also catches NaN
             }
             collide(k, f, g, s);
-
-            // ---- store at own node (pull scheme) ----------------------------
-            const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
-            if (interior) {
-                S* o = out + (long long)(y + 2) * G.pitch + HX + x;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    o[i * G.plane] = Store<S, C>::st(f[i], rest[i]);
-                    o[(9 + i) * G.plane] = Store<S, C>::st(g[i], rest[9 + i]);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    put<S>(out, G, i, x, y, Store<S, C>::st(f[i], rest[i]));
-                    put<S>(out, G, 9 + i, x, y, Store<S, C>::st(g[i], rest[9 + i]));
-                }
-            }
-            // ---- walls: a population leaving through a wall returns reversed
-            if (G.walls && (y == 0 || y == G.ny - 1)) {
-                if (y == 0) wall_store<S, C>(out, G, k, x, y, f[4], f[7], f[8], g[4], g[7], g[8], s.rho);
-                else wall_store<S, C>(out, G, k, x, y, f[2], f[5], f[6], g[2], g[5], g[6], s.rho);
-            }
+            store_node<S, C>(out, G, k, x, y, f, g, s.rho);
+        }
+        if (NS == 1) {
+            __syncthreads();  // every thread is done with the stage: refill it
+            if (tid == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, 0);
         }
     }
     if (!ok && tid == 0) {
         atomicOr(status, ST_TIMEOUT);
-        // give the copies in flight (this iteration's and the next one's) a
-        // bounded chance to land before exiting
-        for (int j = it; j <= it + 1; ++j) {
+        // give the copies in flight (this iteration's and those of the next
+        // NS - 1 tiles) a bounded chance to land before exiting
+        const int jend = it == 0 ? NS : it + NS - 1;  // tiles issued so far: 0 .. jend - 1
+        for (int j = it; j < jend; ++j) {
+            if ((int)blockIdx.x + j * (int)gridDim.x >= ntiles) break;
             const uint64_t t0 = globaltimer_ns();
-            while (!mbar_try_wait(&bar[j & 1], (j >> 1) & 1) && globaltimer_ns() - t0 < WAIT_NS) {}
+            while (!mbar_try_wait(&bar[j % NS], (uint32_t)(j / NS) & 1u) && globaltimer_ns() - t0 < WAIT_NS) {}
         }
     }
 
@@ -318,7 +340,8 @@ cudaError_t launch_t(const Launch& L, const CUtensorMap* tmf, const CUtensorMap*
                      double* partials, double* stats, unsigned* counter, int* status, cudaStream_t s) {
     using SM = Smem<S, C>;
     const int ntiles = ((L.geo.nx + SM::BX - 1) / SM::BX) * ((L.geo.ny + SM::BY - 1) / SM::BY);
-    const int grid = ntiles < L.geo.sms ? ntiles : L.geo.sms;
+    const int slots = Tile<S>::CPS * L.geo.sms;
+    const int grid = ntiles < slots ? ntiles : slots;
     k_step<S, C><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats, counter, status);
     return cudaGetLastError();
 }
@@ -336,8 +359,9 @@ void step_tile(int storage, int* bx, int* by, int* hx) {
 int step_blocks(int storage, const Geometry& g) {
     int bx, by, hx;
     step_tile(storage, &bx, &by, &hx);
+    const int cps = storage == S_F64 ? Tile<double>::CPS : (storage == S_F32 ? Tile<float>::CPS : Tile<__half>::CPS);
     const int ntiles = ((g.nx + bx - 1) / bx) * ((g.ny + by - 1) / by);
-    return ntiles < g.sms ? ntiles : g.sms;
+    return ntiles < cps * g.sms ? ntiles : cps * g.sms;
 }
 
 size_t step_smem_bytes(int storage) {
