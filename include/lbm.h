@@ -235,7 +235,10 @@ int lbm_batch_destroy(lbm_batch* b);
  * periodic padding, bias; BF16 tensor-core kernels, FP32 accumulation):
  *   h0 = lift(x); h_{b+1} = h_b + conv_b2(relu(conv_b1(relu(h_b))));
  *   y  = x + proj(relu(h_B)),
- * on normalised fields x_c = (field_c - off[c]) / scale[c]. Parameters in
+ * on normalised fields x_c = (field_c - off[c]) / scale[c]; with
+ * conserve_mass, an output layer then sets y_rho -= mean over the image of
+ * (y_rho - x_rho), so that every jump keeps each image's mass (the LB
+ * conserves it exactly on a periodic box). Parameters in
  * lbm_surrogate_set_params order: lift weight [9][C][4], lift bias [C], for
  * each block w1 [9][C][C], b1 [C], w2 [9][C][C], b2 [C], proj weight
  * [9][4][C], proj bias [4] (weight index [tap][out][in], tap = 3 (dy + 1) +
@@ -255,7 +258,7 @@ typedef struct lbm_surrogate_config {
     double norm_scale[4];
     void* stream;        /* cudaStream_t; NULL: own stream */
     int32_t device;
-    int32_t pad;
+    int32_t conserve_mass;  /* nonzero: the mass-conserving output layer */
 } lbm_surrogate_config;
 
 int lbm_surrogate_create(const lbm_surrogate_config* cfg, lbm_surrogate** out);
@@ -275,17 +278,25 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
                              int32_t W, double lr, double* loss);
 /* Rollout on a periodic FP32/FP64 case: njumps times, snapshot the state,
  * predict K steps ahead, re-initialise the populations from the predicted
- * fields (the LB continues from the surrogate state), and compare mass and
- * energy (sum rho e_k) before and after; an unphysical prediction
- * (non-finite, rho <= 0 or T <= 0), a relative change above drift_tol, or a
- * liquid area (rho above (rho_v + rho_l)/2) changing by more than drift_tol
- * relative, restores the snapshot and runs K LB steps instead.
+ * fields (the LB continues from the surrogate state), and compare before
+ * and after the jump the two quantities the model conserves, mass and total
+ * energy (lbm_conservation out[0] and out[4]; sum rho e_k is not one of
+ * them, it exchanges latent heat with the pair potential as liquid
+ * evaporates), and the position of the interface: its mean displacement
+ * D / L in lattice units, with D the number of nodes whose phase (liquid:
+ * rho above (rho_v + rho_l) / 2) the jump changed and L = (pi / 4) E the
+ * interface length before the jump from its E liquid-vapour edges between
+ * lattice neighbours. An unphysical
+ * prediction (non-finite, rho <= 0 or T <= 0), a relative mass or energy
+ * change above drift_tol, or a displacement above iface_tol restores the
+ * snapshot and runs K LB steps instead.
  * stats (may be NULL, >= 10): [0] jumps accepted, [1] fallbacks,
  * [2] ms in surrogate jumps, [3] ms in fallback LB steps, [4] largest
- * accepted mass drift, [5] largest accepted energy drift, [6..8] largest
- * mass, energy and liquid-area drift over all jumps, [9] jumps with an
- * unphysical prediction. Synchronous. */
-int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, double drift_tol, double* stats);
+ * accepted mass drift, [5] largest accepted energy drift, [6..7] largest
+ * mass and energy drift over all jumps, [8] largest interface displacement
+ * over all jumps, [9] jumps with an unphysical prediction. Synchronous. */
+int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, double drift_tol, double iface_tol,
+                          double* stats);
 int lbm_surrogate_destroy(lbm_surrogate* s);
 
 /* Largest lattice (nx * ny) lbm_conservation_noalloc accepts. */

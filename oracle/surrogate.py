@@ -17,6 +17,13 @@ and a bias. Tensors are (N, H, W, C) arrays; weights are (9, Cout, Cin) with
 tap t = 3 (dy + 1) + (dx + 1) reading input pixel (y + dy, x + dx).
 The loss is the mean of the squared error over all pixels and the 4
 channels.
+
+With conserve_mass, a fixed output layer makes the network conserve mass
+per sample: the density channel becomes y_rho - mean(y_rho - x_rho) (mean
+over the image), so sum(y_rho) = sum(x_rho), as the LB update conserves
+mass exactly on a periodic box (Eq. 6a). The layer is a linear projection
+P, symmetric and idempotent, so the gradient passes back as P applied to
+the gradient of the loss.
 """
 from __future__ import annotations
 
@@ -67,7 +74,7 @@ def init_params(channels=64, blocks=6, cin=4, seed=0, scale=1.0):
     return p
 
 
-def forward(p, x):
+def forward(p, x, conserve_mass=False):
     """Returns the output and the cache of activations needed for backward."""
     h = conv3x3(x, *p["lift"])
     cache = {"x": x, "h": [h], "z1": []}
@@ -78,6 +85,10 @@ def forward(p, x):
         h = h + z2
         cache["h"].append(h)
     y = x + conv3x3(relu(h), *p["proj"])
+    if conserve_mass:
+        y = y.copy()
+        y[..., 0] -= (y[..., 0] - x[..., 0]).mean(axis=(1, 2), keepdims=True)
+    cache["conserve_mass"] = conserve_mass
     return y, cache
 
 
@@ -89,6 +100,8 @@ def backward(p, cache, y, target):
     """Gradients of the mean-squared loss with respect to every weight and bias."""
     g = {"blocks": [None] * len(p["blocks"])}
     dy = 2.0 * (y - target) / y.size
+    if cache.get("conserve_mass"):
+        dy[..., 0] -= dy[..., 0].mean(axis=(1, 2), keepdims=True)
     hB = cache["h"][-1]
     da, dw, db = conv3x3_backward(relu(hB), p["proj"][0], dy)
     g["proj"] = (dw, db)

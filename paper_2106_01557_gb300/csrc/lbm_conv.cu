@@ -258,13 +258,19 @@ __global__ void k_bgrad(const __nv_bfloat16* __restrict__ dout, long long P, int
     if (threadIdx.x == 0) atomicAdd(&db[c], s[0]);
 }
 
-// loss = mean over P pixels and 4 channels of (out - target)^2; dout = d loss / d out
+// loss = mean over P pixels and 4 channels of (out - target)^2; dout = d loss / d out.
+// With the mass-conserving output layer (csum not null) the density gradient
+// is projected: minus its per-image mean, which equals
+// 2 (mean(x_rho) - mean(target_rho)) / (4 P); csum[n] = sum over image n of
+// (x_rho - target_rho), HW pixels per image.
 __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ target, long long P,
-                      __nv_bfloat16* __restrict__ dout, double* __restrict__ loss) {
+                      __nv_bfloat16* __restrict__ dout, double* __restrict__ loss, const double* __restrict__ csum,
+                      long long HW) {
     __shared__ double s[256];
     double acc = 0.0;
     const float scale = 2.0f / (float)(P * 4);
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const float shift = csum ? (float)(csum[p / HW] / (double)HW) : 0.f;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             float d = 0.f;
@@ -272,7 +278,7 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t
                 d = out[p * 16 + c] - target[p * 4 + c];
                 acc += (double)d * d;
             }
-            dout[p * 16 + c] = __float2bfloat16(c < 4 ? scale * d : 0.f);
+            dout[p * 16 + c] = __float2bfloat16(c < 4 ? scale * (c == 0 ? d - shift : d) : 0.f);
         }
     }
     s[threadIdx.x] = acc;
@@ -338,23 +344,71 @@ __global__ void k_unpack(const float* __restrict__ y, long long P, NormConsts nc
     }
 }
 
-// counts over a field set [4][P]: cnt[0] nodes with rho > mid, cnt[1] nodes
-// that are non-finite or have rho <= 0 or T <= 0
-__global__ void k_field_check(const double* __restrict__ f, long long P, double mid,
-                              unsigned long long* __restrict__ cnt) {
-    unsigned long long liq = 0, bad = 0;
+// Mass-conserving output layer: per image n, sums[n] = sum of
+// (y_rho - x_rho) and, with a target, sums[N + n] = sum of (x_rho - t_rho);
+// then y_rho -= sums[n] / HW. y: [P][16], x, t: [P][4]; grid y = images.
+__global__ void k_mass_stats(const float* __restrict__ y, const float* __restrict__ x, const float* __restrict__ t,
+                             int N, long long HW, double* __restrict__ sums) {
+    __shared__ double s[2][256];
+    const int n = blockIdx.y;
+    double a = 0.0, b = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < HW; q += (long long)gridDim.x * blockDim.x) {
+        const long long p = n * HW + q;
+        a += (double)y[p * 16] - (double)x[p * 4];
+        if (t) b += (double)x[p * 4] - (double)t[p * 4];
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + o];
+            s[1][threadIdx.x] += s[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&sums[n], s[0][0]);
+        if (t) atomicAdd(&sums[N + n], s[1][0]);
+    }
+}
+
+__global__ void k_mass_apply(float* __restrict__ y, long long P, long long HW, const double* __restrict__ sums) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x)
+        y[p * 16] = (float)((double)y[p * 16] - sums[p / HW] / (double)HW);
+}
+
+// counts over a field set [4][P] of one W-wide periodic image: cnt[0] nodes
+// with rho > mid (liquid), cnt[1] nodes that are non-finite or have rho <= 0
+// or T <= 0, cnt[2] liquid-vapour edges between x- and y-neighbours (the
+// interface length on the lattice's staircase), cnt[3] nodes whose phase
+// differs from that in the field set prev (if not null)
+__global__ void k_field_check(const double* __restrict__ f, const double* __restrict__ prev, long long P, int W,
+                              double mid, unsigned long long* __restrict__ cnt) {
+    unsigned long long liq = 0, bad = 0, edge = 0, flip = 0;
+    const long long H = P / W;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         const double r = f[p], u = f[P + p], v = f[2 * P + p], T = f[3 * P + p];
-        liq += r > mid;
+        const bool l = r > mid;
+        liq += l;
         bad += !(isfinite(r) && isfinite(u) && isfinite(v) && isfinite(T) && r > 0.0 && T > 0.0);
+        const long long yy = p / W, xx = p % W;
+        const long long px = yy * W + (xx + 1 == W ? 0 : xx + 1);
+        const long long py = (yy + 1 == H ? 0 : yy + 1) * W + xx;
+        edge += (l != (f[px] > mid)) + (l != (f[py] > mid));
+        if (prev) flip += l != (prev[p] > mid);
     }
     for (int o = 16; o > 0; o >>= 1) {
         liq += __shfl_down_sync(0xffffffffu, liq, o);
         bad += __shfl_down_sync(0xffffffffu, bad, o);
+        edge += __shfl_down_sync(0xffffffffu, edge, o);
+        flip += __shfl_down_sync(0xffffffffu, flip, o);
     }
     if (threadIdx.x % 32 == 0) {
         atomicAdd(&cnt[0], liq);
         atomicAdd(&cnt[1], bad);
+        atomicAdd(&cnt[2], edge);
+        atomicAdd(&cnt[3], flip);
     }
 }
 
@@ -389,12 +443,29 @@ cudaError_t wgrad_t(const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, i
 
 }  // namespace
 
-cudaError_t launch_field_check(const double* f, long long P, double mid, unsigned long long* cnt, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s);
+cudaError_t launch_field_check(const double* f, const double* prev, long long P, int W, double mid,
+                               unsigned long long* cnt, cudaStream_t s) {
+    if (W < 1 || P % W != 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     long long g = (P + 255) / 256;
     if (g > 2048) g = 2048;
-    k_field_check<<<(unsigned)g, 256, 0, s>>>(f, P, mid, cnt);
+    k_field_check<<<(unsigned)g, 256, 0, s>>>(f, prev, P, W, mid, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass_layer(float* y, const float* x, const float* t, int N, long long HW, double* sums,
+                              cudaStream_t s) {
+    if (N < 1 || HW < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * (size_t)N * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    long long gx = (HW + 255) / 256;
+    if (gx > 256) gx = 256;
+    k_mass_stats<<<dim3((unsigned)gx, (unsigned)N), 256, 0, s>>>(y, x, t, N, HW, sums);
+    const long long P = (long long)N * HW;
+    long long g = (P + 255) / 256;
+    if (g > 2048) g = 2048;
+    k_mass_apply<<<(unsigned)g, 256, 0, s>>>(y, P, HW, sums);
     return cudaGetLastError();
 }
 
@@ -429,10 +500,11 @@ cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* d
 }
 
 cudaError_t launch_mse(const float* out, const float* target, long long P, __nv_bfloat16* dout, double* loss,
-                       cudaStream_t s) {
+                       const double* csum, long long HW, cudaStream_t s) {
+    if (csum && HW < 1) return cudaErrorInvalidValue;
     long long g = (P + 255) / 256;
     if (g > 1024) g = 1024;
-    k_mse<<<(unsigned)g, 256, 0, s>>>(out, target, P, dout, loss);
+    k_mse<<<(unsigned)g, 256, 0, s>>>(out, target, P, dout, loss, csum, HW);
     return cudaGetLastError();
 }
 

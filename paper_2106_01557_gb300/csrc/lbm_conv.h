@@ -36,8 +36,16 @@ cudaError_t launch_conv_tc(int cin, int cout, const ConvArgs& a, cudaStream_t s,
 cudaError_t launch_wgrad(int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W,
                          int in_relu, float* dw, cudaStream_t s, int sms);
 cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, cudaStream_t s);
+// csum (may be null): per-image sums of (x_rho - target_rho) of the
+// mass-conserving output layer, HW pixels per image
 cudaError_t launch_mse(const float* out, const float* target, long long P, __nv_bfloat16* dout, double* loss,
-                       cudaStream_t s);
+                       const double* csum, long long HW, cudaStream_t s);
+// Mass-conserving output layer on y [N*HW][16] given the input x [N*HW][4]:
+// y_rho -= mean over each image of (y_rho - x_rho). With a target t, also
+// sums[N + n] = sum over image n of (x_rho - t_rho) for launch_mse.
+// sums: 2 N doubles of scratch.
+cudaError_t launch_mass_layer(float* y, const float* x, const float* t, int N, long long HW, double* sums,
+                              cudaStream_t s);
 cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float b1, float b2, float eps,
                         float c1, float c2, cudaStream_t s);
 cudaError_t launch_refresh(const float* w, int cin, int cout, int cin_real, int cout_real, __nv_bfloat16* w16,
@@ -47,6 +55,10 @@ cudaError_t launch_pack(const double* rho, const double* ux, const double* uy, c
 cudaError_t launch_unpack(const float* y, long long P, const NormConsts& nc, double* rho, double* ux, double* uy,
                           double* T, cudaStream_t s);
 
-cudaError_t launch_field_check(const double* f, long long P, double mid, unsigned long long* cnt, cudaStream_t s);
+// cnt[4]: liquid nodes (rho > mid), unphysical nodes, liquid-vapour edges
+// of the periodic W-wide image f [4][P], and nodes whose phase differs from
+// that in prev (a field set of the same shape, or null)
+cudaError_t launch_field_check(const double* f, const double* prev, long long P, int W, double mid,
+                               unsigned long long* cnt, cudaStream_t s);
 
 }  // namespace lbm

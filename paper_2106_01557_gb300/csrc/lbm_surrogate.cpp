@@ -65,7 +65,9 @@ struct lbm_surrogate {
     __nv_bfloat16* g1 = nullptr;
     __nv_bfloat16* g2 = nullptr;
     double* d_loss = nullptr;
-    unsigned long long* d_cnt = nullptr;  // field checks
+    unsigned long long* d_cnt = nullptr;  // field checks (4 counts)
+    double* d_msum = nullptr;        // mass-layer sums, 2 per image
+    int msum_cap = 0;
     int* d_status = nullptr;         // bit 0: a tensor-core wait ran out of time
     double* fields = nullptr;        // 4 planes of the rollout case (device)
     double* pred = nullptr;
@@ -235,6 +237,22 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
     return LBM_OK;
 }
 
+// the mass-conserving output layer on y32 (with the targets: also the sums
+// the projected loss gradient needs)
+static int mass_layer(lbm_surrogate* s, int N, long long HW, const float* t32) {
+    if (!s->cfg.conserve_mass) return LBM_OK;
+    if (N > s->msum_cap) {
+        SCK(cudaStreamSynchronize(s->stream));
+        s_free(s->d_msum);
+        s->d_msum = nullptr;
+        s->msum_cap = 0;
+        SCK(cudaMalloc(&s->d_msum, 2 * (size_t)N * sizeof(double)));
+        s->msum_cap = N;
+    }
+    SCK(launch_mass_layer(s->y32, s->x32, t32, N, HW, s->d_msum, s->stream));
+    return LBM_OK;
+}
+
 static int pack_inputs(lbm_surrogate* s, const double* in, long long P, float* x32, __nv_bfloat16* x16) {
     SCK(launch_pack(in, in + P, in + 2 * P, in + 3 * P, P, s->nc, x16, x32, s->stream));
     return LBM_OK;
@@ -291,7 +309,7 @@ int lbm_surrogate_create(const lbm_surrogate_config* cfg, lbm_surrogate** out) {
         }
     }
     ok = ok && cudaMalloc(&s->d_loss, sizeof(double)) == cudaSuccess &&
-         cudaMalloc(&s->d_cnt, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+         cudaMalloc(&s->d_cnt, 4 * sizeof(unsigned long long)) == cudaSuccess &&
          cudaMalloc(&s->d_status, sizeof(int)) == cudaSuccess && cudaMemset(s->d_status, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -376,6 +394,8 @@ int lbm_surrogate_forward(lbm_surrogate* s, const double* in, int32_t N, int32_t
     if (rc) return rc;
     rc = run_forward(s, N, H, W, false);
     if (rc) return rc;
+    rc = mass_layer(s, N, (long long)H * W, nullptr);
+    if (rc) return rc;
     SCK(launch_unpack(s->y32, P, s->nc, out, out + P, out + 2 * P, out + 3 * P, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
     return check_status(s);
@@ -392,8 +412,11 @@ static int loss_and_backward(lbm_surrogate* s, const double* in, const double* t
     SCK(launch_pack(target, target + P, target + 2 * P, target + 3 * P, P, s->nc, s->dy16, s->t32, s->stream));
     rc = run_forward(s, N, H, W, true);
     if (rc) return rc;
+    rc = mass_layer(s, N, (long long)H * W, s->t32);
+    if (rc) return rc;
     SCK(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
-    SCK(launch_mse(s->y32, s->t32, P, s->dy16, s->d_loss, s->stream));
+    SCK(launch_mse(s->y32, s->t32, P, s->dy16, s->d_loss, s->cfg.conserve_mass ? s->d_msum + N : nullptr,
+                   (long long)H * W, s->stream));
     rc = run_backward(s, N, H, W);
     if (rc) return rc;
     if (loss) {
@@ -434,8 +457,9 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
     return LBM_OK;
 }
 
-int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, double drift_tol, double* stats) {
-    if (!s || !h || njumps < 0 || !(drift_tol > 0)) return sfail(LBM_ERR_ARG, "bad argument");
+int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, double drift_tol, double iface_tol,
+                          double* stats) {
+    if (!s || !h || njumps < 0 || !(drift_tol > 0) || !(iface_tol > 0)) return sfail(LBM_ERR_ARG, "bad argument");
     double rho_v, rho_l;
     int nx, ny;
     lbm_internal_rho_bounds(h, &rho_v, &rho_l, &nx, &ny);
@@ -458,22 +482,23 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
     double acc = 0, fb = 0, t_sur = 0, t_lb = 0, max_dm = 0, max_de = 0;
     double all_dm = 0, all_de = 0, all_da = 0, n_bad = 0;
     const double mid = 0.5 * (rho_v + rho_l);
-    // device counts: cnt[0] liquid nodes, cnt[1] unphysical nodes
-    auto check = [&](const double* f, unsigned long long cnt[2]) {
-        SCK(launch_field_check(f, P, mid, s->d_cnt, s->stream));
-        SCK(cudaMemcpyAsync(cnt, s->d_cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
+    // device counts: cnt[0] liquid nodes, cnt[1] unphysical nodes, cnt[2]
+    // liquid-vapour edges, cnt[3] nodes whose phase changed from prev
+    auto check = [&](const double* f, const double* prev, unsigned long long cnt[4]) {
+        SCK(launch_field_check(f, prev, P, nx, mid, s->d_cnt, s->stream));
+        SCK(cudaMemcpyAsync(cnt, s->d_cnt, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
         SCK(cudaStreamSynchronize(s->stream));
         return LBM_OK;
     };
     cudaStream_t hs = lbm_internal_stream(h);
     for (int j = 0; j < njumps; ++j) {
         double c0[6], c1[6];
-        unsigned long long n0[2], n1[2];
+        unsigned long long n0[4], n1[4];
         rc = lbm_conservation(h, c0);
         if (rc) return rc;
         rc = lbm_moments(h, s->fields, s->fields + P, s->fields + 2 * P, s->fields + 3 * P, 1);
         if (rc) return rc;
-        rc = check(s->fields, n0);
+        rc = check(s->fields, nullptr, n0);
         if (rc) return rc;
         rc = lbm_internal_snapshot(h, s->snapshot);
         if (rc) return rc;
@@ -482,7 +507,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
         rc = lbm_surrogate_forward(s, s->fields, 1, ny, nx, s->pred);
         if (rc) return rc;
         // an unphysical prediction (non-finite, rho <= 0 or T <= 0) is a rejected jump
-        rc = check(s->pred, n1);
+        rc = check(s->pred, s->fields, n1);
         if (rc) return rc;
         const bool physical = n1[1] == 0;
         double dm = 0, de = 0, da = 0;
@@ -496,10 +521,12 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
             rc = lbm_conservation(h, c1);
             if (rc) return rc;
             dm = std::fabs(c1[0] / c0[0] - 1.0);
-            de = std::fabs(c1[3] / c0[3] - 1.0);
-            da = std::fabs((double)n1[0] - (double)n0[0]) / std::max((double)n0[0], 1.0);
+            de = std::fabs(c1[4] / c0[4] - 1.0);
+            // mean interface displacement: the area that changed phase over the interface length
+            const double len = 0.25 * 3.14159265358979323846 * (double)std::max(n0[2], 1ULL);
+            da = (double)n1[3] / len;
         }
-        const bool bad = !physical || !(dm <= drift_tol) || !(de <= drift_tol) || !(da <= drift_tol);
+        const bool bad = !physical || !(dm <= drift_tol) || !(de <= drift_tol) || !(da <= iface_tol);
         all_dm = std::max(all_dm, dm);
         all_de = std::max(all_de, de);
         all_da = std::max(all_da, da);
@@ -537,7 +564,7 @@ int lbm_surrogate_destroy(lbm_surrogate* s) {
         s_free(L.vb); s_free(L.w16); s_free(L.wflip);
     }
     release_acts(s);
-    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->d_status); s_free(s->fields); s_free(s->pred); s_free(s->snapshot);
+    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->d_status); s_free(s->d_msum); s_free(s->fields); s_free(s->pred); s_free(s->snapshot);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return LBM_OK;

@@ -102,7 +102,7 @@ SIGNATURES = {
                                  _DP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "lbm_surrogate_train_step": ([_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_double, _DP], ctypes.c_int),
-    "lbm_surrogate_rollout": ([_H, _H, ctypes.c_int32, ctypes.c_double, _DP], ctypes.c_int),
+    "lbm_surrogate_rollout": ([_H, _H, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _DP], ctypes.c_int),
     "lbm_surrogate_destroy": ([_H], ctypes.c_int),
     "lbm_conservation_noalloc": ([ctypes.POINTER(LbmConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p], ctypes.c_int),
@@ -369,7 +369,7 @@ class SurrogateConfig(ctypes.Structure):
     _fields_ = [("channels", ctypes.c_int32), ("blocks", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("conv_path", ctypes.c_int32), ("norm_off", ctypes.c_double * 4),
                 ("norm_scale", ctypes.c_double * 4), ("stream", ctypes.c_void_p),
-                ("device", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("conserve_mass", ctypes.c_int32)]
 
 
 class Surrogate:
@@ -377,18 +377,22 @@ class Surrogate:
     tensors of shape (4, N, H, W) = (rho, u_x, u_y, T); parameters are a flat
     float32 numpy array in the library's order."""
 
-    def __init__(self, norm_off, norm_scale, K=50, channels=64, blocks=6, stream=None, conv_path="tcgen05"):
+    def __init__(self, norm_off, norm_scale, K=50, channels=64, blocks=6, stream=None, conv_path="tcgen05",
+                 conserve_mass=True):
         """stream: a torch.cuda.Stream to issue the work on (None: a stream of
         the library's own). Every call first waits for torch's current
         stream, so that the tensors it reads are complete. conv_path:
         "tcgen05" (tensor-memory accumulators) or "mma" (warp-level MMAs) for
-        the 3x3 convolutions."""
+        the 3x3 convolutions. conserve_mass: the output layer that keeps each
+        image's mass."""
         self.lib = load()
         cfg = SurrogateConfig()
         cfg.channels, cfg.blocks, cfg.K = channels, blocks, K
         if conv_path not in ("tcgen05", "mma"):
             raise ValueError("conv_path must be 'tcgen05' or 'mma'")
         cfg.conv_path = 0 if conv_path == "tcgen05" else 1
+        cfg.conserve_mass = 1 if conserve_mass else 0
+        self.conserve_mass = bool(conserve_mass)
         for i in range(4):
             cfg.norm_off[i] = float(norm_off[i])
             cfg.norm_scale[i] = float(norm_scale[i])
@@ -457,15 +461,19 @@ class Surrogate:
                                                  ctypes.byref(loss)))
         return loss.value
 
-    def rollout(self, lattice, njumps, drift_tol=1e-3):
+    def rollout(self, lattice, njumps, drift_tol=1e-3, iface_tol=0.5):
+        """drift_tol: largest relative change of mass and of total energy per
+        jump; iface_tol: largest mean interface displacement per jump, in
+        lattice units."""
         import torch
         torch.cuda.current_stream().synchronize()
         stats = np.zeros(10)
-        _check(self.lib.lbm_surrogate_rollout(self.h, lattice.h, int(njumps), float(drift_tol), _host_ptr(stats)))
+        _check(self.lib.lbm_surrogate_rollout(self.h, lattice.h, int(njumps), float(drift_tol), float(iface_tol),
+                                              _host_ptr(stats)))
         return {"accepted": int(stats[0]), "fallbacks": int(stats[1]), "ms_surrogate": stats[2],
                 "ms_fallback_lb": stats[3], "max_mass_drift": stats[4], "max_energy_drift": stats[5],
-                "max_mass_drift_all": stats[6], "max_energy_drift_all": stats[7], "max_area_drift_all": stats[8],
-                "unphysical": int(stats[9])}
+                "max_mass_drift_all": stats[6], "max_energy_drift_all": stats[7],
+                "max_iface_displacement_all": stats[8], "unphysical": int(stats[9])}
 
 
 def surrogate_params_from_oracle_layout(p):

@@ -12,14 +12,15 @@ pytestmark = pytest.mark.gpu
 PATHS = ["tcgen05", "mma"]
 
 
-def _make(channels=64, blocks=2, seed=0, K=10, conv_path="tcgen05"):
+def _make(channels=64, blocks=2, seed=0, K=10, conv_path="tcgen05", conserve_mass=False):
     from oracle import surrogate as S
     from paper_2106_01557_gb300 import lbm
     p = S.init_params(channels=channels, blocks=blocks, seed=seed)
     # a projection large enough that the network output differs from its input
     rng = np.random.default_rng(seed + 100)
     p["proj"] = (rng.normal(0, 0.05, p["proj"][0].shape), rng.normal(0, 0.05, p["proj"][1].shape))
-    s = lbm.Surrogate([0, 0, 0, 0], [1, 1, 1, 1], K=K, channels=channels, blocks=blocks, conv_path=conv_path)
+    s = lbm.Surrogate([0, 0, 0, 0], [1, 1, 1, 1], K=K, channels=channels, blocks=blocks, conv_path=conv_path,
+                      conserve_mass=conserve_mass)
     s.set_params(lbm.surrogate_params_from_oracle_layout(p))
     return S, p, s
 
@@ -48,13 +49,14 @@ def _close(d, d_ref):
 SHAPES = [(2, 8, 32), (3, 20, 272)]
 
 
+@pytest.mark.parametrize("conserve_mass", [False, True])
 @pytest.mark.parametrize("conv_path", PATHS)
 @pytest.mark.parametrize("shape", SHAPES)
-def test_forward_matches_oracle(gpu_lib, conv_path, shape):
+def test_forward_matches_oracle(gpu_lib, conv_path, shape, conserve_mass):
     import torch
-    S, p, s = _make(conv_path=conv_path)
+    S, p, s = _make(conv_path=conv_path, conserve_mass=conserve_mass)
     x = _fields(*shape, 1)
-    y_ref, _ = S.forward(p, x)
+    y_ref, _ = S.forward(p, x, conserve_mass)
     out = torch.empty((4,) + shape, dtype=torch.float64, device="cuda")
     s.forward(_to_dev(x), out)
     y = np.moveaxis(out.cpu().numpy(), 0, -1)
@@ -82,12 +84,30 @@ def test_forward_full_size_sampled_windows(gpu_lib):
         _close(got - crop[:, R:R + h, R:R + h], ref - crop[:, R:R + h, R:R + h])
 
 
+def test_mass_layer_keeps_each_images_mass(gpu_lib):
+    # the density sums of input and output agree per image to FP32 rounding
+    # of the normalised fields; without the layer the network moves them
+    import torch
+    x = _fields(3, 20, 272, 8)
+    sums = {}
+    for cm in (False, True):
+        S, p, s = _make(seed=9, conserve_mass=cm)
+        out = torch.empty((4, 3, 20, 272), dtype=torch.float64, device="cuda")
+        s.forward(_to_dev(x), out)
+        sums[cm] = out[0].sum(dim=(1, 2)).cpu().numpy()
+    ref = x[..., 0].sum(axis=(1, 2))
+    scale = np.abs(x[..., 0]).sum(axis=(1, 2))
+    assert np.abs(sums[True] - ref).max() < 1e-6 * scale.max()
+    assert np.abs(sums[False] - ref).min() > 1e-3 * scale.min()
+
+
+@pytest.mark.parametrize("conserve_mass", [False, True])
 @pytest.mark.parametrize("conv_path", PATHS)
-def test_gradients_match_oracle(gpu_lib, conv_path):
-    S, p, s = _make(seed=3, conv_path=conv_path)
+def test_gradients_match_oracle(gpu_lib, conv_path, conserve_mass):
+    S, p, s = _make(seed=3, conv_path=conv_path, conserve_mass=conserve_mass)
     x = _fields(2, 8, 32, 4)
     t = x + 0.3 * _fields(2, 8, 32, 5)
-    y_ref, cache = S.forward(p, x)
+    y_ref, cache = S.forward(p, x, conserve_mass)
     g_ref = S.flatten(S.backward(p, cache, y_ref, t))
     loss, g = s.loss_grad(_to_dev(x), _to_dev(t))
     assert loss == pytest.approx(S.loss(y_ref, t), rel=2e-2)
@@ -159,5 +179,45 @@ def test_trained_network_beats_no_change_on_held_out_runs(gpu_lib):
     sur.set_params(S.init_params(seed=1))
     losses, hold, _ = S.train(sur, snaps, iters=250, batch=8, lr=1e-3, seed=2, holdout_runs=2)
     pers = S.persistence_loss(sur, snaps, holdout_runs=2)
-    assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:20])
+    # (the mass-conserving layer already removes the untrained network's
+    # mean density error, so the loss starts lower than without it)
+    assert np.mean(losses[-20:]) < 0.33 * np.mean(losses[:20])
     assert hold < pers, (hold, pers)
+
+
+def test_rollout_rejects_a_moved_interface(gpu_lib):
+    # a network that moves the density field one cell in +x: mass is kept
+    # (a periodic shift, and the mass layer), the total energy barely changes
+    # (uniform T, u = 0), so only the interface check can reject the jump;
+    # a 1-cell shift of a round droplet moves its interface by 2/pi cells on
+    # average, above the 0.5-cell threshold
+    from oracle import Oracle, thermo
+    from oracle import surrogate as S
+    from paper_2106_01557_gb300 import inputs, lbm
+    nx = ny = 64
+    pp = Oracle(thermo.Config(nx=nx, ny=ny)).p
+    rho = inputs.droplets(nx, ny, pp.rho_v, pp.rho_l, [(32, 32)], [14], 4.0)
+    z = np.zeros_like(rho)
+    off = [pp.rho_v, 0.0, 0.0, pp.T0]
+    scale = [pp.rho_l - pp.rho_v, 0.01 * pp.c, 0.01 * pp.c, 0.05 * pp.Tc]
+    p = S.init_params(channels=64, blocks=2, seed=0)
+    zero = lambda a: np.zeros_like(a)
+    wl = zero(p["lift"][0])
+    wl[4, 0, 0] = 1.0                       # h channel 0 = normalised rho
+    p["lift"] = (wl, zero(p["lift"][1]))
+    p["blocks"] = [((zero(w1), zero(b1)), (zero(w2), zero(b2))) for (w1, b1), (w2, b2) in p["blocks"]]
+    wp = zero(p["proj"][0])
+    wp[3, 0, 0], wp[4, 0, 0] = 1.0, -1.0    # y_rho = x_rho + rho(x - 1) - rho(x)
+    p["proj"] = (wp, zero(p["proj"][1]))
+    s = lbm.Surrogate(off, scale, K=10, blocks=2)
+    s.set_params(lbm.surrogate_params_from_oracle_layout(p))
+    lat = lbm.Lattice.create(nx, ny, precision="f32")
+    lat.set_fields(rho, z, z, np.full_like(rho, pp.T0))
+    st = s.rollout(lat, 2, drift_tol=1e-3, iface_tol=0.5)
+    assert st["fallbacks"] == 2 and st["accepted"] == 0 and st["unphysical"] == 0
+    assert st["max_mass_drift_all"] < 1e-5
+    assert 0.5 < st["max_iface_displacement_all"] < 0.9
+    # the same jump passes a looser interface threshold
+    lat.set_fields(rho, z, z, np.full_like(rho, pp.T0))
+    st = s.rollout(lat, 1, drift_tol=1e-2, iface_tol=1.0)
+    assert st["accepted"] == 1
