@@ -278,8 +278,9 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
                              int32_t W, double lr, double* loss);
 /* Rollout on a periodic FP32/FP64 case: njumps times, snapshot the state,
  * predict K steps ahead, re-initialise the populations from the predicted
- * fields (the LB continues from the surrogate state), and compare before
- * and after the jump the two quantities the model conserves, mass and total
+ * fields, and let the LB run verify_steps steps from that surrogate state
+ * (the LB as judge: a state it cannot advance counts as a rejected jump);
+ * then compare before and after the two quantities the model conserves, mass and total
  * energy (lbm_conservation out[0] and out[4]; sum rho e_k is not one of
  * them, it exchanges latent heat with the pair potential as liquid
  * evaporates), and the position of the interface: its mean displacement
@@ -289,14 +290,18 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
  * lattice neighbours. An unphysical
  * prediction (non-finite, rho <= 0 or T <= 0), a relative mass or energy
  * change above drift_tol, or a displacement above iface_tol restores the
- * snapshot and runs K LB steps instead.
- * stats (may be NULL, >= 10): [0] jumps accepted, [1] fallbacks,
- * [2] ms in surrogate jumps, [3] ms in fallback LB steps, [4] largest
- * accepted mass drift, [5] largest accepted energy drift, [6..7] largest
- * mass and energy drift over all jumps, [8] largest interface displacement
- * over all jumps, [9] jumps with an unphysical prediction. Synchronous. */
-int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, double drift_tol, double iface_tol,
-                          double* stats);
+ * snapshot and runs K + verify_steps LB steps instead. Every jump thus
+ * advances the lattice by K + verify_steps steps. LBM_ERR_DIVERGED is
+ * returned only if those fallback LB steps diverge.
+ * stats (may be NULL, >= 11): [0] jumps accepted, [1] fallbacks,
+ * [2] ms in surrogate jumps (prediction and verification), [3] ms in
+ * fallback LB steps, [4] largest accepted mass drift, [5] largest accepted
+ * energy drift, [6..7] largest mass and energy drift over all jumps, [8]
+ * largest interface displacement over all jumps, [9] jumps with an
+ * unphysical prediction, [10] jumps whose verification steps diverged.
+ * Synchronous. */
+int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32_t verify_steps, double drift_tol,
+                          double iface_tol, double* stats);
 int lbm_surrogate_destroy(lbm_surrogate* s);
 
 /* Largest lattice (nx * ny) lbm_conservation_noalloc accepts. */

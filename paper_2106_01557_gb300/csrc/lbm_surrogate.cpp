@@ -457,9 +457,10 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
     return LBM_OK;
 }
 
-int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, double drift_tol, double iface_tol,
-                          double* stats) {
-    if (!s || !h || njumps < 0 || !(drift_tol > 0) || !(iface_tol > 0)) return sfail(LBM_ERR_ARG, "bad argument");
+int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32_t verify_steps, double drift_tol,
+                          double iface_tol, double* stats) {
+    if (!s || !h || njumps < 0 || verify_steps < 0 || !(drift_tol > 0) || !(iface_tol > 0))
+        return sfail(LBM_ERR_ARG, "bad argument");
     double rho_v, rho_l;
     int nx, ny;
     lbm_internal_rho_bounds(h, &rho_v, &rho_l, &nx, &ny);
@@ -480,7 +481,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
         s->snapshot_bytes = sb;
     }
     double acc = 0, fb = 0, t_sur = 0, t_lb = 0, max_dm = 0, max_de = 0;
-    double all_dm = 0, all_de = 0, all_da = 0, n_bad = 0;
+    double all_dm = 0, all_de = 0, all_da = 0, n_bad = 0, n_div = 0;
     const double mid = 0.5 * (rho_v + rho_l);
     // device counts: cnt[0] liquid nodes, cnt[1] unphysical nodes, cnt[2]
     // liquid-vapour edges, cnt[3] nodes whose phase changed from prev
@@ -511,13 +512,24 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
         if (rc) return rc;
         const bool physical = n1[1] == 0;
         double dm = 0, de = 0, da = 0;
+        bool diverged = false;
         if (physical) {
             rc = lbm_set_fields(h, s->pred, s->pred + P, s->pred + 2 * P, s->pred + 3 * P, 1);
             if (rc) return rc;
+            // the LB re-runs from the surrogate state: a state it cannot
+            // advance (non-finite or non-positive density) is a rejected jump
+            if (verify_steps > 0) {
+                rc = lbm_step(h, verify_steps);
+                if (rc) return rc;
+                rc = lbm_synchronize(h);
+                if (rc == LBM_ERR_DIVERGED) diverged = true;
+                else if (rc) return rc;
+            }
         }
         auto t1 = std::chrono::steady_clock::now();
         t_sur += std::chrono::duration<double, std::milli>(t1 - t0).count();
-        if (physical) {
+        n_div += diverged ? 1.0 : 0.0;
+        if (physical && !diverged) {
             rc = lbm_conservation(h, c1);
             if (rc) return rc;
             dm = std::fabs(c1[0] / c0[0] - 1.0);
@@ -526,7 +538,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
             const double len = 0.25 * 3.14159265358979323846 * (double)std::max(n0[2], 1ULL);
             da = (double)n1[3] / len;
         }
-        const bool bad = !physical || !(dm <= drift_tol) || !(de <= drift_tol) || !(da <= iface_tol);
+        const bool bad = !physical || diverged || !(dm <= drift_tol) || !(de <= drift_tol) || !(da <= iface_tol);
         all_dm = std::max(all_dm, dm);
         all_de = std::max(all_de, de);
         all_da = std::max(all_da, da);
@@ -537,7 +549,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
                 if (rc) return rc;
             }
             auto t2 = std::chrono::steady_clock::now();
-            rc = lbm_step(h, s->cfg.K);
+            rc = lbm_step(h, s->cfg.K + verify_steps);
             if (rc) return rc;
             rc = lbm_synchronize(h);
             if (rc) return rc;
@@ -552,6 +564,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, doubl
     if (stats) {
         stats[0] = acc; stats[1] = fb; stats[2] = t_sur; stats[3] = t_lb; stats[4] = max_dm; stats[5] = max_de;
         stats[6] = all_dm; stats[7] = all_de; stats[8] = all_da; stats[9] = n_bad;
+        stats[10] = n_div;
     }
     return LBM_OK;
 }

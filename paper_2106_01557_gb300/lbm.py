@@ -102,7 +102,8 @@ SIGNATURES = {
                                  _DP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "lbm_surrogate_train_step": ([_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_double, _DP], ctypes.c_int),
-    "lbm_surrogate_rollout": ([_H, _H, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _DP], ctypes.c_int),
+    "lbm_surrogate_rollout": ([_H, _H, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _DP],
+                              ctypes.c_int),
     "lbm_surrogate_destroy": ([_H], ctypes.c_int),
     "lbm_conservation_noalloc": ([ctypes.POINTER(LbmConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p], ctypes.c_int),
@@ -461,19 +462,25 @@ class Surrogate:
                                                  ctypes.byref(loss)))
         return loss.value
 
-    def rollout(self, lattice, njumps, drift_tol=1e-3, iface_tol=0.5):
+    def rollout(self, lattice, njumps, drift_tol=1e-3, iface_tol=0.5, verify_steps=None):
         """drift_tol: largest relative change of mass and of total energy per
         jump; iface_tol: largest mean interface displacement per jump, in
-        lattice units."""
+        lattice units; verify_steps: LB steps run from each surrogate state
+        before it is judged (default K / 10). Every jump advances the lattice
+        by K + verify_steps steps."""
         import torch
         torch.cuda.current_stream().synchronize()
-        stats = np.zeros(10)
-        _check(self.lib.lbm_surrogate_rollout(self.h, lattice.h, int(njumps), float(drift_tol), float(iface_tol),
-                                              _host_ptr(stats)))
+        if verify_steps is None:
+            verify_steps = max(1, self.K // 10)
+        self.verify_steps = int(verify_steps)
+        stats = np.zeros(11)
+        _check(self.lib.lbm_surrogate_rollout(self.h, lattice.h, int(njumps), int(verify_steps), float(drift_tol),
+                                              float(iface_tol), _host_ptr(stats)))
         return {"accepted": int(stats[0]), "fallbacks": int(stats[1]), "ms_surrogate": stats[2],
                 "ms_fallback_lb": stats[3], "max_mass_drift": stats[4], "max_energy_drift": stats[5],
                 "max_mass_drift_all": stats[6], "max_energy_drift_all": stats[7],
-                "max_iface_displacement_all": stats[8], "unphysical": int(stats[9])}
+                "max_iface_displacement_all": stats[8], "unphysical": int(stats[9]),
+                "verify_diverged": int(stats[10]), "verify_steps": int(verify_steps)}
 
 
 def surrogate_params_from_oracle_layout(p):

@@ -155,14 +155,15 @@ def test_rollout_falls_back_and_accepts(gpu_lib):
     s.set_params(lbm.surrogate_params_from_oracle_layout(p))
     lat = lbm.Lattice.create(nx, ny, precision="f32")
     lat.set_fields(rho, z, z, np.full_like(rho, pp.T0))
-    st = s.rollout(lat, 3, drift_tol=1e-3)
+    st = s.rollout(lat, 3, drift_tol=1e-3, verify_steps=2)
     assert st["fallbacks"] == 3 and st["accepted"] == 0
-    assert lat.steps == 30
+    assert lat.steps == 36  # every jump advances K + verify_steps
     # a network whose projection is zero is the identity: every jump is accepted
     p["proj"] = (0 * p["proj"][0], 0 * p["proj"][1])
     s.set_params(lbm.surrogate_params_from_oracle_layout(p))
-    st = s.rollout(lat, 3, drift_tol=1e-3)
-    assert st["accepted"] == 3 and st["fallbacks"] == 0
+    st = s.rollout(lat, 3, drift_tol=1e-3, verify_steps=2)
+    # an accepted jump runs only its verification steps on the lattice
+    assert st["accepted"] == 3 and st["fallbacks"] == 0 and lat.steps == 36 + 3 * 2
     assert st["max_mass_drift"] < 1e-6
 
 
