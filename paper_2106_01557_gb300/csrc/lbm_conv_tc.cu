@@ -1,22 +1,32 @@
 // 3x3 periodic convolution of the surrogate on the 5th-generation tensor
 // cores: tcgen05.mma (kind::f16: BF16 operands in shared memory, FP32
-// accumulators in tensor memory), issued by one thread, completion tracked by
-// tcgen05.commit on an mbarrier (every wait bounded in time).
+// accumulators in tensor memory), completion tracked by tcgen05.commit on an
+// mbarrier (every wait bounded in time).
 //
 // Work: the output is cut into rows of TC_TW = 128 pixels (one MMA M); the
 // rows of all (image, 128-pixel strip) columns are dealt out to the CTAs in
-// contiguous runs, so a CTA walks down a strip and loads each input row once
-// (a ring of 4 halo'd input rows in shared memory: 3 in use, 1 filling).
-// Two accumulators in tensor memory let the MMAs of row t + 1 run while the
-// epilogue of row t reads row t out with tcgen05.ld.
+// contiguous runs, so a CTA walks down a strip and loads each input row once,
+// into a ring of TC_NSLOT halo'd input rows in shared memory filled by
+// cp.async copies issued TC_NSLOT - 4 rows ahead of their first use (ReLU,
+// where the layer wants it, is applied in place by the thread that copied
+// the vector).
+//
+// Roles: warps 0-7 copy, apply ReLU and run the epilogue; warp 8 only issues
+// the MMAs (one elected lane), so the next row's MMAs never wait for an
+// epilogue and an epilogue never waits for the issue. Two accumulators in
+// tensor memory let the MMAs of row t + 1 run while the epilogue of row t
+// reads row t out with tcgen05.ld (warp w reads lanes 32 (w % 4) .. + 31 =
+// pixels, half of the columns each), adds the bias and stages FP32 values in
+// a shared tile (16-byte chunks XOR-swizzled by pixel, no bank conflicts);
+// the tile then leaves in coalesced 16-byte stores, where the mask and the
+// residual (loaded one row ahead) are applied.
 //
 // Shared-memory operand layouts (K-major, no swizzle; a core matrix is 8
 // rows of 16 bytes):
 //   input row slot [CIN/8 channel groups][TC_TW + 2 pixels, stride 16 B]
-//     with the channel-group stride GS = (TC_TW + 3) * 16 B (an odd number
-//     of 16-byte units, so the staging stores spread over the banks). An
-//     8-pixel run of one group is one core matrix: the window of tap dx is
-//     the same operand with its start moved by (1 + dx) * 16 B.
+//     with the channel-group stride GS = (TC_TW + 3) * 16 B. An 8-pixel run
+//     of one group is one core matrix: the window of tap dx is the same
+//     operand with its start moved by (1 + dx) * 16 B.
 //     Descriptor: LBO (next channel group, K) = GS, SBO (next 8 pixels, M) = 128.
 //   weights [9 taps][CIN/8][COUT][8 channels]: LBO = COUT * 16, SBO = 128.
 // One output row = 9 taps x CIN/16 MMAs of M = 128, N = COUT, K = 16.
@@ -30,9 +40,10 @@
 namespace lbm {
 namespace {
 
-constexpr int TC_TW = 128;       // pixels per output row segment (MMA M)
-constexpr int TC_THREADS = 256;  // 8 warps; warp w reads TMEM lanes 32 (w % 4) .. + 31
-constexpr int TC_NSLOT = 4;      // input-row ring
+constexpr int TC_TW = 128;          // pixels per output row segment (MMA M)
+constexpr int TC_EPI_THREADS = 256; // warps 0-7: copies and epilogue
+constexpr int TC_THREADS = 288;     // + warp 8: MMA issue
+constexpr int TC_NSLOT = 7;         // input-row ring: 3 rows in use, the rest in flight
 
 template <int CIN, int COUT>
 struct TcCfg {
@@ -41,14 +52,20 @@ struct TcCfg {
     static constexpr int GS = (TC_TW + 3) * 16;         // bytes between channel groups
     static constexpr int SLOT_BYTES = KG * GS;
     static constexpr int W_BYTES = 9 * KG * COUT * 16;
-    static constexpr int BYTES = TC_NSLOT * SLOT_BYTES + W_BYTES + 128;  // + alignment slack
+    static constexpr int OUT_BYTES = TC_TW * COUT * 4;  // FP32 staging tile of one output row
+    static constexpr int BYTES = TC_NSLOT * SLOT_BYTES + W_BYTES + OUT_BYTES + 128;  // + alignment slack
     static constexpr int ROW_VECS = KG * PIX;           // 16-byte vectors per halo'd row
-    static constexpr int VPT = (ROW_VECS + TC_THREADS - 1) / TC_THREADS;
+    static constexpr int VPT = (ROW_VECS + TC_EPI_THREADS - 1) / TC_EPI_THREADS;
     static constexpr int TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;  // two accumulators, power of two
-    static constexpr int EPI_WARPS = COUT >= 32 ? 8 : 4;
-    static constexpr int EPI_COLS = COUT >= 32 ? COUT / 2 : COUT;    // accumulator columns per epilogue warp
-    static constexpr int EPI_CH = EPI_COLS / 16;                      // 16-column chunks per epilogue thread
+    static constexpr int EPI_COLS = COUT / 2;           // accumulator columns per epilogue warp
+    static constexpr int NC = EPI_COLS < 16 ? EPI_COLS : 16;        // columns per tcgen05.ld
+    static constexpr int EPI_CH = EPI_COLS / NC;        // tcgen05.ld per thread and row
+    static constexpr int CPP = COUT / 4;                // 16-byte FP32 chunks per pixel in the tile
+    static constexpr int SWZ = (CPP < 8 ? CPP : 8) - 1; // chunk swizzle mask
+    static constexpr int O16 = TC_TW * COUT / 8 / TC_EPI_THREADS;  // BF16 output chunks per thread
+    static constexpr int O32 = TC_TW * COUT / 4 / TC_EPI_THREADS;  // FP32 output chunks per thread
     static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "tcgen05 f16 shape");
+    static_assert(TC_TW * COUT / 8 >= TC_EPI_THREADS && (NC == 8 || NC == 16), "tile split");
     static_assert(TMEM_COLS <= 512, "tensor memory");
     static_assert(BYTES <= 227 * 1024, "shared memory");
 };
@@ -73,30 +90,31 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// 16 consecutive FP32 columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+// N consecutive FP32 columns (N = 8 or 16) of this thread's tensor-memory lane
+template <int N>
+__device__ __forceinline__ void tc_ld(uint32_t taddr, float* v) {
     uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+    if constexpr (N == 16) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+    }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < N; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// all threads: make this thread's shared-memory stores visible to the tensor
-// cores, then a block barrier that also orders tensor-core work around it
-__device__ __forceinline__ void tc_sync_stores() {
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-}
+// barrier of the 256 epilogue threads only (the issue warp does not wait)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // bounded wait on an mbarrier phase; true when it completed in time
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
@@ -105,6 +123,13 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
         if (globaltimer_ns() - t0 > WAIT_NS) return false;
     return true;
 }
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ uint4 relu8(uint4 v) {
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
@@ -124,11 +149,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_base;
-    __shared__ float s_bias[COUT];
+    __shared__ __align__(16) float s_bias[COUT];
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     unsigned char* s_in = smem;
     unsigned char* s_w = smem + TC_NSLOT * Cf::SLOT_BYTES;
+    unsigned char* s_out = s_w + Cf::W_BYTES;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const bool is_epi = tid < TC_EPI_THREADS;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -148,7 +175,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)tap * COUT + co) * CIN + kg * 8);
         *reinterpret_cast<uint4*>(s_w + ((tap * Cf::KG + kg) * COUT + co) * 16) = v;
     }
-    tc_sync_stores();
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     const uint32_t tmem = tmem_base;
     // instruction descriptor: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9,
     // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22),
@@ -156,6 +186,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) |
                            ((uint32_t)(TC_TW >> 4) << 24);
     const uint32_t s_in_addr = smem_u32(s_in), s_w_addr = smem_u32(s_w);
+    // descriptors of the weights and of ring slot 0; an operand inside them is
+    // the same descriptor with its start moved by a constant (the 14-bit
+    // start field stays below 2^14 for any shared-memory address)
+    const uint64_t b_desc0 = sdesc(s_w_addr, COUT * 16, 128);
+    const uint64_t a_desc0 = sdesc(s_in_addr, Cf::GS, 128);
     const int tiles_x = (W + TC_TW - 1) / TC_TW;
     const long long rows_total = (long long)N * tiles_x * H;
     const long long r_begin = rows_total * blockIdx.x / gridDim.x;
@@ -164,164 +199,220 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t pending = 0;  // bit b: a commit to bar[b] not yet waited for
     bool ok = true;
 
-    // epilogue geometry of this thread: pixel = TMEM lane, a range of columns
-    const bool epi = warp < Cf::EPI_WARPS;
+    // epilogue geometry of this thread: pixel = TMEM lane, a half of the columns
     const int pix = 32 * (warp % 4) + lane;
     const int col0 = (warp / 4) * Cf::EPI_COLS;
     const uint32_t t_lane = tmem + ((uint32_t)(32 * (warp % 4)) << 16);
+    float* tile = reinterpret_cast<float*>(s_out);
 
     for (long long r = r_begin; r < r_end && ok;) {
         const int y0 = (int)(r % H);
         const long long strip = r / H;
         const int x0 = (int)(strip % tiles_x) * TC_TW, n = (int)(strip / tiles_x);
         const int L = (int)((long long)(H - y0) < r_end - r ? (long long)(H - y0) : r_end - r);
+        const int nvalid = W - x0 < TC_TW ? W - x0 : TC_TW;  // output pixels of this strip
         r += L;
         const __nv_bfloat16* img = in + (size_t)n * H * W * CIN;
-        uint4 rv[Cf::VPT];
-        // halo'd input row li of this run (input row y0 - 1 + li, periodic)
-        auto load_row = [&](int li) {
-            const int gy = ((y0 - 1 + li) % H + H) % H;
-            const __nv_bfloat16* row = img + (size_t)gy * W * CIN;
+        // this thread's vectors of a halo'd row: global element offset within
+        // an input row (periodic in x) and byte offset within a slot, fixed
+        // for the run
+        int src_off[Cf::VPT], dst_off[Cf::VPT];
 #pragma unroll
-            for (int i = 0; i < Cf::VPT; ++i) {
-                const int e = tid + i * TC_THREADS;
-                if (e < Cf::ROW_VECS) {
-                    const int kg = e % Cf::KG, px = e / Cf::KG;
-                    const int gx = ((x0 - 1 + px) % W + W) % W;
-                    rv[i] = *reinterpret_cast<const uint4*>(row + (size_t)gx * CIN + kg * 8);
-                }
+        for (int i = 0; i < Cf::VPT; ++i) {
+            const int e = tid + i * TC_EPI_THREADS;
+            const int kg = e % Cf::KG, px = e / Cf::KG;
+            int gx = x0 - 1 + px;
+            gx = gx < 0 ? gx + W : gx;
+            gx = gx >= W ? gx % W : gx;
+            src_off[i] = gx * CIN + kg * 8;
+            dst_off[i] = kg * Cf::GS + px * 16;
+        }
+        // halo'd input row li of this run (input row y0 - 1 + li, periodic)
+        // into ring slot li % TC_NSLOT; one commit group per row, empty for
+        // rows the run does not need, so that group counts stay uniform
+        auto copy_row = [&](int li) {
+            if (li <= L + 1) {
+                int gy = y0 - 1 + li;
+                gy = gy < 0 ? gy + H : (gy >= H ? gy - H : gy);
+                const __nv_bfloat16* row = img + (size_t)gy * W * CIN;
+                unsigned char* slot = s_in + (li % TC_NSLOT) * Cf::SLOT_BYTES;
+#pragma unroll
+                for (int i = 0; i < Cf::VPT; ++i)
+                    if (tid + i * TC_EPI_THREADS < Cf::ROW_VECS) cp_async16(slot + dst_off[i], row + src_off[i]);
             }
+            cp_async_commit();
         };
-        auto store_row = [&](int li) {
+        // ReLU in place on the vectors this thread copied (after they landed)
+        auto relu_row = [&](int li) {
+            if (!in_relu || li > L + 1) return;
             unsigned char* slot = s_in + (li % TC_NSLOT) * Cf::SLOT_BYTES;
 #pragma unroll
             for (int i = 0; i < Cf::VPT; ++i) {
-                const int e = tid + i * TC_THREADS;
-                if (e < Cf::ROW_VECS) {
-                    const int kg = e % Cf::KG, px = e / Cf::KG;
-                    *reinterpret_cast<uint4*>(slot + kg * Cf::GS + px * 16) = in_relu ? relu8(rv[i]) : rv[i];
+                if (tid + i * TC_EPI_THREADS < Cf::ROW_VECS) {
+                    uint4* v = reinterpret_cast<uint4*>(slot + dst_off[i]);
+                    *v = relu8(*v);
                 }
             }
         };
         // MMAs of output row t (input rows li = t, t + 1, t + 2) into accumulator t & 1
         auto issue = [&](int t) {
-            if (tid == 0) {
-                const uint32_t d = tmem + (uint32_t)((t & 1) * COUT);
-                uint32_t accum = 0;
-#pragma unroll 1
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-                    const uint32_t a_tap =
-                        s_in_addr + (uint32_t)(((t + dy + 1) % TC_NSLOT) * Cf::SLOT_BYTES + (1 + dx) * 16);
-                    const uint32_t b_tap = s_w_addr + (uint32_t)(tap * Cf::KG * COUT * 16);
+            const uint32_t d = tmem + (uint32_t)((t & 1) * COUT);
+            uint64_t a_row[3];
 #pragma unroll
-                    for (int kc = 0; kc < CIN / 16; ++kc) {
-                        const uint64_t ad = sdesc(a_tap + (uint32_t)(2 * kc * Cf::GS), Cf::GS, 128);
-                        const uint64_t bd = sdesc(b_tap + (uint32_t)(2 * kc * COUT * 16), COUT * 16, 128);
-                        tc_mma(d, ad, bd, idesc, accum);
-                        accum = 1;
-                    }
+            for (int q = 0; q < 3; ++q) a_row[q] = a_desc0 + (uint64_t)((((t + q) % TC_NSLOT) * Cf::SLOT_BYTES) >> 4);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+                for (int kc = 0; kc < CIN / 16; ++kc) {
+                    const uint64_t ad = a_row[dy + 1] + (uint64_t)(((1 + dx) * 16 + 2 * kc * Cf::GS) >> 4);
+                    const uint64_t bd = b_desc0 + (uint64_t)(((tap * Cf::KG + 2 * kc) * COUT * 16) >> 4);
+                    tc_mma(d, ad, bd, idesc, (tap | kc) ? 1u : 0u);
                 }
-                tc_commit(&bar[t & 1]);
             }
-            pending |= 1u << (t & 1);
+            tc_commit(&bar[t & 1]);
+        };
+        // the mask and residual chunks of output row t this thread stores
+        uint4 mreg[Cf::O16], rreg[Cf::O16];
+        auto prefetch_epi = [&](int t) {
+            if (!out16 || t >= L) return;
+            const size_t row0 = ((size_t)n * H + y0 + t) * W + x0;
+#pragma unroll
+            for (int j = 0; j < Cf::O16; ++j) {
+                const int i = tid + j * TC_EPI_THREADS;
+                const int p = i / (COUT / 8), g8 = i % (COUT / 8);
+                if (p < nvalid) {
+                    const size_t o = (row0 + p) * COUT + g8 * 8;
+                    if (mask) mreg[j] = *reinterpret_cast<const uint4*>(mask + o);
+                    if (res16) rreg[j] = *reinterpret_cast<const uint4*>(res16 + o);
+                }
+            }
         };
 
-        load_row(0);
-        store_row(0);
-        load_row(1);
-        store_row(1);
-        load_row(2);
-        store_row(2);
-        if (L > 1) load_row(3);
-        tc_sync_stores();
-        issue(0);
+        if (is_epi) {
+            // prologue: every slot's row in flight; rows 0..2 in place for row 0's MMAs
+#pragma unroll 1
+            for (int li = 0; li < TC_NSLOT; ++li) copy_row(li);
+            prefetch_epi(0);
+            cp_async_wait<TC_NSLOT - 3>();
+            relu_row(0);
+            relu_row(1);
+            relu_row(2);
+            fence_proxy_async();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == TC_EPI_THREADS) issue(0);
+        pending |= 1u;
+        bool timed_out = false;
         for (int t = 0; t < L; ++t) {
             const int y = y0 + t;
             if (t + 1 < L) {
-                // the slot of row li = t + 3 last served output row t - 1, whose MMAs were waited for
-                store_row(t + 3);
-                tc_sync_stores();  // also: the epilogue of row t - 1 has read accumulator (t + 1) & 1
-                issue(t + 1);
-                if (t + 2 < L) load_row(t + 4);
-            }
-            // prefetch the epilogue's operands of row t
-            const bool valid = epi && x0 + pix < W;
-            const size_t p = ((size_t)n * H + y) * W + (valid ? x0 + pix : 0);
-            uint4 mreg[Cf::EPI_CH][2], rreg[Cf::EPI_CH][2];
-            if (valid) {
-#pragma unroll
-                for (int ch = 0; ch < Cf::EPI_CH; ++ch) {
-                    const int c = col0 + 16 * ch;
-                    if (mask) {
-                        mreg[ch][0] = *reinterpret_cast<const uint4*>(mask + p * COUT + c);
-                        mreg[ch][1] = *reinterpret_cast<const uint4*>(mask + p * COUT + c + 8);
-                    }
-                    if (res16) {
-                        rreg[ch][0] = *reinterpret_cast<const uint4*>(res16 + p * COUT + c);
-                        rreg[ch][1] = *reinterpret_cast<const uint4*>(res16 + p * COUT + c + 8);
-                    }
+                // row li = t + 3 completes the rows of output row t + 1
+                if (is_epi) {
+                    cp_async_wait<TC_NSLOT - 4>();
+                    relu_row(t + 3);
+                    fence_proxy_async();
                 }
+                tc_fence_before();
+                // also: the epilogue of row t - 1 has read accumulator (t + 1) & 1
+                // and every thread has left the staging tile of row t - 1
+                if (__syncthreads_or(timed_out)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (tid == TC_EPI_THREADS) issue(t + 1);
+                pending |= 1u << ((t + 1) & 1);
             }
+            if (!is_epi) continue;
             const uint32_t b = (uint32_t)(t & 1);
-            const bool done = bar_wait(&bar[b], (parity >> b) & 1u);
-            if (__syncthreads_or(!done)) {
-                ok = false;
-                break;
-            }
+            if (!bar_wait(&bar[b], (parity >> b) & 1u)) timed_out = true;
             parity ^= 1u << b;
             pending &= ~(1u << b);
             tc_fence_after();
-            if (epi) {
+            // MMA(t) has read its rows: the slot of row t takes row t + TC_NSLOT
+            copy_row(t + TC_NSLOT);
+            // accumulator + bias -> FP32 staging tile (on the run's last row no
+            // block barrier has separated this from the tile's previous readers)
+            if (t + 1 >= L) epi_sync();
 #pragma unroll
-                for (int ch = 0; ch < Cf::EPI_CH; ++ch) {
-                    const int c = col0 + 16 * ch;
-                    float v[16];
-                    tc_ld16(t_lane + b * COUT + (uint32_t)c, v);
-                    if (!valid) continue;
+            for (int ch = 0; ch < Cf::EPI_CH; ++ch) {
+                const int c = col0 + Cf::NC * ch;
+                float v[16];
+                tc_ld<Cf::NC>(t_lane + b * COUT + (uint32_t)c, v);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] += s_bias[c + j];
+                for (int q = 0; q < Cf::NC / 4; ++q) {
+                    const int k = c / 4 + q;
+                    const float4 bb = *reinterpret_cast<const float4*>(s_bias + 4 * k);
+                    *reinterpret_cast<float4*>(tile + pix * COUT + 4 * (k ^ (pix & Cf::SWZ))) =
+                        make_float4(v[4 * q] + bb.x, v[4 * q + 1] + bb.y, v[4 * q + 2] + bb.z, v[4 * q + 3] + bb.w);
+                }
+            }
+            epi_sync();
+            // staging tile -> global, coalesced 16-byte chunks of the row
+            const size_t row0 = ((size_t)n * H + y) * W + x0;
+            if (out16) {
+#pragma unroll
+                for (int j = 0; j < Cf::O16; ++j) {
+                    const int i = tid + j * TC_EPI_THREADS;
+                    const int p = i / (COUT / 8), g8 = i % (COUT / 8);
+                    if (p >= nvalid) continue;
+                    const float4 lo = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * ((2 * g8) ^ (p & Cf::SWZ)));
+                    const float4 hi = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * ((2 * g8 + 1) ^ (p & Cf::SWZ)));
+                    float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
                     if (mask) {
-                        const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mreg[ch]);
+                        const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(&mreg[j]);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (!(__bfloat162float(mh[j]) > 0.f)) v[j] = 0.f;
+                        for (int q = 0; q < 8; ++q)
+                            if (!(__bfloat162float(mh[q]) > 0.f)) v[q] = 0.f;
                     }
                     if (res16) {
-                        const __nv_bfloat16* rh = reinterpret_cast<const __nv_bfloat16*>(rreg[ch]);
+                        const __nv_bfloat16* rh = reinterpret_cast<const __nv_bfloat16*>(&rreg[j]);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] += __bfloat162float(rh[j]);
+                        for (int q = 0; q < 8; ++q) v[q] += __bfloat162float(rh[q]);
                     }
                     if (res32) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c + j < res32_c) v[j] += res32[p * res32_c + c + j];
+                        for (int q = 0; q < 8; ++q)
+                            if (g8 * 8 + q < res32_c) v[q] += res32[(row0 + p) * res32_c + g8 * 8 + q];
                     }
-                    if (out32) {
-                        float4* o = reinterpret_cast<float4*>(out32 + p * COUT + c);
+                    uint4 ov;
+                    __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&ov);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                    } else {
-                        uint4 o[2];
-                        __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(o);
+                    for (int q = 0; q < 4; ++q) oh[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                    *reinterpret_cast<uint4*>(out16 + (row0 + p) * COUT + g8 * 8) = ov;
+                }
+            } else {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) oh[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        uint4* dst = reinterpret_cast<uint4*>(out16 + p * COUT + c);
-                        dst[0] = o[0];
-                        dst[1] = o[1];
+                for (int j = 0; j < Cf::O32; ++j) {
+                    const int i = tid + j * TC_EPI_THREADS;
+                    const int p = i / (COUT / 4), k = i % (COUT / 4);
+                    if (p >= nvalid) continue;
+                    float4 v = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * (k ^ (p & Cf::SWZ)));
+                    if (res32) {
+                        if (4 * k + 0 < res32_c) v.x += res32[(row0 + p) * res32_c + 4 * k + 0];
+                        if (4 * k + 1 < res32_c) v.y += res32[(row0 + p) * res32_c + 4 * k + 1];
+                        if (4 * k + 2 < res32_c) v.z += res32[(row0 + p) * res32_c + 4 * k + 2];
+                        if (4 * k + 3 < res32_c) v.w += res32[(row0 + p) * res32_c + 4 * k + 3];
                     }
+                    *reinterpret_cast<float4*>(out32 + (row0 + p) * COUT + 4 * k) = v;
                 }
             }
+            prefetch_epi(t + 1);
         }
-        // the next run reuses the slots and accumulator 0
+        // copies still in flight (rows the run does not need) land before the slots are reused
+        if (is_epi) cp_async_wait<0>();
         tc_fence_before();
-        __syncthreads();
+        if (__syncthreads_or(timed_out)) ok = false;
         tc_fence_after();
     }
     if (!ok) {
         // let MMAs still in flight finish (bounded) before the memory is released
-        for (uint32_t b = 0; b < 2; ++b)
-            if (pending & (1u << b)) bar_wait(&bar[b], (parity >> b) & 1u);
+        if (is_epi)
+            for (uint32_t b = 0; b < 2; ++b)
+                if (pending & (1u << b)) bar_wait(&bar[b], (parity >> b) & 1u);
         if (tid == 0) atomicOr(status, 1);
     }
     tc_fence_before();
