@@ -117,6 +117,25 @@ def interface_stats(m, p):
     return liq, edges
 
 
+def network_cost(P, C=64, B=6):
+    """Algorithmic work of one forward pass over P pixels: the FLOPs of its
+    3x3 convolutions at their real channel counts (lift 4 -> C, 2 B
+    convolutions C -> C, projection C -> 4), and the HBM bytes if every
+    layer reads its inputs once and writes its output once: FP64 fields in
+    and out, the packed input (16 BF16 channels and its FP32 copy), each
+    BF16 activation written once and read by the next layer (the second
+    convolution of a block also reads the block's input as residual), and
+    the 16-channel FP32 output."""
+    flops = 2 * 9 * P * (4 * C + 2 * B * C * C + C * 4)
+    act = P * C * 2
+    nbytes = (4 * 8 * P + P * 16 * 2 + P * 4 * 4)   # pack
+    nbytes += P * 16 * 2 + act                          # lift
+    nbytes += B * (2 * act) + B * (3 * act)             # blocks
+    nbytes += act + P * 4 * 4 + P * 16 * 4              # projection with the FP32 residual
+    nbytes += P * 16 * 4 + 4 * 8 * P                    # unpack
+    return flops, nbytes
+
+
 def lb_own_drift(cfg, fields, p, njumps, K):
     """What the plain LB does per K-step jump on the same case: the largest
     relative change of mass and total energy, and the largest mean interface
@@ -184,6 +203,18 @@ def rollout_study(sur, p, size=1024, njumps=10, K=50, tol=1e-3, iface_tol=0.5, s
         sur.forward(x, out)
     torch.cuda.synchronize()
     t_fwd = (time.perf_counter() - t0) / 5
+    # the same network on the warp-level mma.sync convolutions
+    alt = lbm.Surrogate(sur.norm_off, sur.norm_scale, K=K, conv_path="mma", conserve_mass=sur.conserve_mass)
+    alt.set_params(sur.get_params())
+    alt.forward(x, out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        alt.forward(x, out)
+    torch.cuda.synchronize()
+    t_fwd_mma = (time.perf_counter() - t0) / 5
+    alt.close()
+    flops, nbytes = network_cost(size * size)
     c = p["c"]
     err = {"rho": float(np.abs(m["rho"] - m_ref["rho"]).max() / np.abs(m_ref["rho"]).max()),
            "T": float(np.abs(m["T"] - m_ref["T"]).max() / np.abs(m_ref["T"]).max()),
@@ -192,7 +223,10 @@ def rollout_study(sur, p, size=1024, njumps=10, K=50, tol=1e-3, iface_tol=0.5, s
     return {"size": size, "jumps": njumps, "K": K, "verify_steps": kv, "drift_tol": tol, "iface_tol": iface_tol,
             "lb_s": t_lb, "surrogate_path_s": t_sur, "speedup_vs_lb": t_lb / t_sur,
             "accepted": st["accepted"], "fallbacks": st["fallbacks"],
-            "ms_per_jump_network_only": 1e3 * t_fwd, "ms_per_jump_lb_steps": 1e3 * t_lb / njumps,
+            "ms_per_jump_network_only": 1e3 * t_fwd, "ms_per_jump_network_mma_sync": 1e3 * t_fwd_mma,
+            "network_forward": {"flops": flops, "bytes": nbytes, "tflops": flops / t_fwd / 1e12,
+                                "gbs": nbytes / t_fwd / 1e9},
+            "ms_per_jump_lb_steps": 1e3 * t_lb / njumps,
             "max_mass_drift_accepted": st["max_mass_drift"], "max_energy_drift_accepted": st["max_energy_drift"],
             "max_drift_all_jumps": {"mass": st["max_mass_drift_all"], "energy": st["max_energy_drift_all"],
                                     "iface_displacement": st["max_iface_displacement_all"]},
