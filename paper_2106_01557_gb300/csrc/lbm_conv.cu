@@ -154,108 +154,174 @@ __global__ void __launch_bounds__(CT, 1)
 }
 
 // Weight gradient dW[tap][co][ci] += sum_p dOut[p][co] * act(in[p + off(tap)][ci]).
-// Grid: x = 9 taps * COUT/16 output-channel tiles, y = pixel partitions.
+// A CTA owns one filter row dy (its three taps dx = -1, 0, 1) and every
+// output and input channel, over a run of 128-pixel row chunks: the chunk's
+// dOut row [128 px][COUT] and the input row y + dy [130 px][CIN] (periodic
+// halo) are copied with cp.async into padded shared tiles (two stages), and
+// ldmatrix.trans forms the MMA fragments straight from these pixel-major
+// tiles: A = dOut^T (co x pixels), B = input (pixels x ci, shifted by dx).
+// One A fragment serves the three taps. Warp w owns the 16-channel output
+// block w % (COUT/16) and a contiguous group of 8-channel input blocks; its
+// FP32 sums are added to dw once at the end (atomics).
 constexpr int WT = 256;      // threads (8 warps)
-constexpr int WCH = 128;     // pixels per chunk: 8 warps x one k16 step
+constexpr int WCH = 128;     // pixels per chunk
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+// 16-byte async copy; src_bytes = 0 fills the destination with zeros
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+template <int CIN, int COUT>
+struct WgCfg {
+    static constexpr int RSD = COUT * 2 + 16;          // padded row bytes of the dOut tile (ldmatrix: no conflicts)
+    static constexpr int RSX = CIN * 2 + 16;           // padded row bytes of the input tile
+    static constexpr int D_BYTES = WCH * RSD;
+    static constexpr int X_BYTES = (WCH + 2) * RSX;
+    static constexpr int STAGE = D_BYTES + X_BYTES;
+    static constexpr int MT = COUT / 16;               // 16-channel output blocks
+    static constexpr int NG = 8 / MT;                  // warps per output block
+    static constexpr int NPW = (CIN / 8) / NG;         // 8-channel input blocks per warp
+    static_assert(COUT % 16 == 0 && COUT <= 128 && 8 % MT == 0 && (CIN / 8) % NG == 0 && NPW >= 1, "warp split");
+};
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(WT)
     k_wgrad(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dout, int N, int H, int W,
             int in_relu, float* __restrict__ dw) {
-    constexpr int PP = WCH + 8;  // padded pixel stride of the transposed tiles
-    constexpr int TILE_BYTES = 2 * (16 + CIN) * PP;
-    constexpr int RED_BYTES = 4 * 8 * 16 * (CIN + 1);
-    // the transposed tiles and, after the pixel loop, the cross-warp sums share one buffer
-    __shared__ __align__(16) unsigned char s_buf[TILE_BYTES > RED_BYTES ? TILE_BYTES : RED_BYTES];
-    __nv_bfloat16* s_d = reinterpret_cast<__nv_bfloat16*>(s_buf);            // [co][p]
-    __nv_bfloat16* s_x = s_d + 16 * PP;                                       // [ci][p]
-    float (*s_red)[16][CIN + 1] = reinterpret_cast<float (*)[16][CIN + 1]>(s_buf);
+    using Cf = WgCfg<CIN, COUT>;
+    extern __shared__ __align__(16) unsigned char wg_smem[];
     const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
     const int g = lane / 4, t = lane % 4;
-    const int tap = blockIdx.x / (COUT / 16), cot = blockIdx.x % (COUT / 16);
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    const long long P = (long long)N * H * W;
-    const long long nchunks = (P + WCH - 1) / WCH;
-    constexpr int NT8 = CIN / 8;
-    float acc[NT8][4];
+    const int dy = (int)blockIdx.y - 1;
+    const int tiles_x = (W + WCH - 1) / WCH;
+    const long long nchunks = (long long)N * H * tiles_x;
+    const int mt = warp % Cf::MT, nt0 = (warp / Cf::MT) * Cf::NPW;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(wg_smem);
+    float acc[3][Cf::NPW][4];
 #pragma unroll
-    for (int j = 0; j < NT8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    for (long long ch = blockIdx.y; ch < nchunks; ch += gridDim.y) {
-        const long long p0 = ch * WCH;
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < Cf::NPW; ++j) acc[a][j][0] = acc[a][j][1] = acc[a][j][2] = acc[a][j][3] = 0.f;
+
+    // copy chunk ch into stage st (one commit group per call, empty past the end)
+    auto load = [&](long long ch, int st) {
+        if (ch < nchunks) {
+            const int x0 = (int)(ch % tiles_x) * WCH;
+            const long long ry = ch / tiles_x;  // n * H + y
+            const int y = (int)(ry % H), n = (int)(ry / H);
+            int yy = y + dy;
+            yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+            const uint32_t sd = sbase + st * Cf::STAGE, sx = sd + Cf::D_BYTES;
+            const __nv_bfloat16* drow = dout + (size_t)ry * W * COUT;
+            const __nv_bfloat16* xrow = in + ((size_t)n * H + yy) * W * CIN;
+            for (int e = tid; e < WCH * (COUT / 8); e += WT) {
+                const int px = e / (COUT / 8), c8 = e % (COUT / 8);
+                const int x = x0 + px;
+                cp16(sd + px * Cf::RSD + c8 * 16, drow + (size_t)(x < W ? x : 0) * COUT + c8 * 8, x < W ? 16 : 0);
+            }
+            for (int e = tid; e < (WCH + 2) * (CIN / 8); e += WT) {
+                const int px = e / (CIN / 8), c8 = e % (CIN / 8);
+                int x = x0 - 1 + px;
+                x = x < 0 ? x + W : (x >= W ? x % W : x);
+                cp16(sx + px * Cf::RSX + c8 * 16, xrow + (size_t)x * CIN + c8 * 8, 16);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // ReLU in place on the input vectors this thread copied
+    auto relu_tile = [&](int st) {
+        unsigned char* sx = wg_smem + st * Cf::STAGE + Cf::D_BYTES;
+        for (int e = tid; e < (WCH + 2) * (CIN / 8); e += WT) {
+            const int px = e / (CIN / 8), c8 = e % (CIN / 8);
+            uint4* v = reinterpret_cast<uint4*>(sx + px * Cf::RSX + c8 * 16);
+            uint4 u = *v;
+            __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(&u);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) h[q] = relu_bf(h[q]);
+            *v = u;
+        }
+    };
+
+    long long ch = blockIdx.x;
+    load(ch, 0);
+    for (int it = 0; ch < nchunks; ch += gridDim.x, ++it) {
+        const int st = it & 1;
+        load(ch + gridDim.x, st ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        if (in_relu) relu_tile(st);
         __syncthreads();
-        // 16-byte coalesced loads (8 channels of one pixel), scattered into
-        // the transposed [channel][pixel] tiles
-        constexpr int C8 = (16 + CIN) / 8;  // 8-channel groups per pixel: 2 of dOut, CIN/8 of input
-        for (int e = tid; e < WCH * C8; e += WT) {
-            const int grp = e % C8, px = e / C8;
-            const long long p = p0 + px;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (p < P) {
-                if (grp < 2) {
-                    v = *reinterpret_cast<const uint4*>(dout + p * COUT + cot * 16 + grp * 8);
-                } else {
-                    const int n = (int)(p / ((long long)H * W));
-                    const int rem = (int)(p % ((long long)H * W));
-                    int yy = rem / W + dy, xx = rem % W + dx;
-                    yy = (yy % H + H) % H;
-                    xx = (xx % W + W) % W;
-                    v = *reinterpret_cast<const uint4*>(in + (((size_t)n * H + yy) * W + xx) * CIN + (grp - 2) * 8);
-                    if (in_relu) {
-                        __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&v);
+        const uint32_t sd = sbase + st * Cf::STAGE, sx = sd + Cf::D_BYTES;
+#pragma unroll 2
+        for (int k0 = 0; k0 < WCH; k0 += 16) {
+            // A = dOut^T: rows co (mt*16 ..), columns pixels k0 .. k0+15
+            const int q = lane / 8;
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4_t(sd + (k0 + (q >= 2 ? 8 : 0) + lane % 8) * Cf::RSD + (mt * 16 + (q & 1) * 8) * 2, a0, a1, a2, a3);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) hh[j] = relu_bf(hh[j]);
-                    }
+            for (int tap = 0; tap < 3; ++tap) {
+                // B = input pixels k0 + dx .. (tile pixel index + 1 for the halo)
+#pragma unroll
+                for (int j = 0; j < Cf::NPW; ++j) {
+                    uint32_t b0, b1;
+                    const int l = lane % 16;
+                    ldsm_x2_t(sx + (k0 + tap + (l >= 8 ? 8 : 0) + l % 8) * Cf::RSX + (nt0 + j) * 16, b0, b1);
+                    mma_bf16(acc[tap][j][0], acc[tap][j][1], acc[tap][j][2], acc[tap][j][3], a0, a1, a2, a3, b0, b1);
                 }
             }
-            const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v);
-            __nv_bfloat16* dst = grp < 2 ? s_d + (grp * 8) * PP + px : s_x + ((grp - 2) * 8) * PP + px;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) dst[j * PP] = hv[j];
         }
-        __syncthreads();
-        // warp w: pixels [16 w, 16 w + 16) as the k16 step; A = dOut^T (co x p), B = in (p x ci)
-        const int k0 = warp * 16;
-        const __nv_bfloat16* a = s_d + k0 + 2 * t;
-        const uint32_t a0 = ld32(a + g * PP), a1 = ld32(a + (g + 8) * PP);
-        const uint32_t a2 = ld32(a + g * PP + 8), a3 = ld32(a + (g + 8) * PP + 8);
+        __syncthreads();  // the stage is refilled by the next iteration's load
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // accumulator (row co, column ci) -> dw[tap][co][ci], tap = 3 (dy + 1) + dx + 1
 #pragma unroll
-        for (int j = 0; j < NT8; ++j) {
-            const __nv_bfloat16* b = s_x + (j * 8 + g) * PP + k0 + 2 * t;
-            mma_bf16(acc[j][0], acc[j][1], acc[j][2], acc[j][3], a0, a1, a2, a3, ld32(b), ld32(b + 8));
+    for (int tap = 0; tap < 3; ++tap) {
+        const int tp = 3 * (dy + 1) + tap;
+#pragma unroll
+        for (int j = 0; j < Cf::NPW; ++j) {
+            const int co = mt * 16 + g, ci = (nt0 + j) * 8 + 2 * t;
+            float* d = dw + ((size_t)tp * COUT + co) * CIN + ci;
+            atomicAdd(d, acc[tap][j][0]);
+            atomicAdd(d + 1, acc[tap][j][1]);
+            atomicAdd(d + 8 * CIN, acc[tap][j][2]);
+            atomicAdd(d + 8 * CIN + 1, acc[tap][j][3]);
         }
-    }
-    // reduce the 8 warps' partial sums, then one atomic per element
-    __syncthreads();  // last chunk's tile reads done before the buffer is reused
-#pragma unroll
-    for (int j = 0; j < NT8; ++j) {
-        s_red[warp][g][j * 8 + 2 * t] = acc[j][0];
-        s_red[warp][g][j * 8 + 2 * t + 1] = acc[j][1];
-        s_red[warp][g + 8][j * 8 + 2 * t] = acc[j][2];
-        s_red[warp][g + 8][j * 8 + 2 * t + 1] = acc[j][3];
-    }
-    __syncthreads();
-    for (int e = tid; e < 16 * CIN; e += WT) {
-        const int co = e / CIN, ci = e % CIN;
-        float s = 0.f;
-#pragma unroll
-        for (int w8 = 0; w8 < 8; ++w8) s += s_red[w8][co][ci];
-        atomicAdd(&dw[((size_t)tap * COUT + cot * 16 + co) * CIN + ci], s);
     }
 }
 
+// Bias gradient db[c] += sum_p dOut[p][c] (C a multiple of 8, C <= 256):
+// thread = one 8-channel group of a pixel (16-byte loads, coalesced across
+// the block), per-thread sums reduced per channel group in shared memory.
 __global__ void k_bgrad(const __nv_bfloat16* __restrict__ dout, long long P, int C, float* __restrict__ db) {
-    __shared__ float s[256];
-    const int c = blockIdx.x;
-    float acc = 0.f;
-    for (long long p = blockIdx.y * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.y * blockDim.x)
-        acc += __bfloat162float(dout[p * C + c]);
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-        __syncthreads();
+    __shared__ float s[256][9];
+    const int G8 = C / 8;
+    const int per = blockDim.x / G8;  // pixels per block sweep
+    const int c8 = threadIdx.x % G8, sub = threadIdx.x / G8;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (sub < per) {
+        for (long long p = (long long)blockIdx.x * per + sub; p < P; p += (long long)gridDim.x * per) {
+            const uint4 v = *reinterpret_cast<const uint4*>(dout + p * C + c8 * 8);
+            const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] += __bfloat162float(h[q]);
+        }
     }
-    if (threadIdx.x == 0) atomicAdd(&db[c], s[0]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[threadIdx.x][q] = acc[q];
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        const int g8 = c / 8, q = c % 8;
+        float t = 0.f;
+        for (int k = 0; k < per; ++k) t += s[k * G8 + g8][q];
+        atomicAdd(&db[c], t);
+    }
 }
 
 // loss = mean over P pixels and 4 channels of (out - target)^2; dout = d loss / d out.
@@ -431,13 +497,18 @@ cudaError_t conv_t(const ConvArgs& a, cudaStream_t s, int sms) {
 template <int CIN, int COUT>
 cudaError_t wgrad_t(const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W, int in_relu, float* dw,
                     cudaStream_t s, int sms) {
-    const long long P = (long long)N * H * W;
-    long long chunks = (P + WCH - 1) / WCH;
-    const int gx = 9 * (COUT / 16);
-    long long gy = (2 * sms + gx - 1) / gx * 4;
-    if (gy > chunks) gy = chunks;
-    if (gy < 1) gy = 1;
-    k_wgrad<CIN, COUT><<<dim3(gx, (unsigned)gy), WT, 0, s>>>(in, dout, N, H, W, in_relu, dw);
+    using Cf = WgCfg<CIN, COUT>;
+    static bool set = false;
+    if (!set) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * Cf::STAGE);
+        if (e != cudaSuccess) return e;
+        set = true;
+    }
+    const long long chunks = (long long)N * H * ((W + WCH - 1) / WCH);
+    long long gx = (2 * sms + 2) / 3;  // with the three filter rows: about two CTAs per SM
+    if (gx > chunks) gx = chunks;
+    if (gx < 1) gx = 1;
+    k_wgrad<CIN, COUT><<<dim3((unsigned)gx, 3), WT, 2 * Cf::STAGE, s>>>(in, dout, N, H, W, in_relu, dw);
     return cudaGetLastError();
 }
 
@@ -493,9 +564,11 @@ cudaError_t launch_wgrad(int cin, int cout, const __nv_bfloat16* in, const __nv_
 }
 
 cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, cudaStream_t s) {
-    long long gy = (P + 255) / 256;
-    if (gy > 64) gy = 64;
-    k_bgrad<<<dim3(C, (unsigned)gy), 256, 0, s>>>(dout, P, C, db);
+    if (C < 8 || C % 8 != 0 || C > 256) return cudaErrorInvalidValue;
+    const int per = 256 / (C / 8);
+    long long g = (P + per - 1) / per;
+    if (g > 608) g = 608;
+    k_bgrad<<<(unsigned)g, 256, 0, s>>>(dout, P, C, db);
     return cudaGetLastError();
 }
 
