@@ -391,7 +391,7 @@ def main():
     ap.add_argument("--batch-study", type=int, default=0,
                     help="run the 256-case sweep for this many steps and report coexistence per case")
     ap.add_argument("--batch-precision", default="f16s", choices=["f32", "f16s", "bf16s"])
-    ap.add_argument("--surrogate-iters", type=int, default=600,
+    ap.add_argument("--surrogate-iters", type=int, default=3000,
                     help="training iterations of the surrogate study in the default run (0: skip)")
     ap.add_argument("--nx", type=int, default=NX, help="smaller lattice for profiling captures")
     ap.add_argument("--ny", type=int, default=NY)

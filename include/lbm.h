@@ -293,13 +293,17 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
  * snapshot and runs K + verify_steps LB steps instead. Every jump thus
  * advances the lattice by K + verify_steps steps. LBM_ERR_DIVERGED is
  * returned only if those fallback LB steps diverge.
- * stats (may be NULL, >= 11): [0] jumps accepted, [1] fallbacks,
- * [2] ms in surrogate jumps (prediction and verification), [3] ms in
- * fallback LB steps, [4] largest accepted mass drift, [5] largest accepted
- * energy drift, [6..7] largest mass and energy drift over all jumps, [8]
- * largest interface displacement over all jumps, [9] jumps with an
- * unphysical prediction, [10] jumps whose verification steps diverged.
- * Synchronous. */
+ * stats (may be NULL, >= 15): [0] jumps accepted, [1] fallbacks,
+ * [2] ms in surrogate jumps (prediction, checks, re-initialisation and
+ * verification: [12] + [13] + [14]), [3] ms in fallback LB steps, [4]
+ * largest accepted mass drift, [5] largest accepted energy drift, [6..7]
+ * largest mass and energy drift over all jumps, [8] largest interface
+ * displacement over all jumps, [9] jumps with an unphysical prediction,
+ * [10] jumps whose verification steps diverged, [11] ms reading the state
+ * before each jump (fields, conservation record, checks, snapshot), [12] ms
+ * in the network, [13] ms in the checks of the prediction, the
+ * re-initialisation of the populations and the conservation record, [14]
+ * ms in the verification steps. Synchronous. */
 int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32_t verify_steps, double drift_tol,
                           double iface_tol, double* stats);
 int lbm_surrogate_destroy(lbm_surrogate* s);

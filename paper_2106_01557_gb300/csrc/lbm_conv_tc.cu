@@ -11,12 +11,12 @@
 // where the layer wants it, is applied in place by the thread that copied
 // the vector).
 //
-// Roles: warps 0-7 copy, apply ReLU and run the epilogue; warp 8 only issues
-// the MMAs (one elected lane), so the next row's MMAs never wait for an
-// epilogue and an epilogue never waits for the issue. Two accumulators in
-// tensor memory let the MMAs of row t + 1 run while the epilogue of row t
-// reads row t out with tcgen05.ld (warp w reads lanes 32 (w % 4) .. + 31 =
-// pixels, half of the columns each), adds the bias and stages FP32 values in
+// Roles: warps 0 .. TC_EPI_WARPS - 1 copy, apply ReLU and run the epilogue;
+// the last warp only issues the MMAs (one elected lane), so the next row's
+// MMAs never wait for an epilogue and an epilogue never waits for the issue.
+// Two accumulators in tensor memory let the MMAs of row t + 1 run while the
+// epilogue of row t reads row t out with tcgen05.ld (warp w reads lanes
+// 32 (w % 4) .. + 31 = pixels, a share of the columns), adds the bias and stages FP32 values in
 // a shared tile (16-byte chunks XOR-swizzled by pixel, no bank conflicts);
 // the tile then leaves in coalesced 16-byte stores, where the mask and the
 // residual (loaded one row ahead) are applied.
@@ -41,8 +41,9 @@ namespace lbm {
 namespace {
 
 constexpr int TC_TW = 128;          // pixels per output row segment (MMA M)
-constexpr int TC_EPI_THREADS = 256; // warps 0-7: copies and epilogue
-constexpr int TC_THREADS = 288;     // + warp 8: MMA issue
+constexpr int TC_EPI_WARPS = 16;    // warps 0 .. TC_EPI_WARPS - 1: copies and epilogue
+constexpr int TC_EPI_THREADS = 32 * TC_EPI_WARPS;
+constexpr int TC_THREADS = TC_EPI_THREADS + 32;  // + one warp: MMA issue
 constexpr int TC_NSLOT = 7;         // input-row ring: 3 rows in use, the rest in flight
 
 template <int CIN, int COUT>
@@ -57,15 +58,18 @@ struct TcCfg {
     static constexpr int ROW_VECS = KG * PIX;           // 16-byte vectors per halo'd row
     static constexpr int VPT = (ROW_VECS + TC_EPI_THREADS - 1) / TC_EPI_THREADS;
     static constexpr int TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;  // two accumulators, power of two
-    static constexpr int EPI_COLS = COUT / 2;           // accumulator columns per epilogue warp
+    // warps reading the accumulator (4 per lane quarter group, >= 8 columns each)
+    static constexpr int TW_WARPS = TC_EPI_WARPS < COUT / 2 ? TC_EPI_WARPS : COUT / 2;
+    static constexpr int EPI_COLS = COUT / (TW_WARPS / 4);  // accumulator columns per reading warp
     static constexpr int NC = EPI_COLS < 16 ? EPI_COLS : 16;        // columns per tcgen05.ld
     static constexpr int EPI_CH = EPI_COLS / NC;        // tcgen05.ld per thread and row
     static constexpr int CPP = COUT / 4;                // 16-byte FP32 chunks per pixel in the tile
     static constexpr int SWZ = (CPP < 8 ? CPP : 8) - 1; // chunk swizzle mask
-    static constexpr int O16 = TC_TW * COUT / 8 / TC_EPI_THREADS;  // BF16 output chunks per thread
-    static constexpr int O32 = TC_TW * COUT / 4 / TC_EPI_THREADS;  // FP32 output chunks per thread
+    static constexpr int N16 = TC_TW * COUT / 8, N32 = TC_TW * COUT / 4;  // 16-byte output chunks of a row
+    static constexpr int O16 = (N16 + TC_EPI_THREADS - 1) / TC_EPI_THREADS;  // BF16 chunks per thread
+    static constexpr int O32 = (N32 + TC_EPI_THREADS - 1) / TC_EPI_THREADS;  // FP32 chunks per thread
     static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "tcgen05 f16 shape");
-    static_assert(TC_TW * COUT / 8 >= TC_EPI_THREADS && (NC == 8 || NC == 16), "tile split");
+    static_assert(TW_WARPS % 4 == 0 && COUT % (TW_WARPS / 4) == 0 && (NC == 8 || NC == 16), "tile split");
     static_assert(TMEM_COLS <= 512, "tensor memory");
     static_assert(BYTES <= 227 * 1024, "shared memory");
 };
@@ -113,8 +117,8 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, float* v) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// barrier of the 256 epilogue threads only (the issue warp does not wait)
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// barrier of the epilogue threads only (the issue warp does not wait)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_THREADS) : "memory"); }
 
 // bounded wait on an mbarrier phase; true when it completed in time
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t pending = 0;  // bit b: a commit to bar[b] not yet waited for
     bool ok = true;
 
-    // epilogue geometry of this thread: pixel = TMEM lane, a half of the columns
+    // epilogue geometry of this thread: pixel = TMEM lane, a share of the columns
     const int pix = 32 * (warp % 4) + lane;
     const int col0 = (warp / 4) * Cf::EPI_COLS;
     const uint32_t t_lane = tmem + ((uint32_t)(32 * (warp % 4)) << 16);
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int j = 0; j < Cf::O16; ++j) {
                 const int i = tid + j * TC_EPI_THREADS;
                 const int p = i / (COUT / 8), g8 = i % (COUT / 8);
-                if (p < nvalid) {
+                if (i < Cf::N16 && p < nvalid) {
                     const size_t o = (row0 + p) * COUT + g8 * 8;
                     if (mask) mreg[j] = *reinterpret_cast<const uint4*>(mask + o);
                     if (res16) rreg[j] = *reinterpret_cast<const uint4*>(res16 + o);
@@ -339,6 +343,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (t + 1 >= L) epi_sync();
 #pragma unroll
             for (int ch = 0; ch < Cf::EPI_CH; ++ch) {
+                if (warp >= Cf::TW_WARPS) break;
                 const int c = col0 + Cf::NC * ch;
                 float v[16];
                 tc_ld<Cf::NC>(t_lane + b * COUT + (uint32_t)c, v);
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int j = 0; j < Cf::O16; ++j) {
                     const int i = tid + j * TC_EPI_THREADS;
                     const int p = i / (COUT / 8), g8 = i % (COUT / 8);
-                    if (p >= nvalid) continue;
+                    if (i >= Cf::N16 || p >= nvalid) continue;
                     const float4 lo = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * ((2 * g8) ^ (p & Cf::SWZ)));
                     const float4 hi = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * ((2 * g8 + 1) ^ (p & Cf::SWZ)));
                     float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int j = 0; j < Cf::O32; ++j) {
                     const int i = tid + j * TC_EPI_THREADS;
                     const int p = i / (COUT / 4), k = i % (COUT / 4);
-                    if (p >= nvalid) continue;
+                    if (i >= Cf::N32 || p >= nvalid) continue;
                     float4 v = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * (k ^ (p & Cf::SWZ)));
                     if (res32) {
                         if (4 * k + 0 < res32_c) v.x += res32[(row0 + p) * res32_c + 4 * k + 0];

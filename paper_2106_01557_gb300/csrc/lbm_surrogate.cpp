@@ -492,11 +492,18 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
         return LBM_OK;
     };
     cudaStream_t hs = lbm_internal_stream(h);
+    using clk = std::chrono::steady_clock;
+    auto ms = [](clk::time_point a, clk::time_point b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+    double t_prep = 0, t_net = 0, t_judge = 0, t_ver = 0;
+    double c0[6], c1[6];
+    bool have_c0 = false;  // the record of the current state is known (after an accepted jump)
     for (int j = 0; j < njumps; ++j) {
-        double c0[6], c1[6];
         unsigned long long n0[4], n1[4];
-        rc = lbm_conservation(h, c0);
-        if (rc) return rc;
+        const auto tp = clk::now();
+        if (!have_c0) {
+            rc = lbm_conservation(h, c0);
+            if (rc) return rc;
+        }
         rc = lbm_moments(h, s->fields, s->fields + P, s->fields + 2 * P, s->fields + 3 * P, 1);
         if (rc) return rc;
         rc = check(s->fields, nullptr, n0);
@@ -504,18 +511,24 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
         rc = lbm_internal_snapshot(h, s->snapshot);
         if (rc) return rc;
         SCK(cudaStreamSynchronize(hs));
-        auto t0 = std::chrono::steady_clock::now();
+        auto t0 = clk::now();
+        t_prep += ms(tp, t0);
         rc = lbm_surrogate_forward(s, s->fields, 1, ny, nx, s->pred);
         if (rc) return rc;
+        const auto tn = clk::now();
+        t_net += ms(t0, tn);
         // an unphysical prediction (non-finite, rho <= 0 or T <= 0) is a rejected jump
         rc = check(s->pred, s->fields, n1);
         if (rc) return rc;
         const bool physical = n1[1] == 0;
         double dm = 0, de = 0, da = 0;
         bool diverged = false;
+        auto tv = clk::now();
         if (physical) {
             rc = lbm_set_fields(h, s->pred, s->pred + P, s->pred + 2 * P, s->pred + 3 * P, 1);
             if (rc) return rc;
+            SCK(cudaStreamSynchronize(hs));
+            tv = clk::now();
             // the LB re-runs from the surrogate state: a state it cannot
             // advance (non-finite or non-positive density) is a rejected jump
             if (verify_steps > 0) {
@@ -526,12 +539,16 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
                 else if (rc) return rc;
             }
         }
-        auto t1 = std::chrono::steady_clock::now();
-        t_sur += std::chrono::duration<double, std::milli>(t1 - t0).count();
+        auto t1 = clk::now();
+        t_ver += ms(tv, t1);
+        t_judge += ms(tn, tv);
         n_div += diverged ? 1.0 : 0.0;
         if (physical && !diverged) {
             rc = lbm_conservation(h, c1);
             if (rc) return rc;
+            const auto t2 = clk::now();
+            t_judge += ms(t1, t2);
+            t1 = t2;
             dm = std::fabs(c1[0] / c0[0] - 1.0);
             de = std::fabs(c1[4] / c0[4] - 1.0);
             // mean interface displacement: the area that changed phase over the interface length
@@ -555,16 +572,20 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
             if (rc) return rc;
             t_lb += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t2).count();
             fb += 1;
+            have_c0 = false;
         } else {
             acc += 1;
             max_dm = std::max(max_dm, dm);
             max_de = std::max(max_de, de);
+            std::memcpy(c0, c1, sizeof c0);
+            have_c0 = true;
         }
     }
+    t_sur = t_net + t_judge + t_ver;
     if (stats) {
         stats[0] = acc; stats[1] = fb; stats[2] = t_sur; stats[3] = t_lb; stats[4] = max_dm; stats[5] = max_de;
         stats[6] = all_dm; stats[7] = all_de; stats[8] = all_da; stats[9] = n_bad;
-        stats[10] = n_div;
+        stats[10] = n_div; stats[11] = t_prep; stats[12] = t_net; stats[13] = t_judge; stats[14] = t_ver;
     }
     return LBM_OK;
 }

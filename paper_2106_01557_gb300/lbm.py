@@ -473,14 +473,16 @@ class Surrogate:
         if verify_steps is None:
             verify_steps = max(1, self.K // 10)
         self.verify_steps = int(verify_steps)
-        stats = np.zeros(11)
+        stats = np.zeros(15)
         _check(self.lib.lbm_surrogate_rollout(self.h, lattice.h, int(njumps), int(verify_steps), float(drift_tol),
                                               float(iface_tol), _host_ptr(stats)))
         return {"accepted": int(stats[0]), "fallbacks": int(stats[1]), "ms_surrogate": stats[2],
                 "ms_fallback_lb": stats[3], "max_mass_drift": stats[4], "max_energy_drift": stats[5],
                 "max_mass_drift_all": stats[6], "max_energy_drift_all": stats[7],
                 "max_iface_displacement_all": stats[8], "unphysical": int(stats[9]),
-                "verify_diverged": int(stats[10]), "verify_steps": int(verify_steps)}
+                "verify_diverged": int(stats[10]), "verify_steps": int(verify_steps),
+                "ms_read_state": stats[11], "ms_network": stats[12], "ms_check_reinit": stats[13],
+                "ms_verify": stats[14]}
 
 
 def surrogate_params_from_oracle_layout(p):

@@ -223,6 +223,9 @@ def rollout_study(sur, p, size=1024, njumps=10, K=50, tol=1e-3, iface_tol=0.5, s
     return {"size": size, "jumps": njumps, "K": K, "verify_steps": kv, "drift_tol": tol, "iface_tol": iface_tol,
             "lb_s": t_lb, "surrogate_path_s": t_sur, "speedup_vs_lb": t_lb / t_sur,
             "accepted": st["accepted"], "fallbacks": st["fallbacks"],
+            "ms_in_rollout": {"read_state": st["ms_read_state"], "network": st["ms_network"],
+                              "check_and_reinit": st["ms_check_reinit"], "verify_steps": st["ms_verify"],
+                              "fallback_lb": st["ms_fallback_lb"]},
             "ms_per_jump_network_only": 1e3 * t_fwd, "ms_per_jump_network_mma_sync": 1e3 * t_fwd_mma,
             "network_forward": {"flops": flops, "bytes": nbytes, "tflops": flops / t_fwd / 1e12,
                                 "gbs": nbytes / t_fwd / 1e9},

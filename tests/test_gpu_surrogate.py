@@ -103,10 +103,13 @@ def test_mass_layer_keeps_each_images_mass(gpu_lib):
 
 @pytest.mark.parametrize("conserve_mass", [False, True])
 @pytest.mark.parametrize("conv_path", PATHS)
-def test_gradients_match_oracle(gpu_lib, conv_path, conserve_mass):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_gradients_match_oracle(gpu_lib, conv_path, conserve_mass, shape):
+    # every weight and bias gradient; the second shape has several 128-pixel
+    # strips with a ragged 16-pixel tail and more row chunks than CTAs
     S, p, s = _make(seed=3, conv_path=conv_path, conserve_mass=conserve_mass)
-    x = _fields(2, 8, 32, 4)
-    t = x + 0.3 * _fields(2, 8, 32, 5)
+    x = _fields(*shape, 4)
+    t = x + 0.3 * _fields(*shape, 5)
     y_ref, cache = S.forward(p, x, conserve_mass)
     g_ref = S.flatten(S.backward(p, cache, y_ref, t))
     loss, g = s.loss_grad(_to_dev(x), _to_dev(t))
