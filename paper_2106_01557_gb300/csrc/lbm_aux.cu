@@ -1,7 +1,9 @@
 // Kernels around the time step: initial populations from macroscopic fields,
 // population import/export, and the macroscopic fields / conservation record
-// of the current state. All of them compute in FP64 and convert to the
-// storage type at the end; none is on the per-step path.
+// of the current state. They compute in FP64 and convert to the storage type
+// at the end; k_init, k_rho and k_moments also come in an FP32 form for
+// 32- and 16-bit storage (per-node arithmetic in FP32, sums in FP64), which
+// the surrogate rollout uses. None is on the per-step path.
 //
 // Addressing: the stored state holds post-collision populations; the
 // post-streaming population l_i(x) sits at x - e_i (pull streaming,
@@ -31,6 +33,19 @@ __device__ __forceinline__ S to_store(double v, double rest) {
     else return (S)v;
 }
 
+// load_d / to_store in the compute type C (identical to them for C = double)
+template <class S, class C>
+__device__ __forceinline__ C load_c(const S* buf, const Geometry& G, int p, int x, int y, C rest) {
+    const S v = buf[(long long)p * G.plane + (long long)(y + 2) * G.pitch + G.PX + x];
+    if constexpr (sizeof(S) == 2) return rest + (C)Store<S, float>::ld(v, 0.0f);
+    else return (C)v;
+}
+template <class S, class C>
+__device__ __forceinline__ S to_store_c(C v, C rest) {
+    if constexpr (sizeof(S) == 2) return Store<S, float>::st((float)(v - rest), 0.0f);
+    else return (S)v;
+}
+
 __device__ __forceinline__ int ex_of(int i) {
     return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
 }
@@ -55,32 +70,32 @@ __device__ __forceinline__ double rho_nb(const double* rho, const Geometry& G, i
     return rho[(long long)y * G.nx + x];
 }
 
-template <class S>
+template <class S, class C>
 __global__ void k_init(const Launch L, const double* __restrict__ rho, const double* __restrict__ ux,
                        const double* __restrict__ uy, const double* __restrict__ T, S* __restrict__ buf) {
     const Geometry& G = L.geo;
-    const KC<double>& k = L.kd;
+    const KC<C>& k = kc<C>(L);
     const long long n = (long long)G.nx * G.ny;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(idx % G.nx), y = (int)(idx / G.nx);
-        NodeMacro<double> s;
-        double rn[9];
+        NodeMacro<C> s;
+        C rn[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) rn[i] = rho_nb(rho, G, x + ex_of(i), y + ey_of(i));
-        const double r = rho[idx];
+        for (int i = 0; i < 9; ++i) rn[i] = (C)rho_nb(rho, G, x + ex_of(i), y + ey_of(i));
+        const C r = (C)rho[idx], vx = (C)ux[idx], vy = (C)uy[idx];
         s.rho = r;
-        s.inv_rho = 1.0 / r;
-        s.gx = (rn[1] - rn[3]) / 3.0 + ((rn[5] - rn[7]) + (rn[8] - rn[6])) / 12.0;
-        s.gy = (rn[2] - rn[4]) / 3.0 + ((rn[5] - rn[7]) + (rn[6] - rn[8])) / 12.0;
+        s.inv_rho = C(1) / r;
+        s.gx = (rn[1] - rn[3]) / C(3) + ((rn[5] - rn[7]) + (rn[8] - rn[6])) / C(12);
+        s.gy = (rn[2] - rn[4]) / C(3) + ((rn[5] - rn[7]) + (rn[6] - rn[8])) / C(12);
         s.Fhx = k.G2c * r * s.gx + r * k.axc;
         s.Fhy = k.G2c * r * s.gy + r * k.ayc;
-        s.uhx = ux[idx] / k.c;
-        s.uhy = uy[idx] / k.c;
+        s.uhx = vx / k.c;
+        s.uhy = vy / k.c;
         s.q = k.c2 * (s.Fhx * s.uhx + s.Fhy * s.uhy);
-        s.T = T[idx];
-        s.rek = r * k.cv * s.T + 0.5 * r * (ux[idx] * ux[idx] + uy[idx] * uy[idx]);
-        double meq[9], Fm[9], neq[9], qm[9], m[9], nn[9], f[9], g[9];
+        s.T = (C)T[idx];
+        s.rek = r * k.cv * s.T + C(0.5) * r * (vx * vx + vy * vy);
+        C meq[9], Fm[9], neq[9], qm[9], m[9], nn[9], f[9], g[9];
         equilibria(k, s, meq, Fm, neq, qm);
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
@@ -91,8 +106,8 @@ __global__ void k_init(const Launch L, const double* __restrict__ rho, const dou
         populations9(nn, g);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            scatter<S>(buf, G, i, i, x, y, to_store<S>(f[i], (double)L.kf.rest[i]));
-            scatter<S>(buf, G, 9 + i, i, x, y, to_store<S>(g[i], (double)L.kf.rest[9 + i]));
+            scatter<S>(buf, G, i, i, x, y, to_store_c<S, C>(f[i], (C)L.kf.rest[i]));
+            scatter<S>(buf, G, 9 + i, i, x, y, to_store_c<S, C>(g[i], (C)L.kf.rest[9 + i]));
         }
     }
 }
@@ -129,57 +144,57 @@ __global__ void k_get_pops(const Launch L, const S* __restrict__ buf, double* __
     }
 }
 
-template <class S>
+template <class S, class C>
 __global__ void k_rho(const Launch L, const S* __restrict__ buf, double* __restrict__ rho) {
     const Geometry& G = L.geo;
     const long long n = (long long)G.nx * G.ny;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(idx % G.nx), y = (int)(idx / G.nx);
-        double r = 0.0;
+        C r = C(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) r += load_d<S>(buf, G, i, x - ex_of(i), y - ey_of(i), (double)L.kf.rest[i]);
-        rho[idx] = r;
+        for (int i = 0; i < 9; ++i) r += load_c<S, C>(buf, G, i, x - ex_of(i), y - ey_of(i), (C)L.kf.rest[i]);
+        rho[idx] = (double)r;
     }
 }
 
 // Macroscopic fields (Eq. 13, 14) and, if partials != NULL, the FP64
 // conservation record reduced deterministically into stats[0..6].
-template <class S>
+template <class S, class C>
 __global__ void __launch_bounds__(AUX_NT) k_moments(const Launch L, const S* __restrict__ buf,
                                                     const double* __restrict__ rho_f, double* __restrict__ o_rho,
                                                     double* __restrict__ o_ux, double* __restrict__ o_uy,
                                                     double* __restrict__ o_T, double* __restrict__ partials,
                                                     double* __restrict__ stats, unsigned* __restrict__ counter) {
     const Geometry& G = L.geo;
-    const KC<double>& k = L.kd;
+    const KC<C>& k = kc<C>(L);
     const long long n = (long long)G.nx * G.ny;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(idx % G.nx), y = (int)(idx / G.nx);
-        double f[9], g[9], rn[9];
+        C f[9], g[9], rn[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            f[i] = load_d<S>(buf, G, i, x - ex_of(i), y - ey_of(i), (double)L.kf.rest[i]);
-            g[i] = load_d<S>(buf, G, 9 + i, x - ex_of(i), y - ey_of(i), (double)L.kf.rest[9 + i]);
-            rn[i] = rho_nb(rho_f, G, x + ex_of(i), y + ey_of(i));
+            f[i] = load_c<S, C>(buf, G, i, x - ex_of(i), y - ey_of(i), (C)L.kf.rest[i]);
+            g[i] = load_c<S, C>(buf, G, 9 + i, x - ex_of(i), y - ey_of(i), (C)L.kf.rest[9 + i]);
+            rn[i] = (C)rho_nb(rho_f, G, x + ex_of(i), y + ey_of(i));
         }
-        NodeMacro<double> s;
+        NodeMacro<C> s;
         node_macro(k, f, g, rn, s);
-        if (o_rho) o_rho[idx] = s.rho;
-        if (o_ux) o_ux[idx] = s.uhx * k.c;
-        if (o_uy) o_uy[idx] = s.uhy * k.c;
-        if (o_T) o_T[idx] = s.T;
-        const double lap = 2.0 * (((rn[1] + rn[2]) + (rn[3] + rn[4])) / 3.0 +
-                                  ((rn[5] + rn[6]) + (rn[7] + rn[8])) / 12.0 - (5.0 / 3.0) * s.rho);
-        acc[0] += s.rho;
-        acc[1] += s.rho * s.uhx * k.c;
-        acc[2] += s.rho * s.uhy * k.c;
-        acc[3] += s.rek;
-        acc[4] += s.rek - k.a * s.rho * s.rho - k.half_kappa * s.rho * lap;
-        acc[5] = fmax(acc[5], k.c2 * (s.uhx * s.uhx + s.uhy * s.uhy));
-        if (!(s.rho > 0.0) || !isfinite(s.rho)) acc[6] += 1.0;
+        if (o_rho) o_rho[idx] = (double)s.rho;
+        if (o_ux) o_ux[idx] = (double)(s.uhx * k.c);
+        if (o_uy) o_uy[idx] = (double)(s.uhy * k.c);
+        if (o_T) o_T[idx] = (double)s.T;
+        const C lap = C(2) * (((rn[1] + rn[2]) + (rn[3] + rn[4])) / C(3) +
+                              ((rn[5] + rn[6]) + (rn[7] + rn[8])) / C(12) - (C(5) / C(3)) * s.rho);
+        acc[0] += (double)s.rho;
+        acc[1] += (double)(s.rho * s.uhx * k.c);
+        acc[2] += (double)(s.rho * s.uhy * k.c);
+        acc[3] += (double)s.rek;
+        acc[4] += (double)(s.rek - k.a * s.rho * s.rho - k.half_kappa * s.rho * lap);
+        acc[5] = fmax(acc[5], (double)(k.c2 * (s.uhx * s.uhx + s.uhy * s.uhy)));
+        if (!(s.rho > C(0)) || !isfinite((double)s.rho)) acc[6] += 1.0;
     }
     if (!partials) return;
     __shared__ double red[AUX_NT / 32][7];
@@ -206,13 +221,32 @@ __global__ void __launch_bounds__(AUX_NT) k_moments(const Launch L, const S* __r
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (tid == 0) {
-        double t[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            const volatile double* pp = partials + (size_t)b * NQ;
-            for (int q = 0; q < 7; ++q) t[q] = (q == 5) ? fmax(t[q], pp[q]) : t[q] + pp[q];
+    // every thread combines the blocks tid, tid + AUX_NT, ... (independent L2
+    // loads), then a fixed-order tree over the threads: the same record on
+    // every run
+    double t[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (unsigned b = tid; b < gridDim.x; b += AUX_NT)
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const double pv = __ldcg(partials + (size_t)b * NQ + q);
+            t[q] = (q == 5) ? fmax(t[q], pv) : t[q] + pv;
         }
-        for (int q = 0; q < 7; ++q) stats[q] = (q == 5) ? sqrt(t[q]) : t[q];
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, t[q], o);
+            t[q] = (q == 5) ? fmax(t[q], w) : t[q] + w;
+        }
+    __syncthreads();  // red[] of the block pass is no longer needed
+    if (lane == 0)
+        for (int q = 0; q < 7; ++q) red[warp][q] = t[q];
+    __syncthreads();
+    if (tid == 0) {
+        double u[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < AUX_NT / 32; ++w)
+            for (int q = 0; q < 7; ++q) u[q] = (q == 5) ? fmax(u[q], red[w][q]) : u[q] + red[w][q];
+        for (int q = 0; q < 7; ++q) stats[q] = (q == 5) ? sqrt(u[q]) : u[q];
         *counter = 0u;
     }
 }
@@ -225,9 +259,16 @@ int aux_blocks(const Geometry& g) {
 
 template <class S>
 struct AuxT {
+    // fast: FP32 per-node arithmetic (32- and 16-bit storage only)
     static cudaError_t init(const Launch& L, const double* rho, const double* ux, const double* uy, const double* T,
-                            void* buf, cudaStream_t s) {
-        k_init<S><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, rho, ux, uy, T, static_cast<S*>(buf));
+                            void* buf, cudaStream_t s, bool fast) {
+        if constexpr (sizeof(S) < 8) {
+            if (fast) {
+                k_init<S, float><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, rho, ux, uy, T, static_cast<S*>(buf));
+                return cudaGetLastError();
+            }
+        }
+        k_init<S, double><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, rho, ux, uy, T, static_cast<S*>(buf));
         return cudaGetLastError();
     }
     static cudaError_t set(const Launch& L, const double* f, const double* g, void* buf, cudaStream_t s) {
@@ -240,10 +281,18 @@ struct AuxT {
     }
     static cudaError_t moments(const Launch& L, const void* buf, double* rho_scratch, double* rho, double* ux,
                                double* uy, double* T, double* partials, double* stats, unsigned* counter,
-                               cudaStream_t s) {
-        k_rho<S><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, static_cast<const S*>(buf), rho_scratch);
-        k_moments<S><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, static_cast<const S*>(buf), rho_scratch, rho, ux, uy, T,
-                                                         partials, stats, counter);
+                               cudaStream_t s, bool fast) {
+        if constexpr (sizeof(S) < 8) {
+            if (fast) {
+                k_rho<S, float><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, static_cast<const S*>(buf), rho_scratch);
+                k_moments<S, float><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, static_cast<const S*>(buf), rho_scratch,
+                                                                        rho, ux, uy, T, partials, stats, counter);
+                return cudaGetLastError();
+            }
+        }
+        k_rho<S, double><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, static_cast<const S*>(buf), rho_scratch);
+        k_moments<S, double><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, static_cast<const S*>(buf), rho_scratch, rho, ux,
+                                                                 uy, T, partials, stats, counter);
         return cudaGetLastError();
     }
 };
@@ -262,8 +311,8 @@ int moments_blocks(const Geometry& g) { return aux_blocks(g); }
     return cudaErrorInvalidValue;
 
 cudaError_t launch_init(int storage, const Launch& L, const double* rho, const double* ux, const double* uy,
-                        const double* T, void* buf, cudaStream_t s) {
-    LBM_DISPATCH(storage, init(L, rho, ux, uy, T, buf, s))
+                        const double* T, void* buf, cudaStream_t s, bool fast) {
+    LBM_DISPATCH(storage, init(L, rho, ux, uy, T, buf, s, fast))
 }
 cudaError_t launch_set_pops(int storage, const Launch& L, const double* f, const double* g, void* buf,
                             cudaStream_t s) {
@@ -274,8 +323,8 @@ cudaError_t launch_get_pops(int storage, const Launch& L, const void* buf, doubl
 }
 cudaError_t launch_moments(int storage, const Launch& L, const void* buf, double* rho_scratch, double* rho,
                            double* ux, double* uy, double* T, double* partials, double* stats, unsigned* counter,
-                           cudaStream_t s) {
-    LBM_DISPATCH(storage, moments(L, buf, rho_scratch, rho, ux, uy, T, partials, stats, counter, s))
+                           cudaStream_t s, bool fast) {
+    LBM_DISPATCH(storage, moments(L, buf, rho_scratch, rho, ux, uy, T, partials, stats, counter, s, fast))
 }
 
 }  // namespace lbm

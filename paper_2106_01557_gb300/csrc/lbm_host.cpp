@@ -1107,6 +1107,31 @@ int lbm_internal_snapshot(lbm_handle* h, void* dst) {
     return LBM_OK;
 }
 
+int lbm_internal_set_fields_fast(lbm_handle* h, const double* fields) {
+    const size_t n = (size_t)h->cfg.nx * h->cfg.ny;
+    const size_t bytes = (size_t)18 * h->L.geo.plane * h->esize;
+    CK(cudaMemsetAsync(h->buf[0], 0, bytes, h->stream));
+    CK(launch_init(h->storage, h->L, fields, fields + n, fields + 2 * n, fields + 3 * n, h->buf[0], h->stream, true));
+    h->cur = 0;
+    return check_status(h);
+}
+
+int lbm_internal_read_fast(lbm_handle* h, double* fields, double out[6]) {
+    const size_t n = (size_t)h->cfg.nx * h->cfg.ny;
+    double* d[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (fields)
+        for (int k = 0; k < 4; ++k) d[k] = fields + k * n;
+    CK(launch_moments(h->storage, h->L, h->buf[h->cur], h->scratch, d[0], d[1], d[2], d[3], h->partials,
+                      h->stats + NQ, h->counter + 1, h->stream, true));
+    double st[NQ];
+    CK(cudaMemcpyAsync(st, h->stats + NQ, NQ * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int rc = check_status(h);
+    if (rc) return rc;
+    for (int k = 0; k < 6; ++k) out[k] = st[k];
+    if (st[6] > 0) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density");
+    return LBM_OK;
+}
+
 int lbm_internal_restore(lbm_handle* h, const void* src) {
     CK(cudaMemcpyAsync(h->buf[h->cur], src, lbm_internal_state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
     return LBM_OK;

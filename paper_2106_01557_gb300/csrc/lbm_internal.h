@@ -70,15 +70,17 @@ int step_blocks(int storage, const Geometry& g);
 size_t step_smem_bytes(int storage);
 cudaError_t prepare_step(int storage);  // per-device kernel attributes; call before capture
 
+// fast: FP32 per-node arithmetic for 32- and 16-bit storage (sums in FP64);
+// FP64 storage always computes in FP64
 cudaError_t launch_init(int storage, const Launch& L, const double* rho, const double* ux,
-                        const double* uy, const double* T, void* buf, cudaStream_t s);
+                        const double* uy, const double* T, void* buf, cudaStream_t s, bool fast = false);
 cudaError_t launch_set_pops(int storage, const Launch& L, const double* f, const double* g, void* buf,
                             cudaStream_t s);
 cudaError_t launch_get_pops(int storage, const Launch& L, const void* buf, double* f, double* g,
                             cudaStream_t s);
 cudaError_t launch_moments(int storage, const Launch& L, const void* buf, double* rho_scratch,
                            double* rho, double* ux, double* uy, double* T, double* partials,
-                           double* stats, unsigned* counter, cudaStream_t s);
+                           double* stats, unsigned* counter, cudaStream_t s, bool fast = false);
 int moments_blocks(const Geometry& g);
 
 // Conservation record of caller-owned [9][ny][nx] FP64 populations with all
@@ -95,5 +97,11 @@ int lbm_internal_fail(int code, const char* msg);
 size_t lbm_internal_state_bytes(const lbm_handle* h);
 int lbm_internal_snapshot(lbm_handle* h, void* dst);       // device copy of the current state
 int lbm_internal_restore(lbm_handle* h, const void* src);  // and back
+// lbm_set_fields from device fields [4][n] with FP32 per-node arithmetic
+// (32- and 16-bit storage), synchronous
+int lbm_internal_set_fields_fast(lbm_handle* h, const double* fields);
+// the fields [4][n] (device, may be null) and the conservation record of the
+// current state in one FP32 pass (sums in FP64), synchronous
+int lbm_internal_read_fast(lbm_handle* h, double* fields, double out[6]);
 cudaStream_t lbm_internal_stream(const lbm_handle* h);
 void lbm_internal_rho_bounds(const lbm_handle* h, double* rho_v, double* rho_l, int* nx, int* ny);

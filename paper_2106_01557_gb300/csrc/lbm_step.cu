@@ -318,15 +318,25 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (tid < 7) {
-        const int q = tid;
+    // warp q < 7 combines quantity q: lane l takes blocks l, l + 32, ...
+    // (independent L2 loads), then a butterfly; a fixed order, so the
+    // record is the same on every run
+    if (warp < 7) {
+        const int q = warp;
         double t = 0.0;
-        for (unsigned b = 0; b < nblocks; ++b) {
-            const double pv = ((volatile double*)partials)[(size_t)b * NQ + q];
+        for (unsigned b = lane; b < nblocks; b += 32) {
+            const double pv = __ldcg(partials + (size_t)b * NQ + q);
             t = (q == 5) ? fmax(t, pv) : t + pv;
         }
-        stats[q] = (q == 5) ? sqrt(t) : t;
-        if (q == 6 && t > 0.0) atomicOr(status, ST_NONFINITE);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, t, o);
+            t = (q == 5) ? fmax(t, w) : t + w;
+        }
+        if (lane == 0) {
+            stats[q] = (q == 5) ? sqrt(t) : t;
+            if (q == 6 && t > 0.0) atomicOr(status, ST_NONFINITE);
+        }
     }
     __syncthreads();
     if (tid == 0) {
