@@ -115,6 +115,24 @@ class ClockSampler:
 
 METRIC = "MLUPS of the fused f+g step (FP32 plain)"
 
+# DRAM bytes (read + write) of one k_step launch on this workload, from one
+# ncu capture (profiles/k_step_f32_4096x1024_full.md), valid only for the
+# kernel sources it was taken on: any change to them makes it null.
+STEP_TRAFFIC = {"bytes_per_launch": 309331712 + 255340032,
+                "sources_sha256": "68606f42395c25bde68459b510edde8ffa5f46d061cc3f5a4d2a055e14bcf0e2"}
+STEP_SOURCES = ["lbm_step.cu", "lbm_device.cuh", "lbm_internal.h", "lbm_ptx.cuh"]
+
+
+def step_traffic():
+    """The captured traffic per launch, or None once the kernel changed."""
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2106_01557_gb300", "csrc")
+    for f in STEP_SOURCES:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    return STEP_TRAFFIC["bytes_per_launch"] if h.hexdigest() == STEP_TRAFFIC["sources_sha256"] else None
+
 
 def slowest_rank_ms(ms, world, device):
     """The whole-job clock: the largest of the ranks' timed durations
@@ -463,7 +481,7 @@ def main():
                   "bf16s": "bf16 storage / f32 math"}[args.precision],
         "data": "synthetic", "config": config,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_kind": kind,
+                     "frac": achieved / hbm, "traffic": step_traffic(), "traffic_unit": "DRAM bytes per launch (ncu capture)", "peak_kind": kind,
                      "algorithmic_bytes_per_lu": res["bytes_step"] / (NX * NY),
                      "timing": "CUDA events over the timed steps on the launching stream / steps"},
         "gpu_launches": args.steps,
