@@ -226,6 +226,18 @@ def run_ours(args, rank, world):
         if args.surrogate_iters:
             from paper_2106_01557_gb300 import surrogate as sur_mod
             variants["surrogate"] = sur_mod.study(iters=args.surrogate_iters)
+            # the same study at longer jumps: the network's cost stays, the LB's grows with K
+            scan = []
+            for K in [int(k) for k in args.surrogate_ks.split(",") if k]:
+                st = sur_mod.study(iters=args.surrogate_iters, K=K)
+                ro = st["rollout"]
+                scan.append({"K": K, "holdout_gain_vs_persistence": st["holdout_gain_vs_persistence"],
+                             "accepted": ro.get("accepted"), "fallbacks": ro.get("fallbacks"),
+                             "speedup_vs_lb": ro.get("speedup_vs_lb"),
+                             "ms_per_jump_network_only": ro.get("ms_per_jump_network_only"),
+                             "ms_per_jump_lb_steps": ro.get("ms_per_jump_lb_steps"),
+                             "err_vs_lb": ro.get("err_vs_lb"), "error": ro.get("error")})
+            variants["surrogate_k_scan"] = scan
     return {"ms_step": ms_step, "mlups": mlups, "bytes_step": bytes_step, "clocks": clk.summary(),
             "e2e": e2e, "stats": stats.tolist(), "variants": variants}
 
@@ -426,6 +438,8 @@ def main():
     ap.add_argument("--batch-study", type=int, default=0,
                     help="run the 256-case sweep for this many steps and report coexistence per case")
     ap.add_argument("--batch-precision", default="f16s", choices=["f32", "f16s", "bf16s"])
+    ap.add_argument("--surrogate-ks", default="100,200",
+                    help="jump lengths K of the extra surrogate studies (comma list; empty: none)")
     ap.add_argument("--surrogate-iters", type=int, default=3000,
                     help="training iterations of the surrogate study in the default run (0: skip)")
     ap.add_argument("--nx", type=int, default=NX, help="smaller lattice for profiling captures")
