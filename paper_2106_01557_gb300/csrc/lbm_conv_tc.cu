@@ -364,8 +364,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int i = tid + j * TC_EPI_THREADS;
                     const int p = i / (COUT / 8), g8 = i % (COUT / 8);
                     if (i >= Cf::N16 || p >= nvalid) continue;
-                    const float4 lo = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * ((2 * g8) ^ (p & Cf::SWZ)));
-                    const float4 hi = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * ((2 * g8 + 1) ^ (p & Cf::SWZ)));
+                    // the two FP32 chunks 2 g8 and 2 g8 + 1, read first the one that puts the
+                    // 8 threads of a shared-memory phase on 8 different bank groups
+                    const int c1 = 2 * g8 + (g8 >> 2) % 2, c2 = 2 * g8 + 1 - (g8 >> 2) % 2;
+                    const float4 q1 = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * (c1 ^ (p & Cf::SWZ)));
+                    const float4 q2 = *reinterpret_cast<const float4*>(tile + p * COUT + 4 * (c2 ^ (p & Cf::SWZ)));
+                    const float4 lo = c1 < c2 ? q1 : q2, hi = c1 < c2 ? q2 : q1;
                     float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
                     if (mask) {
                         const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(&mreg[j]);
