@@ -84,6 +84,12 @@ def test_default_config_and_argument_errors_without_gpu(lib):
     assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
     bad = lbm.default_config(64, 32, Tr0=1.2)
     assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
+    # size limits: at least 8 x 8 nodes, at most 2^31 nodes (rejected before any device call)
+    bad = lbm.default_config(64, 7)
+    assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad = lbm.default_config(65536, 32769)
+    assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
+    assert b"too large" in l.lbm_last_error()
 
 
 def test_library_maxwell_matches_oracle_on_host(lib):
