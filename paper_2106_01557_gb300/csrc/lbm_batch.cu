@@ -148,7 +148,6 @@ __global__ void __launch_bounds__(T::NT, 1)
         const BatchCase& cs = *reinterpret_cast<const BatchCase*>(smem + T::C_OFF + stage * T::C_BYTES);
         const Geometry& G = cs.geo;
         S* out = arena_out + cs.off;
-        const float* rest = k.rest;
         float a_mass = 0.f, a_mx = 0.f, a_my = 0.f, a_ek = 0.f, a_et = 0.f, a_u2 = 0.f, a_bad = 0.f;
 
         const int lx = tid % BX;
@@ -163,12 +162,12 @@ __global__ void __launch_bounds__(T::NT, 1)
             const float* pr = srho + (ly + 1) * RX + lx + 1;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                f[i] = Store<S, C>::ld(pf[i * FR * WX - bey(i) * WX - bex(i)], rest[i]);
-                g[i] = Store<S, C>::ld(pg[i * GR * WX - bey(i) * WX - bex(i)], rest[9 + i]);
+                f[i] = Store<S, C>::raw(pf[i * FR * WX - bey(i) * WX - bex(i)]);
+                g[i] = Store<S, C>::raw(pg[i * GR * WX - bey(i) * WX - bex(i)]);
                 rn[i] = pr[bey(i) * RX + bex(i)];
             }
             NodeMacro<float> s;
-            node_macro(k, f, g, rn, s);
+            node_macro<Store<S, C>::SHIFTED>(k, f, g, rn, s);
             {
                 const float rho = s.rho;
                 a_mass += rho;
@@ -182,20 +181,21 @@ __global__ void __launch_bounds__(T::NT, 1)
                 a_u2 = fmaxf(a_u2, u2);
                 if (!(rho > 0.f && rho < 1e30f && u2 < 1e30f)) a_bad += 1.f;  // also catches NaN
             }
-            collide(k, f, g, s);
+            // shifted formats: f and g leave the collision as deviations from the rest populations
+            collide<Store<S, C>::SHIFTED>(k, f, g, s);
             const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
             if (interior) {
                 S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    o[i * G.plane] = Store<S, C>::st(f[i], rest[i]);
-                    o[(9 + i) * G.plane] = Store<S, C>::st(g[i], rest[9 + i]);
+                    o[i * G.plane] = Store<S, C>::cvt(f[i]);
+                    o[(9 + i) * G.plane] = Store<S, C>::cvt(g[i]);
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    put<S>(out, G, i, x, y, Store<S, C>::st(f[i], rest[i]));
-                    put<S>(out, G, 9 + i, x, y, Store<S, C>::st(g[i], rest[9 + i]));
+                    put<S>(out, G, i, x, y, Store<S, C>::cvt(f[i]));
+                    put<S>(out, G, 9 + i, x, y, Store<S, C>::cvt(g[i]));
                 }
             }
         }

@@ -13,25 +13,41 @@ namespace lbm {
 // ---- storage <-> compute ---------------------------------------------------
 template <class S, class C>
 struct Store;
+// ld / st convert a stored population to / from its value; raw / cvt only
+// convert, leaving the rest population to the caller (shifted formats add it
+// in moment space, where it touches three moments instead of nine values).
+// SHIFTED marks the formats that store deviations from the rest state.
 template <>
 struct Store<double, double> {
+    static constexpr bool SHIFTED = false;
     static __device__ __forceinline__ double ld(double v, double) { return v; }
     static __device__ __forceinline__ double st(double v, double) { return v; }
+    static __device__ __forceinline__ double raw(double v) { return v; }
+    static __device__ __forceinline__ double cvt(double v) { return v; }
 };
 template <>
 struct Store<float, float> {
+    static constexpr bool SHIFTED = false;
     static __device__ __forceinline__ float ld(float v, float) { return v; }
     static __device__ __forceinline__ float st(float v, float) { return v; }
+    static __device__ __forceinline__ float raw(float v) { return v; }
+    static __device__ __forceinline__ float cvt(float v) { return v; }
 };
 template <>
 struct Store<__half, float> {
+    static constexpr bool SHIFTED = true;
     static __device__ __forceinline__ float ld(__half v, float rest) { return rest + __half2float(v); }
     static __device__ __forceinline__ __half st(float v, float rest) { return __float2half_rn(v - rest); }
+    static __device__ __forceinline__ float raw(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half cvt(float v) { return __float2half_rn(v); }
 };
 template <>
 struct Store<__nv_bfloat16, float> {
+    static constexpr bool SHIFTED = true;
     static __device__ __forceinline__ float ld(__nv_bfloat16 v, float rest) { return rest + __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 st(float v, float rest) { return __float2bfloat16_rn(v - rest); }
+    static __device__ __forceinline__ float raw(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 cvt(float v) { return __float2bfloat16_rn(v); }
 };
 
 // Reciprocal: IEEE in FP64; in FP32 the hardware approximation (relative
@@ -104,11 +120,20 @@ struct NodeMacro {
     C m[9], n[9];
 };
 
-template <class C, class K>
+// SH: f and g hold deviations from the rest populations; their moments get
+// the rest moments added back (moments 0-2, the others vanish).
+template <bool SH = false, class C, class K>
 __device__ __forceinline__ void node_macro(const K& k, const C f[9], const C g[9], const C rn[9],
                                            NodeMacro<C>& s) {
     moments9(f, s.m);
     moments9(g, s.n);
+    if constexpr (SH) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            s.m[q] += k.mrest[q];
+            s.n[q] += k.nrest[q];
+        }
+    }
     const C rho = rn[0];
     // Eq. 13 weights: 1/3 on the axes, 1/12 on the diagonals
     const C third = C(1.0 / 3.0), twelfth = C(1.0 / 12.0);
@@ -193,7 +218,9 @@ __device__ __forceinline__ void equilibria(const KC<C>& k, const NodeMacro<C>& s
 // collision populations. Rows 0, 3, 5 of m - m^eq + dt/2 F_m and row 0 of
 // n - n^eq + dt/2 q_m vanish by Eq. 14, so s_0, s_j and sigma_0 never act
 // and are not applied.
-template <class C, class K>
+// SH: on exit f and g hold the post-collision deviations from the rest
+// populations (the rest moments are taken off before the back-transform).
+template <bool SH = false, class C, class K>
 __device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMacro<C>& s) {
     const C rho = s.rho, ux = s.uhx, uy = s.uhy;
     const C u2 = ux * ux + uy * uy;
@@ -241,6 +268,10 @@ __device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMa
     const C d1 = C(0.5) * (m[1] + mb[1]) - meq1;
     const C d7 = C(0.5) * (m[7] + mb[7]) - meq7;
     const C d8 = C(0.5) * (m[8] + mb[8]) - meq8;
+    if constexpr (SH) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) mb[q] -= k.mrest[q];
+    }
     populations9(mb, f);
 
     // ---- g: n_bar = n + dt q_m - L (n - n^eq + dt/2 q_m) + c^2 Y d -------
@@ -269,6 +300,10 @@ __device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMa
     nb[6] = n[6] - k.dt * quy - sj * z6 - yy;
     nb[7] = n[7] - k.sigp * n[7];
     nb[8] = n[8] - k.sigp * n[8];
+    if constexpr (SH) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) nb[q] -= k.nrest[q];
+    }
     populations9(nb, g);
 }
 

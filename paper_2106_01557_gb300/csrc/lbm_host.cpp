@@ -337,6 +337,7 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     // near zero; liquid nodes then carry deviations of their own size, so
     // both phases keep the format's relative precision.
     for (int i = 0; i < 18; ++i) { L.kf.rest[i] = 0.0f; L.kd.rest[i] = 0.0; }
+    for (int q = 0; q < 3; ++q) { L.kf.mrest[q] = L.kf.nrest[q] = 0.0f; L.kd.mrest[q] = L.kd.nrest[q] = 0.0; }
     if (storage == S_F16 || storage == S_BF16) {
         const double rho = c.rho_ref > 0 ? c.rho_ref : p.rho_v;
         const double T = p.T0;
@@ -361,6 +362,24 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
             L.kf.rest[9 + i] = (float)rg[i];
             L.kd.rest[i] = (double)L.kf.rest[i];
             L.kd.rest[9 + i] = (double)L.kf.rest[9 + i];
+        }
+        // moments 0-2 of the rounded rest populations (M of SM Eq. S2); the
+        // rest state has u = 0, so moments 3-8 vanish exactly (equal axis and
+        // equal diagonal populations)
+        auto m012 = [](const float* r, double* m) {
+            const double ax = (double)r[1] + r[2] + r[3] + r[4], dg = (double)r[5] + r[6] + r[7] + r[8];
+            m[0] = r[0] + ax + dg;
+            m[1] = -4.0 * r[0] - ax + 2.0 * dg;
+            m[2] = 4.0 * r[0] - 2.0 * ax + dg;
+        };
+        double mf[3], mg[3];
+        m012(L.kf.rest, mf);
+        m012(L.kf.rest + 9, mg);
+        for (int q = 0; q < 3; ++q) {
+            L.kf.mrest[q] = (float)mf[q];
+            L.kf.nrest[q] = (float)mg[q];
+            L.kd.mrest[q] = mf[q];
+            L.kd.nrest[q] = mg[q];
         }
     }
     return LBM_OK;

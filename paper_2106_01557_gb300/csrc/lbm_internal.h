@@ -39,6 +39,7 @@ struct KC {
     C c2_third;      // c^2 / 3
     C T_bottom, T_top, T_hot;
     C rest[18];      // shifted-storage rest populations (f 0..8, g 9..17)
+    C mrest[3], nrest[3];  // moments 0-2 of the f and g rest populations (the others vanish)
 };
 
 struct Geometry {

@@ -115,30 +115,36 @@ struct Acc {
 
 // Post-collision populations of node (x, y) into its own slot of the output
 // state (pull scheme), with the periodic ghost copies near the edges and the
-// wall reflections in the rows next to a wall.
+// wall reflections in the rows next to a wall. For shifted formats f and g
+// already hold the deviations from the rest populations.
 template <class S, class C>
 __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
                                            const C f[9], const C g[9], C rho) {
     const C* rest = k.rest;
+    constexpr bool SH = Store<S, C>::SHIFTED;
     const int HX = G.HX;
     const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
     if (interior) {
         S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            o[i * G.plane] = Store<S, C>::st(f[i], rest[i]);
-            o[(9 + i) * G.plane] = Store<S, C>::st(g[i], rest[9 + i]);
+            o[i * G.plane] = Store<S, C>::cvt(f[i]);
+            o[(9 + i) * G.plane] = Store<S, C>::cvt(g[i]);
         }
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            put<S>(out, G, i, x, y, Store<S, C>::st(f[i], rest[i]));
-            put<S>(out, G, 9 + i, x, y, Store<S, C>::st(g[i], rest[9 + i]));
+            put<S>(out, G, i, x, y, Store<S, C>::cvt(f[i]));
+            put<S>(out, G, 9 + i, x, y, Store<S, C>::cvt(g[i]));
         }
     }
     if (G.walls && (y == 0 || y == G.ny - 1)) {
-        if (y == 0) wall_store<S, C>(out, G, k, x, y, f[4], f[7], f[8], g[4], g[7], g[8], rho);
-        else wall_store<S, C>(out, G, k, x, y, f[2], f[5], f[6], g[2], g[5], g[6], rho);
+        // the reflections work on the populations themselves
+        auto a = [&](const C* v, int i, int off) { return SH ? v[i] + rest[off + i] : v[i]; };
+        if (y == 0)
+            wall_store<S, C>(out, G, k, x, y, a(f, 4, 0), a(f, 7, 0), a(f, 8, 0), a(g, 4, 9), a(g, 7, 9), a(g, 8, 9), rho);
+        else
+            wall_store<S, C>(out, G, k, x, y, a(f, 2, 0), a(f, 5, 0), a(f, 6, 0), a(g, 2, 9), a(g, 5, 9), a(g, 6, 9), rho);
     }
 }
 
@@ -185,7 +191,6 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
             if ((int)blockIdx.x + j * (int)gridDim.x < ntiles) issue(blockIdx.x + j * gridDim.x, j);
     }
 
-    const C* rest = k.rest;
     Acc<C> acc = {0, 0, 0, 0, 0, 0, 0};
     bool ok = true;
     int it = 0;
@@ -221,9 +226,10 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
                 else if (gy >= G.ny) sy -= gy - (G.ny - 1);
             }
             const S* p = sf + sy * WX + rx - 1 + HX;
-            C r = C(0);
+            // shifted formats: the rest populations sum to mrest[0]
+            C r = Store<S, C>::SHIFTED ? k.mrest[0] : C(0);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) r += Store<S, C>::ld(p[i * FR * WX - EYf(i) * WX - EXf(i)], rest[i]);
+            for (int i = 0; i < 9; ++i) r += Store<S, C>::raw(p[i * FR * WX - EYf(i) * WX - EXf(i)]);
             srho[idx] = r;
         }
         if (__syncthreads_or(timed_out)) { ok = false; break; }
@@ -244,12 +250,12 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
             const C* pr = srho + (ly + 1) * RX + lx + 1;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                f[i] = Store<S, C>::ld(pf[i * FR * WX - EYf(i) * WX - EXf(i)], rest[i]);
-                g[i] = Store<S, C>::ld(pg[i * GR * WX - EYf(i) * WX - EXf(i)], rest[9 + i]);
+                f[i] = Store<S, C>::raw(pf[i * FR * WX - EYf(i) * WX - EXf(i)]);
+                g[i] = Store<S, C>::raw(pg[i * GR * WX - EYf(i) * WX - EXf(i)]);
                 rn[i] = pr[EYf(i) * RX + EXf(i)];
             }
             NodeMacro<C> s;
-            node_macro(k, f, g, rn, s);
+            node_macro<Store<S, C>::SHIFTED>(k, f, g, rn, s);
             {   // conservation record of the entering state
                 const C rho = s.rho;
                 acc.mass += rho;
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
                 acc.u2max = u2 > acc.u2max ? u2 : acc.u2max;
                 if (!(rho > C(0) && rho < C(1e30) && u2 < C(1e30))) acc.bad += C(1);  // also catches NaN
             }
-            collide(k, f, g, s);
+            collide<Store<S, C>::SHIFTED>(k, f, g, s);
             store_node<S, C>(out, G, k, x, y, f, g, s.rho);
         }
         if (NS == 1) {
