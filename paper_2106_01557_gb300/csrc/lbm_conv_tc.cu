@@ -44,7 +44,7 @@ constexpr int TC_TW = 128;          // pixels per output row segment (MMA M)
 constexpr int TC_EPI_WARPS = 16;    // warps 0 .. TC_EPI_WARPS - 1: copies and epilogue
 constexpr int TC_EPI_THREADS = 32 * TC_EPI_WARPS;
 constexpr int TC_THREADS = TC_EPI_THREADS + 32;  // + one warp: MMA issue
-constexpr int TC_NSLOT = 7;         // input-row ring: 3 rows in use, the rest in flight
+constexpr int TC_NSLOT = 5;         // input-row ring: 3 rows in use, the rest in flight
 
 template <int CIN, int COUT>
 struct TcCfg {
@@ -53,7 +53,8 @@ struct TcCfg {
     static constexpr int GS = (TC_TW + 3) * 16;         // bytes between channel groups
     static constexpr int SLOT_BYTES = KG * GS;
     static constexpr int W_BYTES = 9 * KG * COUT * 16;
-    static constexpr int OUT_BYTES = TC_TW * COUT * 4;  // FP32 staging tile of one output row
+    static constexpr int TILE = TC_TW * COUT;            // FP32 values of one output row
+    static constexpr int OUT_BYTES = 2 * TILE * 4;      // two staging tiles (rows t and t - 1)
     static constexpr int BYTES = TC_NSLOT * SLOT_BYTES + W_BYTES + OUT_BYTES + 128;  // + alignment slack
     static constexpr int ROW_VECS = KG * PIX;           // 16-byte vectors per halo'd row
     static constexpr int VPT = (ROW_VECS + TC_EPI_THREADS - 1) / TC_EPI_THREADS;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int pix = 32 * (warp % 4) + lane;
     const int col0 = (warp / 4) * Cf::EPI_COLS;
     const uint32_t t_lane = tmem + ((uint32_t)(32 * (warp % 4)) << 16);
-    float* tile = reinterpret_cast<float*>(s_out);
+    float* tiles = reinterpret_cast<float*>(s_out);
 
     for (long long r = r_begin; r < r_end && ok;) {
         const int y0 = (int)(r % H);
@@ -293,70 +294,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         };
 
-        if (is_epi) {
-            // prologue: every slot's row in flight; rows 0..2 in place for row 0's MMAs
-#pragma unroll 1
-            for (int li = 0; li < TC_NSLOT; ++li) copy_row(li);
-            prefetch_epi(0);
-            cp_async_wait<TC_NSLOT - 3>();
-            relu_row(0);
-            relu_row(1);
-            relu_row(2);
-            fence_proxy_async();
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == TC_EPI_THREADS) issue(0);
-        pending |= 1u;
-        bool timed_out = false;
-        for (int t = 0; t < L; ++t) {
-            const int y = y0 + t;
-            if (t + 1 < L) {
-                // row li = t + 3 completes the rows of output row t + 1
-                if (is_epi) {
-                    cp_async_wait<TC_NSLOT - 4>();
-                    relu_row(t + 3);
-                    fence_proxy_async();
-                }
-                tc_fence_before();
-                // also: the epilogue of row t - 1 has read accumulator (t + 1) & 1
-                // and every thread has left the staging tile of row t - 1
-                if (__syncthreads_or(timed_out)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                if (tid == TC_EPI_THREADS) issue(t + 1);
-                pending |= 1u << ((t + 1) & 1);
-            }
-            if (!is_epi) continue;
-            const uint32_t b = (uint32_t)(t & 1);
-            if (!bar_wait(&bar[b], (parity >> b) & 1u)) timed_out = true;
-            parity ^= 1u << b;
-            pending &= ~(1u << b);
-            tc_fence_after();
-            // MMA(t) has read its rows: the slot of row t takes row t + TC_NSLOT
-            copy_row(t + TC_NSLOT);
-            // accumulator + bias -> FP32 staging tile (on the run's last row no
-            // block barrier has separated this from the tile's previous readers)
-            if (t + 1 >= L) epi_sync();
-#pragma unroll
-            for (int ch = 0; ch < Cf::EPI_CH; ++ch) {
-                if (warp >= Cf::TW_WARPS) break;
-                const int c = col0 + Cf::NC * ch;
-                float v[16];
-                tc_ld<Cf::NC>(t_lane + b * COUT + (uint32_t)c, v);
-#pragma unroll
-                for (int q = 0; q < Cf::NC / 4; ++q) {
-                    const int k = c / 4 + q;
-                    const float4 bb = *reinterpret_cast<const float4*>(s_bias + 4 * k);
-                    *reinterpret_cast<float4*>(tile + pix * COUT + 4 * (k ^ (pix & Cf::SWZ))) =
-                        make_float4(v[4 * q] + bb.x, v[4 * q + 1] + bb.y, v[4 * q + 2] + bb.z, v[4 * q + 3] + bb.w);
-                }
-            }
-            epi_sync();
-            // staging tile -> global, coalesced 16-byte chunks of the row
+        // staging tile -> global, coalesced 16-byte chunks of output row tr
+        // of the run, applying mask and residual (loaded by prefetch_epi(tr))
+        auto copy_out = [&](int tr, const float* tile) {
+            const int y = y0 + tr;
             const size_t row0 = ((size_t)n * H + y) * W + x0;
             if (out16) {
 #pragma unroll
@@ -409,7 +350,78 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     *reinterpret_cast<float4*>(out32 + (row0 + p) * COUT + 4 * k) = v;
                 }
             }
-            prefetch_epi(t + 1);
+        };
+
+        if (is_epi) {
+            // prologue: every slot's row in flight; rows 0..2 in place for row 0's MMAs
+#pragma unroll 1
+            for (int li = 0; li < TC_NSLOT; ++li) copy_row(li);
+            cp_async_wait<TC_NSLOT - 3>();
+            relu_row(0);
+            relu_row(1);
+            relu_row(2);
+            fence_proxy_async();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == TC_EPI_THREADS) issue(0);
+        pending |= 1u;
+        bool timed_out = false;
+        for (int t = 0; t < L; ++t) {
+            if (t + 1 < L) {
+                // row li = t + 3 completes the rows of output row t + 1
+                if (is_epi) {
+                    cp_async_wait<TC_NSLOT - 4>();
+                    relu_row(t + 3);
+                    fence_proxy_async();
+                }
+                tc_fence_before();
+                // also: the epilogue of row t - 1 has read accumulator (t + 1) & 1
+                // and every thread has left the staging tile of row t - 1
+                if (__syncthreads_or(timed_out)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (tid == TC_EPI_THREADS) issue(t + 1);
+                pending |= 1u << ((t + 1) & 1);
+            }
+            if (!is_epi) continue;
+            const uint32_t b = (uint32_t)(t & 1);
+            if (!bar_wait(&bar[b], (parity >> b) & 1u)) timed_out = true;
+            parity ^= 1u << b;
+            pending &= ~(1u << b);
+            tc_fence_after();
+            // MMA(t) has read its rows: the slot of row t takes row t + TC_NSLOT
+            copy_row(t + TC_NSLOT);
+            // accumulator + bias -> FP32 staging tile t & 1 (on the run's last row
+            // no block barrier has separated this from the tile's previous readers)
+            if (t + 1 >= L) epi_sync();
+            float* tile = tiles + (t & 1) * Cf::TILE;
+#pragma unroll
+            for (int ch = 0; ch < Cf::EPI_CH; ++ch) {
+                if (warp >= Cf::TW_WARPS) break;
+                const int c = col0 + Cf::NC * ch;
+                float v[16];
+                tc_ld<Cf::NC>(t_lane + b * COUT + (uint32_t)c, v);
+#pragma unroll
+                for (int q = 0; q < Cf::NC / 4; ++q) {
+                    const int k = c / 4 + q;
+                    const float4 bb = *reinterpret_cast<const float4*>(s_bias + 4 * k);
+                    *reinterpret_cast<float4*>(tile + pix * COUT + 4 * (k ^ (pix & Cf::SWZ))) =
+                        make_float4(v[4 * q] + bb.x, v[4 * q + 1] + bb.y, v[4 * q + 2] + bb.z, v[4 * q + 3] + bb.w);
+                }
+            }
+            // row t - 1 leaves from the other tile (written in the previous
+            // iteration, one block barrier ago)
+            if (t >= 1) copy_out(t - 1, tiles + ((t - 1) & 1) * Cf::TILE);
+            prefetch_epi(t);  // row t's mask and residual, for its copy-out
+        }
+        // the run's last row (after a timeout every thread has left the loop together)
+        if (ok && is_epi) {
+            epi_sync();
+            copy_out(L - 1, tiles + ((L - 1) & 1) * Cf::TILE);
         }
         // copies still in flight (rows the run does not need) land before the slots are reused
         if (is_epi) cp_async_wait<0>();
