@@ -7,7 +7,7 @@
 // rows of all (image, 128-pixel strip) columns are dealt out to the CTAs in
 // contiguous runs, so a CTA walks down a strip and loads each input row once,
 // into a ring of TC_NSLOT halo'd input rows in shared memory filled by
-// cp.async copies issued TC_NSLOT - 4 rows ahead of their first use (ReLU,
+// cp.async copies issued TC_NSLOT - 3 rows ahead of their first use (ReLU,
 // where the layer wants it, is applied in place by the thread that copied
 // the vector).
 //
@@ -16,10 +16,11 @@
 // MMAs never wait for an epilogue and an epilogue never waits for the issue.
 // Two accumulators in tensor memory let the MMAs of row t + 1 run while the
 // epilogue of row t reads row t out with tcgen05.ld (warp w reads lanes
-// 32 (w % 4) .. + 31 = pixels, a share of the columns), adds the bias and stages FP32 values in
-// a shared tile (16-byte chunks XOR-swizzled by pixel, no bank conflicts);
-// the tile then leaves in coalesced 16-byte stores, where the mask and the
-// residual (loaded one row ahead) are applied.
+// 32 (w % 4) .. + 31 = pixels, a share of the columns), adds the bias and
+// stages FP32 values in one of two shared tiles (16-byte chunks XOR-swizzled
+// by pixel, no bank conflicts); in the next iteration the tile leaves in
+// coalesced 16-byte stores, where the mask and the residual (loaded a row
+// ahead) are applied, while the other tile takes the next row.
 //
 // Shared-memory operand layouts (K-major, no swizzle; a core matrix is 8
 // rows of 16 bytes):
