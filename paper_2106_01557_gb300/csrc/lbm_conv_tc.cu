@@ -7,30 +7,51 @@
 // rows of all (image, 128-pixel strip) columns are dealt out to the CTAs in
 // contiguous runs, so a CTA walks down a strip and loads each input row once,
 // into a ring of TC_NSLOT halo'd input rows in shared memory filled by
-// cp.async copies issued TC_NSLOT - 3 rows ahead of their first use (ReLU,
-// where the layer wants it, is applied in place by the thread that copied
-// the vector).
+// cp.async copies issued TC_NSLOT - 2 rows ahead of their use (ReLU, where
+// the layer wants it, is applied in place by the thread that copied the
+// vector).
+//
+// The MMAs are input-stationary: input row li of a run (image row y0 - 1 +
+// li) feeds output rows t = li - 2, li - 1 and li of the run through taps
+// dy = +1, 0 and -1; the weights of the three dy taps sit side by side in N, so one MMA (M = 128 pixels, N = 3 COUT, K = 16) applies one
+// (dx, 16-channel) step of input row li to all three output rows at once.
+// Output row t accumulates in block t % TC_NBLK of tensor memory (COUT
+// columns each); where the blocks of the rows wrap around, or where a row
+// starts its accumulator (its first step, accumulate flag off), the step is
+// split into two or three MMAs over adjacent blocks. Per output row this
+// reads the input operand 3 CIN / 16 times instead of 9 CIN / 16 and issues
+// about 3 CIN / 16 + 1 MMAs instead of 9 CIN / 16; every output still sums
+// its 9 CIN / 16 K-steps in the order (dy, dx, channel chunk).
 //
 // Roles: warps 0 .. TC_EPI_WARPS - 1 copy, apply ReLU and run the epilogue;
-// the last warp only issues the MMAs (one elected lane), so the next row's
-// MMAs never wait for an epilogue and an epilogue never waits for the issue.
-// Two accumulators in tensor memory let the MMAs of row t + 1 run while the
-// epilogue of row t reads row t out with tcgen05.ld (warp w reads lanes
-// 32 (w % 4) .. + 31 = pixels, a share of the columns), adds the bias and
-// stages FP32 values in one of two shared tiles (16-byte chunks XOR-swizzled
-// by pixel, no bank conflicts); in the next iteration the tile leaves in
-// coalesced 16-byte stores, where the mask and the residual (loaded a row
-// ahead) are applied, while the other tile takes the next row.
+// the last warp only issues the MMAs (one elected lane), so the next input
+// row's MMAs never wait for an epilogue. The epilogue of output row t runs
+// once input row t + 2 is done, while the MMAs of input row t + 3 run: it
+// reads the row out with tcgen05.ld (warp w reads lanes 32 (w % 4) .. + 31
+// = pixels, a share of the columns), adds the bias and stages FP32 values in
+// one of two shared tiles (16-byte chunks XOR-swizzled by pixel, no bank
+// conflicts); in the next iteration the tile leaves in coalesced 16-byte
+// stores, where the mask and the residual (loaded a row ahead) are applied,
+// while the other tile takes the next row.
 //
-// Shared-memory operand layouts (K-major, no swizzle; a core matrix is 8
-// rows of 16 bytes):
-//   input row slot [CIN/8 channel groups][TC_TW + 2 pixels, stride 16 B]
-//     with the channel-group stride GS = (TC_TW + 3) * 16 B. An 8-pixel run
-//     of one group is one core matrix: the window of tap dx is the same
-//     operand with its start moved by (1 + dx) * 16 B.
-//     Descriptor: LBO (next channel group, K) = GS, SBO (next 8 pixels, M) = 128.
-//   weights [9 taps][CIN/8][COUT][8 channels]: LBO = COUT * 16, SBO = 128.
-// One output row = 9 taps x CIN/16 MMAs of M = 128, N = COUT, K = 16.
+// Shared-memory operand layouts (K-major). With CIN = 64 both operands use
+// the tensor core's 128-byte swizzle: one 128-byte row of 64 channels per
+// pixel (A) or per N row (B), the 16-byte chunk c of a row stored at chunk
+// c ^ (row address bits 7-9), 1024-byte atoms of 8 rows (SBO); the K step
+// of 16 channels moves the descriptor start 32 bytes along the rows.
+//   input row slot [TC_TW + 2 pixels][128 B] (1024-byte aligned): the window
+//     of tap dx is the same operand started dx + 1 rows in.
+//   weights [3 dx][3 blocks: dy = +1, 0, -1][COUT][128 B].
+// With CIN = 16 (the lift layer), no swizzle; a core matrix is 8 rows of 16
+// bytes:
+//   input row slot [CIN/8 channel groups][TC_TW + 2 pixels, stride 16 B],
+//     channel-group stride GS = (TC_TW + 3) * 16 B (LBO), SBO = 128; the
+//     window of tap dx starts (1 + dx) * 16 B in.
+//   weights [3 dx][CIN/8][3 blocks][COUT][8 channels]: LBO = 3 COUT * 16,
+//     SBO = 128.
+// The block of tap dy for output row t and input row li is t - li + 2, so
+// adjacent output rows take adjacent blocks in N, as they take adjacent
+// blocks of tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,21 +66,32 @@ constexpr int TC_TW = 128;          // pixels per output row segment (MMA M)
 constexpr int TC_EPI_WARPS = 16;    // warps 0 .. TC_EPI_WARPS - 1: copies and epilogue
 constexpr int TC_EPI_THREADS = 32 * TC_EPI_WARPS;
 constexpr int TC_THREADS = TC_EPI_THREADS + 32;  // + one warp: MMA issue
-constexpr int TC_NSLOT = 5;         // input-row ring: 3 rows in use, the rest in flight
+constexpr int TC_NSLOT = 5;         // input-row ring: 1 row in use, 1 ready, the rest in flight
+constexpr int TC_NBLK = 8;          // accumulator blocks in tensor memory (output rows in flight)
 
 template <int CIN, int COUT>
 struct TcCfg {
     static constexpr int KG = CIN / 8;                  // 8-channel groups
     static constexpr int PIX = TC_TW + 2;               // halo'd pixels per row
     static constexpr int GS = (TC_TW + 3) * 16;         // bytes between channel groups
-    static constexpr int SLOT_BYTES = KG * GS;
-    static constexpr int W_BYTES = 9 * KG * COUT * 16;
+    // input rows: with CIN = 64, one 128-byte row per pixel, 16-byte chunks
+    // swizzled by the pixel's address (the tensor core's 128-byte swizzle);
+    // otherwise no swizzle, channel groups GS bytes apart
+    static constexpr bool ASW = CIN == 64;
+    static constexpr int SLOT_BYTES = ASW ? (PIX * 128 + 1023) / 1024 * 1024 : KG * GS;
+    // weights: with CIN = 64, one 128-byte row of channels per N row, 16-byte
+    // chunks swizzled by the row (the tensor core's 128-byte swizzle);
+    // otherwise no swizzle, channel groups WGS bytes apart
+    static constexpr bool WSW = CIN == 64;
+    static constexpr int WGS = 3 * COUT * 16;
+    static constexpr int WDX = WSW ? 3 * COUT * 128 : KG * WGS;  // bytes per tap dx
+    static constexpr int W_BYTES = 3 * WDX;
     static constexpr int TILE = TC_TW * COUT;            // FP32 values of one output row
     static constexpr int OUT_BYTES = 2 * TILE * 4;      // two staging tiles (rows t and t - 1)
-    static constexpr int BYTES = TC_NSLOT * SLOT_BYTES + W_BYTES + OUT_BYTES + 128;  // + alignment slack
+    static constexpr int BYTES = W_BYTES + TC_NSLOT * SLOT_BYTES + OUT_BYTES + 1024;  // + alignment slack
     static constexpr int ROW_VECS = KG * PIX;           // 16-byte vectors per halo'd row
     static constexpr int VPT = (ROW_VECS + TC_EPI_THREADS - 1) / TC_EPI_THREADS;
-    static constexpr int TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;  // two accumulators, power of two
+    static constexpr int TMEM_COLS = TC_NBLK * COUT < 32 ? 32 : TC_NBLK * COUT;  // power of two
     // warps reading the accumulator (4 per lane quarter group, >= 8 columns each)
     static constexpr int TW_WARPS = TC_EPI_WARPS < COUT / 2 ? TC_EPI_WARPS : COUT / 2;
     static constexpr int EPI_COLS = COUT / (TW_WARPS / 4);  // accumulator columns per reading warp
@@ -70,7 +102,9 @@ struct TcCfg {
     static constexpr int N16 = TC_TW * COUT / 8, N32 = TC_TW * COUT / 4;  // 16-byte output chunks of a row
     static constexpr int O16 = (N16 + TC_EPI_THREADS - 1) / TC_EPI_THREADS;  // BF16 chunks per thread
     static constexpr int O32 = (N32 + TC_EPI_THREADS - 1) / TC_EPI_THREADS;  // FP32 chunks per thread
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "tcgen05 f16 shape");
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && 3 * COUT <= 256, "tcgen05 f16 shape");
+    static_assert((TMEM_COLS & (TMEM_COLS - 1)) == 0 && TC_NBLK >= 4, "accumulator blocks");
+    static_assert(WDX % 1024 == 0, "swizzle atoms of the weights start on 1024-byte boundaries");
     static_assert(TW_WARPS % 4 == 0 && COUT % (TW_WARPS / 4) == 0 && (NC == 8 || NC == 16), "tile split");
     static_assert(TMEM_COLS <= 512, "tensor memory");
     static_assert(BYTES <= 227 * 1024, "shared memory");
@@ -81,6 +115,13 @@ struct TcCfg {
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// the same for a K-major operand in 128-byte swizzled rows: 8-row atoms of
+// 1024 bytes (SBO), LBO unused (16), swizzle mode 2 (bits 61-63)
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
@@ -156,10 +197,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_base;
     __shared__ __align__(16) float s_bias[COUT];
-    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    unsigned char* s_in = smem;
-    unsigned char* s_w = smem + TC_NSLOT * Cf::SLOT_BYTES;
-    unsigned char* s_out = s_w + Cf::W_BYTES;
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char* s_w = smem;
+    unsigned char* s_in = s_w + Cf::W_BYTES;
+    unsigned char* s_out = s_in + TC_NSLOT * Cf::SLOT_BYTES;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const bool is_epi = tid < TC_EPI_THREADS;
 
@@ -175,11 +216,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         fence_mbar_init();
     }
     for (int c = tid; c < COUT; c += TC_THREADS) s_bias[c] = bias ? bias[c] : 0.f;
-    // weights [9][COUT][CIN] -> [9][CIN/8][COUT][8]
+    // weights [9 taps (dy, dx)][COUT][CIN] -> per dx, N rows n = block (dy = +1,
+    // 0, -1) * COUT + co: [3 dx][n][64 channels, chunk kg at kg ^ (n % 8)]
+    // (CIN = 64) or [3 dx][CIN/8][n][8 channels]
     for (int e = tid; e < 9 * COUT * Cf::KG; e += TC_THREADS) {
         const int kg = e % Cf::KG, co = (e / Cf::KG) % COUT, tap = e / (Cf::KG * COUT);
+        const int dyi = tap / 3, dxi = tap % 3, n = (2 - dyi) * COUT + co;
         const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)tap * COUT + co) * CIN + kg * 8);
-        *reinterpret_cast<uint4*>(s_w + ((tap * Cf::KG + kg) * COUT + co) * 16) = v;
+        const int off = Cf::WSW ? dxi * Cf::WDX + n * 128 + ((kg ^ (n & 7)) * 16)
+                                : (dxi * Cf::KG + kg) * Cf::WGS + n * 16;
+        *reinterpret_cast<uint4*>(s_w + off) = v;
     }
     fence_proxy_async();
     tc_fence_before();
@@ -187,16 +233,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     // instruction descriptor: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9,
-    // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22),
-    // M >> 4 (bits 24-28)
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) |
-                           ((uint32_t)(TC_TW >> 4) << 24);
+    // 10-12 = 1), both K-major (bits 15, 16 = 0), M >> 4 (bits 24-28); N >> 3
+    // (bits 17-22) is added per MMA
+    const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_TW >> 4) << 24);
     const uint32_t s_in_addr = smem_u32(s_in), s_w_addr = smem_u32(s_w);
     // descriptors of the weights and of ring slot 0; an operand inside them is
     // the same descriptor with its start moved by a constant (the 14-bit
     // start field stays below 2^14 for any shared-memory address)
-    const uint64_t b_desc0 = sdesc(s_w_addr, COUT * 16, 128);
-    const uint64_t a_desc0 = sdesc(s_in_addr, Cf::GS, 128);
+    const uint64_t b_desc0 = Cf::WSW ? sdesc_sw128(s_w_addr) : sdesc(s_w_addr, Cf::WGS, 128);
+    const uint64_t a_desc0 = Cf::ASW ? sdesc_sw128(s_in_addr) : sdesc(s_in_addr, Cf::GS, 128);
     const int tiles_x = (W + TC_TW - 1) / TC_TW;
     const long long rows_total = (long long)N * tiles_x * H;
     const long long r_begin = rows_total * blockIdx.x / gridDim.x;
@@ -231,7 +276,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             gx = gx < 0 ? gx + W : gx;
             gx = gx >= W ? gx % W : gx;
             src_off[i] = gx * CIN + kg * 8;
-            dst_off[i] = kg * Cf::GS + px * 16;
+            dst_off[i] = Cf::ASW ? px * 128 + ((kg ^ (px & 7)) * 16) : kg * Cf::GS + px * 16;
         }
         // halo'd input row li of this run (input row y0 - 1 + li, periodic)
         // into ring slot li % TC_NSLOT; one commit group per row, empty for
@@ -260,23 +305,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
         };
-        // MMAs of output row t (input rows li = t, t + 1, t + 2) into accumulator t & 1
-        auto issue = [&](int t) {
-            const uint32_t d = tmem + (uint32_t)((t & 1) * COUT);
-            uint64_t a_row[3];
+        // MMAs of input row li (in ring slot li % TC_NSLOT): it feeds output rows
+        // li - 2 (tap dy = +1), li - 1 (dy = 0) and li (dy = -1), those of them in
+        // the run. One MMA per (dx, channel chunk) step covers the rows whose
+        // accumulator blocks are adjacent; the first step starts row li's
+        // accumulator in an MMA of its own.
+        auto issue = [&](int li) {
+            const int tlo = li - 2 > 0 ? li - 2 : 0, thi = li < L - 1 ? li : L - 1;
+            const uint64_t a_row = a_desc0 + (uint64_t)(((li % TC_NSLOT) * Cf::SLOT_BYTES) >> 4);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) a_row[q] = a_desc0 + (uint64_t)((((t + q) % TC_NSLOT) * Cf::SLOT_BYTES) >> 4);
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            for (int dxi = 0; dxi < 3; ++dxi) {
 #pragma unroll
                 for (int kc = 0; kc < CIN / 16; ++kc) {
-                    const uint64_t ad = a_row[dy + 1] + (uint64_t)(((1 + dx) * 16 + 2 * kc * Cf::GS) >> 4);
-                    const uint64_t bd = b_desc0 + (uint64_t)(((tap * Cf::KG + 2 * kc) * COUT * 16) >> 4);
-                    tc_mma(d, ad, bd, idesc, (tap | kc) ? 1u : 0u);
+                    const bool first = dxi == 0 && kc == 0;
+                    // swizzled: the window of tap dx starts dx + 1 pixels (128-byte rows)
+                    // in and the K step moves the start 32 bytes along the rows; the
+                    // swizzle follows the address bits, so the base offset stays 0
+                    const uint64_t ad = a_row + (uint64_t)((Cf::ASW ? dxi * 128 + kc * 32
+                                                                    : dxi * 16 + 2 * kc * Cf::GS) >> 4);
+                    // swizzled: the K step moves the start 32 bytes along the 128-byte rows
+                    const uint64_t bs = b_desc0 + (uint64_t)((Cf::WSW ? dxi * Cf::WDX + kc * 32
+                                                                      : (dxi * Cf::KG + 2 * kc) * Cf::WGS) >> 4);
+                    for (int t0 = tlo; t0 <= thi;) {
+                        int t1 = t0;
+                        while (t1 < thi && (t1 + 1) % TC_NBLK != 0 && !(first && t1 + 1 == li)) ++t1;
+                        const uint32_t d = tmem + (uint32_t)((t0 % TC_NBLK) * COUT);
+                        const uint64_t bd = bs + (uint64_t)(((t0 - li + 2) * COUT * (Cf::WSW ? 128 : 16)) >> 4);
+                        const uint32_t idesc = idesc0 | ((uint32_t)(((t1 - t0 + 1) * COUT) >> 3) << 17);
+                        tc_mma(d, ad, bd, idesc, (first && t0 == li) ? 0u : 1u);
+                        t0 = t1 + 1;
+                    }
                 }
             }
-            tc_commit(&bar[t & 1]);
+            tc_commit(&bar[li & 1]);
         };
         // the mask and residual chunks of output row t this thread stores
         uint4 mreg[Cf::O16], rreg[Cf::O16];
@@ -354,13 +415,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         };
 
         if (is_epi) {
-            // prologue: every slot's row in flight; rows 0..2 in place for row 0's MMAs
+            // prologue: every slot's row in flight; input row 0 in place for its MMAs
 #pragma unroll 1
             for (int li = 0; li < TC_NSLOT; ++li) copy_row(li);
-            cp_async_wait<TC_NSLOT - 3>();
+            cp_async_wait<TC_NSLOT - 1>();
             relu_row(0);
-            relu_row(1);
-            relu_row(2);
             fence_proxy_async();
         }
         tc_fence_before();
@@ -369,43 +428,48 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (tid == TC_EPI_THREADS) issue(0);
         pending |= 1u;
         bool timed_out = false;
-        for (int t = 0; t < L; ++t) {
-            if (t + 1 < L) {
-                // row li = t + 3 completes the rows of output row t + 1
+        // iteration j: issue input row j + 1, then (epilogue) wait for input row
+        // j, whose MMAs complete output row j - 2, and write that row out
+        for (int j = 0; j < L + 2; ++j) {
+            if (j + 1 < L + 2) {
                 if (is_epi) {
-                    cp_async_wait<TC_NSLOT - 4>();
-                    relu_row(t + 3);
+                    cp_async_wait<TC_NSLOT - 2>();
+                    relu_row(j + 1);
                     fence_proxy_async();
                 }
                 tc_fence_before();
-                // also: the epilogue of row t - 1 has read accumulator (t + 1) & 1
-                // and every thread has left the staging tile of row t - 1
+                // also: every thread has left the staging tile that row j - 2 takes
+                // (and tensor-memory blocks of rows read out are free long before
+                // they come round again)
                 if (__syncthreads_or(timed_out)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                if (tid == TC_EPI_THREADS) issue(t + 1);
-                pending |= 1u << ((t + 1) & 1);
+                if (tid == TC_EPI_THREADS) issue(j + 1);
+                pending |= 1u << ((j + 1) & 1);
             }
             if (!is_epi) continue;
-            const uint32_t b = (uint32_t)(t & 1);
+            const uint32_t b = (uint32_t)(j & 1);
             if (!bar_wait(&bar[b], (parity >> b) & 1u)) timed_out = true;
             parity ^= 1u << b;
             pending &= ~(1u << b);
             tc_fence_after();
-            // MMA(t) has read its rows: the slot of row t takes row t + TC_NSLOT
-            copy_row(t + TC_NSLOT);
+            // input row j's MMAs are done: its slot takes row j + TC_NSLOT
+            copy_row(j + TC_NSLOT);
+            const int t = j - 2;
+            if (t < 0) continue;
             // accumulator + bias -> FP32 staging tile t & 1 (on the run's last row
             // no block barrier has separated this from the tile's previous readers)
-            if (t + 1 >= L) epi_sync();
+            if (j + 1 >= L + 2) epi_sync();
             float* tile = tiles + (t & 1) * Cf::TILE;
+            const uint32_t blk = (uint32_t)((t % TC_NBLK) * COUT);
 #pragma unroll
             for (int ch = 0; ch < Cf::EPI_CH; ++ch) {
                 if (warp >= Cf::TW_WARPS) break;
                 const int c = col0 + Cf::NC * ch;
                 float v[16];
-                tc_ld<Cf::NC>(t_lane + b * COUT + (uint32_t)c, v);
+                tc_ld<Cf::NC>(t_lane + blk + (uint32_t)c, v);
 #pragma unroll
                 for (int q = 0; q < Cf::NC / 4; ++q) {
                     const int k = c / 4 + q;

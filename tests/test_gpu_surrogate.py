@@ -63,6 +63,29 @@ def test_forward_matches_oracle(gpu_lib, conv_path, shape, conserve_mass):
     _close(y - x, y_ref - x)
 
 
+@pytest.mark.parametrize("shape", SHAPES + [(1, 300, 1024)])
+def test_conv_paths_bit_identical(gpu_lib, shape):
+    # both convolution paths sum each output's 9 CIN / 16 K-steps in the same
+    # (dy, dx, channel chunk) order, each step a K = 16 product of BF16
+    # operands with FP32 accumulation: the forward output agrees bit for bit.
+    # The gradients agree to the rounding of the weight-gradient kernel's
+    # atomic FP32 sums, whose order varies from run to run. The 1 x 300 x 1024
+    # case gives each CTA a run of about 16 rows of eight 128-pixel strips,
+    # some runs going on from one strip into the next.
+    import torch
+    x = _to_dev(_fields(*shape, 11))
+    t = _to_dev(_fields(*shape, 12))
+    outs, grads = [], []
+    for path in PATHS:
+        S, p, s = _make(seed=13, conv_path=path)
+        out = torch.empty((4,) + shape, dtype=torch.float64, device="cuda")
+        s.forward(x, out)
+        outs.append(out)
+        grads.append(s.loss_grad(x, t)[1])
+    assert torch.equal(outs[0], outs[1])
+    assert np.linalg.norm(grads[0] - grads[1]) <= 1e-5 * np.linalg.norm(grads[1])
+
+
 def test_forward_full_size_sampled_windows(gpu_lib):
     # 1024 x 1024 (the rollout size): every CTA walks long runs of rows.
     # The output at a pixel depends only on inputs within R = 2 B + 2 pixels
