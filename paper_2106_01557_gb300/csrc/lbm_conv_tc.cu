@@ -312,12 +312,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // accumulator in an MMA of its own.
         auto issue = [&](int li) {
             const int tlo = li - 2 > 0 ? li - 2 : 0, thi = li < L - 1 ? li : L - 1;
+            // The cut of the rows into MMA segments is the same for every step but
+            // the first, so it is worked out once per row and the steps only add
+            // constant offsets (worked out per MMA, the issuing thread's scalar
+            // code took longer than the MMAs). Cut points in (tlo, thi], thi + 1
+            // where there is none: wr, the row whose block index wraps to 0 (at
+            // most one in three rows); sp, row li where it starts its accumulator
+            // after other rows of the step.
+            int wr = thi + 1;
+            for (int t = tlo + 1; t <= thi; ++t)
+                if ((t & (TC_NBLK - 1)) == 0) wr = t;
+            const int sp = li > tlo && li <= thi ? li : thi + 1;
+            const int q1 = wr < sp ? wr : sp, q2 = wr < sp ? sp : (sp < wr ? wr : thi + 1);
+            // one MMA segment, output rows a .. b: tensor-memory column, offset of
+            // the weight block (16-byte units) and instruction descriptor
+            auto seg = [&](int a, int b, uint32_t& d, uint32_t& bo, uint32_t& id) {
+                d = tmem + (uint32_t)((a & (TC_NBLK - 1)) * COUT);
+                bo = (uint32_t)(((a - li + 2) * COUT * (Cf::WSW ? 128 : 16)) >> 4);
+                id = idesc0 | ((uint32_t)(((b - a + 1) * COUT) >> 3) << 17);
+            };
+            uint32_t f0d, f0b, f0i, f1d = 0, f1b = 0, f1i = 0, f2d = 0, f2b = 0, f2i = 0;  // first step
+            uint32_t g0d, g0b, g0i, g1d = 0, g1b = 0, g1i = 0;                           // the others
+            seg(tlo, q1 - 1, f0d, f0b, f0i);
+            if (q1 <= thi) seg(q1, q2 - 1, f1d, f1b, f1i);
+            if (q2 <= thi) seg(q2, thi, f2d, f2b, f2i);
+            seg(tlo, wr - 1, g0d, g0b, g0i);
+            if (wr <= thi) seg(wr, thi, g1d, g1b, g1i);
             const uint64_t a_row = a_desc0 + (uint64_t)(((li % TC_NSLOT) * Cf::SLOT_BYTES) >> 4);
 #pragma unroll
             for (int dxi = 0; dxi < 3; ++dxi) {
 #pragma unroll
                 for (int kc = 0; kc < CIN / 16; ++kc) {
-                    const bool first = dxi == 0 && kc == 0;
                     // swizzled: the window of tap dx starts dx + 1 pixels (128-byte rows)
                     // in and the K step moves the start 32 bytes along the rows; the
                     // swizzle follows the address bits, so the base offset stays 0
@@ -326,14 +351,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     // swizzled: the K step moves the start 32 bytes along the 128-byte rows
                     const uint64_t bs = b_desc0 + (uint64_t)((Cf::WSW ? dxi * Cf::WDX + kc * 32
                                                                       : (dxi * Cf::KG + 2 * kc) * Cf::WGS) >> 4);
-                    for (int t0 = tlo; t0 <= thi;) {
-                        int t1 = t0;
-                        while (t1 < thi && (t1 + 1) % TC_NBLK != 0 && !(first && t1 + 1 == li)) ++t1;
-                        const uint32_t d = tmem + (uint32_t)((t0 % TC_NBLK) * COUT);
-                        const uint64_t bd = bs + (uint64_t)(((t0 - li + 2) * COUT * (Cf::WSW ? 128 : 16)) >> 4);
-                        const uint32_t idesc = idesc0 | ((uint32_t)(((t1 - t0 + 1) * COUT) >> 3) << 17);
-                        tc_mma(d, ad, bd, idesc, (first && t0 == li) ? 0u : 1u);
-                        t0 = t1 + 1;
+                    if (dxi == 0 && kc == 0) {
+                        tc_mma(f0d, ad, bs + f0b, f0i, tlo == li ? 0u : 1u);
+                        if (q1 <= thi) tc_mma(f1d, ad, bs + f1b, f1i, q1 == li ? 0u : 1u);
+                        if (q2 <= thi) tc_mma(f2d, ad, bs + f2b, f2i, q2 == li ? 0u : 1u);
+                    } else {
+                        tc_mma(g0d, ad, bs + g0b, g0i, 1u);
+                        if (wr <= thi) tc_mma(g1d, ad, bs + g1b, g1i, 1u);
                     }
                 }
             }
