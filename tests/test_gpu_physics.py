@@ -1,0 +1,47 @@
+"""Laplace's law on the GPU path at the sizes the oracle cannot reach: one
+static droplet per periodic 512 x 512 box (radii 40 to 100, R/W = 3 to 13),
+started from the planar square-gradient profile of the EOS, at three reduced
+temperatures. After 60,000 steps the pressure jump, from the EOS (Eq. 17) at
+each bulk's measured density and temperature, against 1/R (R the equimolar
+radius) has the slope of the surface tension that gradient theory gives for
+the configured K_EOS and K_INT (the paragraph after Eq. 19 prescribes
+sigma = 0.01 at T_r = 0.8 and reports 0.0101676 measured). The bound is 15%:
+the droplets end slightly warmer than the vapour (the total-energy drift of
+the scheme), and the liquid's stiff EOS turns that into a pressure error; the
+oracle's small-droplet pin is looser still (20%)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("tr", [0.7, 0.8, 0.9])
+def test_laplace_law_large_droplets(gpu_lib, tr):
+    from oracle import thermo
+    from gpu_common import gpu_case, oracle_case
+    N, steps = 512, 60000
+    o = oracle_case(N, N, Tr0=tr)
+    p = o.p
+    K_EOS, K_INT = o.cfg.K_EOS, o.cfg.K_INT
+    sigma, _ = thermo.surface_tension_and_width(p.T0, 1.0, 4.0, 1.0, K_EOS, K_INT)
+    yy, xx = np.meshgrid(np.arange(N) + 0.0, np.arange(N) + 0.0, indexing="ij")
+    rr = np.hypot(xx - N / 2, yy - N / 2)
+    c = N // 2
+    inv_r, dp = [], []
+    for R in (40.0, 60.0, 80.0, 100.0):
+        rho = thermo.planar_profile(p.T0, 1.0, 4.0, 1.0, K_EOS, K_INT, R - rr)
+        g = gpu_case(N, N, "f32", Tr0=tr)
+        g.set_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+        g.step(steps)
+        m = g.moments()
+        g.close()
+        r, T = m["rho"], m["T"]
+        dp.append(thermo.p_eos(r[c, c], T[c, c], 1.0, 4.0, 1.0, K_EOS)
+                  - thermo.p_eos(r[0, 0], T[0, 0], 1.0, 4.0, 1.0, K_EOS))
+        area = ((r - r[0, 0]) / (r[c, c] - r[0, 0])).sum()
+        inv_r.append(1.0 / np.sqrt(area / np.pi))
+        # spurious currents stay small against the lattice speed
+        assert np.hypot(m["ux"], m["uy"]).max() < 1e-2 * p.c
+    slope, icpt = np.polyfit(np.array(inv_r), np.array(dp), 1)
+    assert slope == pytest.approx(sigma, rel=0.15)
+    assert abs(icpt) < 0.2 * min(dp)
