@@ -401,6 +401,57 @@ def batch_study(steps, ncases=256, seed=4, precision="f16s"):
             "per_case": rows}
 
 
+def precision_study(checkpoints=(1000, 10000, 100000)):
+    """The storage formats on the boiling workload over long runs: FP64,
+    FP32, FP16S and BF16S lattices stepped side by side to each checkpoint.
+    Per format and checkpoint: the field errors against FP64 (max and rms of
+    |x - x64| over the field's scale; for u over c) and observables that a
+    moving interface does not scramble: the vapour fraction (nodes below the
+    mean of the Maxwell densities), the relative drift of mass and of total
+    energy from the conservation record, and the mean temperature."""
+    import torch
+    from paper_2106_01557_gb300 import lbm
+    precs = ("f64", "f32", "f16s", "bf16s")
+    lats, c0 = {}, {}
+    stream = torch.cuda.Stream()
+    for prec in precs:
+        lat, fields = boiling_case(lbm, NX, NY, prec, stream_ptr=stream.cuda_stream)
+        lat.set_fields(*fields)
+        lats[prec] = lat
+        c0[prec] = lat.conservation()
+    p = lats["f64"].params()
+    mid, c = 0.5 * (p["rho_v"] + p["rho_l"]), p["c"]
+    out, done, t0 = [], 0, time.perf_counter()
+    for cp in checkpoints:
+        for prec in precs:
+            lats[prec].step(cp - done)
+        done = cp
+        ms = {prec: lats[prec].moments() for prec in precs}
+        ref = ms["f64"]
+        row = {"steps": cp}
+        for prec in precs:
+            m, cr = ms[prec], lats[prec].conservation()
+            rec = {"vapour_fraction": float((m["rho"] < mid).mean()),
+                   "mass_drift": float(cr[0] / c0[prec][0] - 1),
+                   "energy_drift": float(cr[4] / c0[prec][4] - 1),
+                   "mean_T_over_Tc": float(m["T"].mean() / p["Tc"])}
+            if prec != "f64":
+                for f in ("rho", "T"):
+                    d = m[f] - ref[f]
+                    scale = np.abs(ref[f]).max()
+                    rec[f"err_{f}_max"] = float(np.abs(d).max() / scale)
+                    rec[f"err_{f}_rms"] = float(np.sqrt((d * d).mean()) / scale)
+                du = np.hypot(m["ux"] - ref["ux"], m["uy"] - ref["uy"])
+                rec["err_u_over_c_max"] = float(du.max() / c)
+                rec["err_u_over_c_rms"] = float(np.sqrt((du * du).mean()) / c)
+            row[prec] = rec
+        out.append(row)
+    for lat in lats.values():
+        lat.close()
+    return {"metric": "storage formats against FP64 over long runs", "workload": f"boiling {NX}x{NY}",
+            "wall_s": time.perf_counter() - t0, "checkpoints": out}
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle as it stands, on this host's cores, on a bounded
     slice of the workload (4096 x 64 rows of the same layout with walls)."""
@@ -438,6 +489,8 @@ def main():
     ap.add_argument("--batch-study", type=int, default=0,
                     help="run the 256-case sweep for this many steps and report coexistence per case")
     ap.add_argument("--batch-precision", default="f16s", choices=["f32", "f16s", "bf16s"])
+    ap.add_argument("--precision-study", type=int, default=0,
+                    help="run FP64/FP32/FP16S/BF16S side by side to 1,000, 10,000 and this many steps; print the errors")
     ap.add_argument("--surrogate-ks", default="100,200",
                     help="jump lengths K of the extra surrogate studies (comma list; empty: none)")
     ap.add_argument("--surrogate-iters", type=int, default=3000,
@@ -454,6 +507,11 @@ def main():
     if args.batch_study:
         if rank == 0:
             print(json.dumps(batch_study(args.batch_study, precision=args.batch_precision)))
+        return
+    if args.precision_study:
+        if rank == 0:
+            cps = tuple(sorted({k for k in (1000, 10000, args.precision_study) if k <= args.precision_study}))
+            print(json.dumps(precision_study(cps)))
         return
     config = {"workload": f"boiling {NX}x{NY}, walls, hot spot 32 cells, g=1e-5, {args.precision.upper()} storage",
               "nx": NX, "ny": NY, "precision": args.precision,
