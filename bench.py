@@ -151,11 +151,11 @@ def whole_job_mlups(nodes_per_rank, world, ms_step):
     return nodes_per_rank * world / (ms_step * 1e-3) / 1e6
 
 
-def boiling_case(lbm, nx, ny, precision, stream_ptr=None):
+def boiling_case(lbm, nx, ny, precision, stream_ptr=None, **overrides):
     from paper_2106_01557_gb300 import inputs
     x0 = inputs.hot_spot_x0(nx, 32, seed=3)
     cfg = lbm.default_config(nx, ny, precision=precision, walls=1, accel_y=-1e-5, Tr_bottom=0.8,
-                             Tr_hot=0.95, hot_x0=x0, hot_len=32, Tr_top=0.0)
+                             Tr_hot=0.95, hot_x0=x0, hot_len=32, Tr_top=0.0, **overrides)
     if stream_ptr is not None:
         cfg.stream = stream_ptr
     lat = lbm.Lattice(cfg)
@@ -403,7 +403,9 @@ def batch_study(steps, ncases=256, seed=4, precision="f16s"):
 
 def precision_study(checkpoints=(1000, 10000, 100000)):
     """The storage formats on the boiling workload over long runs: FP64,
-    FP32, FP16S and BF16S lattices stepped side by side to each checkpoint.
+    FP32, FP16S and BF16S lattices (the 16-bit ones with stochastic
+    rounding, the default, and rounded to nearest: "_rn") stepped side by
+    side to each checkpoint.
     Per format and checkpoint: the field errors against FP64 (max and rms of
     |x - x64| over the field's scale; for u over c) and observables that a
     moving interface does not scramble: the vapour fraction (nodes below the
@@ -411,11 +413,12 @@ def precision_study(checkpoints=(1000, 10000, 100000)):
     energy from the conservation record, and the mean temperature."""
     import torch
     from paper_2106_01557_gb300 import lbm
-    precs = ("f64", "f32", "f16s", "bf16s")
+    precs = ("f64", "f32", "f16s", "f16s_rn", "bf16s", "bf16s_rn")
     lats, c0 = {}, {}
     stream = torch.cuda.Stream()
     for prec in precs:
-        lat, fields = boiling_case(lbm, NX, NY, prec, stream_ptr=stream.cuda_stream)
+        lat, fields = boiling_case(lbm, NX, NY, prec.split("_")[0], stream_ptr=stream.cuda_stream,
+                                   rounding=0 if prec.endswith("_rn") else 1)
         lat.set_fields(*fields)
         lats[prec] = lat
         c0[prec] = lat.conservation()

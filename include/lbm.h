@@ -94,7 +94,13 @@ typedef struct lbm_config {
     double rho_ref;        /* shifted storage reference density; <= 0: rho_v(Tr0) */
     void* stream;          /* cudaStream_t to issue work on; NULL: own stream */
     int32_t device;        /* CUDA device ordinal */
-    int32_t reserved;
+    int32_t rounding;      /* 16-bit storage only: 0 rounds each stored value
+                              to nearest; 1 (default) rounds stochastically,
+                              up with probability equal to the discarded
+                              fraction, from a counter-based dither of (node,
+                              step, population), so that increments below
+                              half a 16-bit step still act on average and
+                              runs stay deterministic; other values: LBM_ERR_ARG */
 } lbm_config;
 
 /* Quantities derived in lbm_init (Eq. 16-19, SM Eq. S3-S5 constants). */

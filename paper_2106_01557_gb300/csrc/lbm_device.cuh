@@ -24,6 +24,10 @@ struct Store<double, double> {
     static __device__ __forceinline__ double st(double v, double) { return v; }
     static __device__ __forceinline__ double raw(double v) { return v; }
     static __device__ __forceinline__ double cvt(double v) { return v; }
+    static __device__ __forceinline__ void cvt_sr2(double a, double b, uint32_t, double& sa, double& sb) {
+        sa = a;
+        sb = b;
+    }
 };
 template <>
 struct Store<float, float> {
@@ -32,6 +36,10 @@ struct Store<float, float> {
     static __device__ __forceinline__ float st(float v, float) { return v; }
     static __device__ __forceinline__ float raw(float v) { return v; }
     static __device__ __forceinline__ float cvt(float v) { return v; }
+    static __device__ __forceinline__ void cvt_sr2(float a, float b, uint32_t, float& sa, float& sb) {
+        sa = a;
+        sb = b;
+    }
 };
 template <>
 struct Store<__half, float> {
@@ -40,6 +48,15 @@ struct Store<__half, float> {
     static __device__ __forceinline__ __half st(float v, float rest) { return __float2half_rn(v - rest); }
     static __device__ __forceinline__ float raw(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half cvt(float v) { return __float2half_rn(v); }
+    // a and b rounded stochastically (up with probability equal to the
+    // discarded fraction, subnormals included) by the stochastic-rounding
+    // conversion; the upper 16 bits of r drive a, the lower 16 bits b
+    static __device__ __forceinline__ void cvt_sr2(float a, float b, uint32_t r, __half& sa, __half& sb) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(r));
+        sa = __ushort_as_half((unsigned short)(d >> 16));
+        sb = __ushort_as_half((unsigned short)(d & 0xffffu));
+    }
 };
 template <>
 struct Store<__nv_bfloat16, float> {
@@ -48,7 +65,30 @@ struct Store<__nv_bfloat16, float> {
     static __device__ __forceinline__ __nv_bfloat16 st(float v, float rest) { return __float2bfloat16_rn(v - rest); }
     static __device__ __forceinline__ float raw(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 cvt(float v) { return __float2bfloat16_rn(v); }
+    // as for half precision: the upper 16 bits of r drive a, the lower b
+    static __device__ __forceinline__ void cvt_sr2(float a, float b, uint32_t r, __nv_bfloat16& sa,
+                                                   __nv_bfloat16& sb) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(r));
+        sa = __ushort_as_bfloat16((unsigned short)(d >> 16));
+        sb = __ushort_as_bfloat16((unsigned short)(d & 0xffffu));
+    }
 };
+
+// Dither of the stochastic rounding: the 32-bit finaliser of MurmurHash3
+// (A. Appleby) mixes (node, step) into a seed per node, and the linear
+// congruential step of Numerical Recipes (x -> 1664525 x + 1013904223)
+// gives one 32-bit value per pair of stored populations (its weak low half
+// is mixed with its high half before use).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ uint32_t lcg_next(uint32_t r) { return r * 1664525u + 1013904223u; }
 
 // Reciprocal: IEEE in FP64; in FP32 the hardware approximation (relative
 // error ~1e-7, far below the FP32 path's 1e-5 parity bound).

@@ -208,6 +208,7 @@ void lbm_default_config(lbm_config* c, int32_t nx, int32_t ny) {
     c->rho_ref = 0.0;
     c->stream = nullptr;
     c->device = 0;
+    c->rounding = 1;
 }
 
 static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
@@ -216,6 +217,8 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     if ((long long)c.nx * c.ny > (1ll << 31)) return fail(LBM_ERR_ARG, "lattice too large");
     if (storage_of(c.precision) < 0) return fail(LBM_ERR_ARG, "unknown precision");
     if (c.walls != 0 && c.walls != 1) return fail(LBM_ERR_ARG, "walls must be 0 or 1");
+    if (c.rounding != 0 && c.rounding != 1) return fail(LBM_ERR_ARG, "rounding must be 0 or 1");
+    L.rounding = c.rounding;
     if (!(c.a_t > 0 && c.b_t > 0 && c.R > 0 && c.K_EOS > 0 && c.K_INT > 0))
         return fail(LBM_ERR_ARG, "a~, b~, R, K_EOS, K_INT must be positive");
     if (!(c.Tr0 > 0.3 && c.Tr0 < 1.0)) return fail(LBM_ERR_ARG, "Tr0 must lie in (0.3, 1)");
@@ -695,6 +698,10 @@ int lbm_load(lbm_handle* h, const char* path) {
     if (!ok) return fail(LBM_ERR_IO, std::string("read failed: ") + path);
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaMemcpy(h->buf[0], host.data(), bytes, cudaMemcpyHostToDevice));
+    // the device copy of the step count keys the stochastic rounding of
+    // 16-bit storage: a resumed run continues with the same dither
+    const double st = (double)steps;
+    CK(cudaMemcpy(h->stats + 7, &st, sizeof st, cudaMemcpyHostToDevice));
     h->cur = 0;
     h->steps = steps;
     return LBM_OK;

@@ -57,6 +57,7 @@ struct Launch {
     Geometry geo;
     KC<float> kf;
     KC<double> kd;
+    int rounding;  // 16-bit storage: 0 nearest, 1 stochastic
 };
 
 // Storage kinds

@@ -119,23 +119,40 @@ struct Acc {
 // already hold the deviations from the rest populations.
 template <class S, class C>
 __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
-                                           const C f[9], const C g[9], C rho) {
+                                           const C f[9], const C g[9], C rho, uint32_t dither) {
     const C* rest = k.rest;
     constexpr bool SH = Store<S, C>::SHIFTED;
     const int HX = G.HX;
     const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
-    if (interior) {
-        S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
+    // the values as stored: 16-bit storage rounds stochastically where a
+    // dither seed is given (non-zero), else to nearest
+    S sf[9], sg[9];
+    if (SH && dither) {
+        uint32_t r = dither;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            o[i * G.plane] = Store<S, C>::cvt(f[i]);
-            o[(9 + i) * G.plane] = Store<S, C>::cvt(g[i]);
+            r = lcg_next(r);
+            Store<S, C>::cvt_sr2(f[i], g[i], r ^ (r >> 15), sf[i], sg[i]);
         }
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            put<S>(out, G, i, x, y, Store<S, C>::cvt(f[i]));
-            put<S>(out, G, 9 + i, x, y, Store<S, C>::cvt(g[i]));
+            sf[i] = Store<S, C>::cvt(f[i]);
+            sg[i] = Store<S, C>::cvt(g[i]);
+        }
+    }
+    if (interior) {
+        S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            o[i * G.plane] = sf[i];
+            o[(9 + i) * G.plane] = sg[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            put<S>(out, G, i, x, y, sf[i]);
+            put<S>(out, G, 9 + i, x, y, sg[i]);
         }
     }
     if (G.walls && (y == 0 || y == G.ny - 1)) {
@@ -194,6 +211,11 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     Acc<C> acc = {0, 0, 0, 0, 0, 0, 0};
     bool ok = true;
     int it = 0;
+    // stochastic rounding of 16-bit storage: the step count (kept in the
+    // record by the last block of the previous launch) keys the dither
+    const uint32_t step_key = (Store<S, C>::SHIFTED && L.rounding)
+                                  ? fmix32((uint32_t)(long long)__ldcg(&stats[7]) * 0x9e3779b9u + 0x7f4a7c15u)
+                                  : 0u;
     // NS >= 2: one block barrier per tile. At the barrier after the density
     // pass of tile `it`, every thread has finished tile it-1, so its stage is
     // refilled with tile it+NS-1 and the other density buffer is free.
@@ -271,7 +293,8 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
                 if (!(rho > C(0) && rho < C(1e30) && u2 < C(1e30))) acc.bad += C(1);  // also catches NaN
             }
             collide<Store<S, C>::SHIFTED>(k, f, g, s);
-            store_node<S, C>(out, G, k, x, y, f, g, s.rho);
+            store_node<S, C>(out, G, k, x, y, f, g, s.rho,
+                             step_key ? fmix32((uint32_t)(y * G.nx + x) ^ step_key) | 1u : 0u);
         }
         if (NS == 1) {
             __syncthreads();  // every thread is done with the stage: refill it

@@ -43,7 +43,7 @@ class LbmConfig(ctypes.Structure):
         ("hot_x0", ctypes.c_int32), ("hot_len", ctypes.c_int32),
         ("rho_ref", ctypes.c_double),
         ("stream", ctypes.c_void_p),
-        ("device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("device", ctypes.c_int32), ("rounding", ctypes.c_int32),
     ]
 
 
