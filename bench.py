@@ -118,8 +118,8 @@ METRIC = "MLUPS of the fused f+g step (FP32 plain)"
 # DRAM bytes (read + write) of one k_step launch on this workload, from one
 # ncu capture (profiles/k_step_f32_4096x1024_full.md), valid only for the
 # kernel sources it was taken on: any change to them makes it null.
-STEP_TRAFFIC = {"bytes_per_launch": 309392640 + 255536896,
-                "sources_sha256": "af0d6389fe75869c8aa101ea78227afc27bdf6277ddce96657f5baf8d3ebd600"}
+STEP_TRAFFIC = {"bytes_per_launch": 309387264 + 255035648,
+                "sources_sha256": "b485551e2a88545a6c8ed52728d22b68aef39e5d68fabd73a80eb5ad44fabc40"}
 STEP_SOURCES = ["lbm_step.cu", "lbm_device.cuh", "lbm_internal.h", "lbm_ptx.cuh"]
 
 
@@ -174,7 +174,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
     prec = args.precision
-    lat, fields = boiling_case(lbm, NX, NY, prec, stream_ptr=stream.cuda_stream)
+    lat, fields = boiling_case(lbm, NX, NY, prec, stream_ptr=stream.cuda_stream, rounding=args.rounding)
     lat.set_fields(*fields)
     nodes = NX * NY
     bytes_step = lat.bytes_per_step()
@@ -485,6 +485,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
+    ap.add_argument("--rounding", type=int, default=1, choices=[0, 1],
+                    help="16-bit storage: 1 stochastic rounding (the library default), 0 nearest")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=1000,
                     help="steps of each storage format for the error-vs-FP64 comparison")
