@@ -100,7 +100,9 @@ typedef struct lbm_config {
                               fraction, from a counter-based dither of (node,
                               step, population), so that increments below
                               half a 16-bit step still act on average and
-                              runs stay deterministic; other values: LBM_ERR_ARG */
+                              runs stay deterministic; other values:
+                              LBM_ERR_ARG. The batched sweep (lbm_batch_*)
+                              rounds to nearest whatever the value. */
 } lbm_config;
 
 /* Quantities derived in lbm_init (Eq. 16-19, SM Eq. S3-S5 constants). */
@@ -197,7 +199,8 @@ int lbm_destroy(lbm_handle* h);
  * in device tables. The rows are the same model as lbm_step; a case in a
  * batch gives the same populations as that case on its own handle with the
  * same precision, up to floating-point rounding (the two kernels are
- * compiled separately). Extension of the paper's method for
+ * compiled separately; with 16-bit storage the batch rounds stores to
+ * nearest, a single handle by default stochastically: lbm_config.rounding). Extension of the paper's method for
  * parameter sweeps (the paper runs single cases). Requirements: every
  * cfgs[i] periodic (walls = 0), one precision for all (LBM_F32, LBM_F16S or
  * LBM_BF16S), the stream and device of cfgs[0] are used. */
