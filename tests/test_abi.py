@@ -90,6 +90,11 @@ def test_default_config_and_argument_errors_without_gpu(lib):
     bad = lbm.default_config(65536, 32769)
     assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
     assert b"too large" in l.lbm_last_error()
+    # 16-bit storage rounds stochastically by default; only 0 and 1 are valid
+    assert lbm.default_config(64, 32).rounding == 1
+    bad = lbm.default_config(64, 32, precision="f16s", rounding=2)
+    assert l.lbm_init(ctypes.byref(bad), ctypes.byref(h)) == -1
+    assert b"rounding" in l.lbm_last_error()
 
 
 def test_library_maxwell_matches_oracle_on_host(lib):
