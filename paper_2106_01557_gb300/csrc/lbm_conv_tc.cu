@@ -13,8 +13,9 @@
 //
 // The MMAs are input-stationary: input row li of a run (image row y0 - 1 +
 // li) feeds output rows t = li - 2, li - 1 and li of the run through taps
-// dy = +1, 0 and -1; the weights of the three dy taps sit side by side in N, so one MMA (M = 128 pixels, N = 3 COUT, K = 16) applies one
-// (dx, 16-channel) step of input row li to all three output rows at once.
+// dy = +1, 0 and -1; the weights of the three dy taps sit side by side in
+// N, so one MMA (M = 128 pixels, N = 3 COUT, K = 16) applies one (dx,
+// 16-channel) step of input row li to all three output rows at once.
 // Output row t accumulates in block t % TC_NBLK of tensor memory (COUT
 // columns each); where the blocks of the rows wrap around, or where a row
 // starts its accumulator (its first step, accumulate flag off), the step is
