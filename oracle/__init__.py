@@ -7,9 +7,11 @@ and the CPU-baseline leg of ``bench.py``; never by the product package.
 ``lbm_oracle.c`` holds one time step, initialisation and moments (plain C,
 FP64), built here with gcc and called through ctypes.
 
-Parity status of each function is stated in its docstring; the one part the
-paper gives no independent check for is the velocity coupling of S (SM
-Eq. S5a) and the wall treatment: "parity unpinned" beyond GPU-vs-oracle.
+Parity status of each function is stated in its docstring; the parts the
+paper gives no independent check for are the coefficient k s_eps omega_e of
+S (row e, column eps; SM Eq. S5a), the sign of the 3 rho |u^|^2 term of m^eq
+row eps (SM Eq. S3a) and the wall treatment: "parity unpinned" beyond
+GPU-vs-oracle.
 """
 from __future__ import annotations
 

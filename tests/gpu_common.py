@@ -33,3 +33,34 @@ def slab_fields(o, seed=0, eps=0.02, uamp=0.01):
 def rel_err(a, b):
     """max |a - b| / max |b| (per field: the error relative to the field's scale)."""
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def shear_wave_viscous_work_factor(make, nx=4, N=128, amp=0.1):
+    """A decaying shear wave u_x = A(t) sin(ky) in a uniform vapour, on a
+    lattice make(nx, N) with .p (cs, rho_v, T0), set_fields, step and
+    moments. The energy equation (Eq. 6c) carries the viscous work flux
+    u . Pi, whose divergence feeds the cos(2ky) mode of rho e_k at
+    lambda rho nu k^2 A^2 with lambda = 1, while the cos(2ky) mode of the
+    macroscopic kinetic energy rho u^2 / 2 grows at rho nu k^2 A^2 / 2 (the
+    wave's own decay). Their ratio over a short window (steps 5 to 10, before
+    conduction and sound act) is 2 lambda, whatever the transport
+    coefficients. Returns lambda: without the Y term of Eq. 12c it is 0,
+    with m - m^eq in place of (m + m_bar)/2 - m^eq it is 2."""
+    lat = make(nx, N)
+    p = lat.p
+    y = np.arange(N) + 0.0
+    cos2 = np.cos(4 * np.pi * y / N)
+    ux = np.repeat((amp * p["cs"] * np.sin(2 * np.pi * y / N))[:, None], nx, axis=1)
+    lat.set_fields(np.full((N, nx), p["rho_v"]), ux, 0 * ux, 0 * ux + p["T0"])
+
+    def coefficients():
+        m = lat.moments()
+        r, u, v, T = (m[f].mean(axis=1) for f in ("rho", "ux", "uy", "T"))
+        ek = r * 1.5 * T + 0.5 * r * (u * u + v * v)  # rho e_k = rho c_v T + rho |u|^2 / 2, c_v = 3/2 R
+        return (2 / N) * (ek * cos2).sum(), (2 / N) * (0.5 * r * u * u * cos2).sum()
+
+    lat.step(5)
+    e0, k0 = coefficients()
+    lat.step(5)
+    e1, k1 = coefficients()
+    return (e1 - e0) / (2 * (k1 - k0))

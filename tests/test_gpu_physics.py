@@ -45,3 +45,16 @@ def test_laplace_law_large_droplets(gpu_lib, tr):
     slope, icpt = np.polyfit(np.array(inv_r), np.array(dp), 1)
     assert slope == pytest.approx(sigma, rel=0.15)
     assert abs(icpt) < 0.2 * min(dp)
+
+
+def test_viscous_work_on_gpu(gpu_lib):
+    # the oracle's pin of the Y term (Eq. 12c, SM Eq. S6b), on the FP64 GPU path
+    from gpu_common import gpu_case, shear_wave_viscous_work_factor
+
+    class _Lat:
+        def __init__(self, nx, ny):
+            self.g = gpu_case(nx, ny, "f64")
+            self.p = self.g.params()
+            self.moments, self.step, self.set_fields = self.g.moments, self.g.step, self.g.set_fields
+
+    assert shear_wave_viscous_work_factor(_Lat, nx=8) == pytest.approx(1.0, abs=0.05)
