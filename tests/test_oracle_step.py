@@ -201,14 +201,15 @@ def test_single_node_collision_budget():
     assert gb.sum() == pytest.approx(gl.sum() + p.dt * q, rel=1e-14)
 
 
-def _growth(o, rho0, ngrid=10):
+def _growth(o, rho0, ngrid=10, U=0.0):
     """Largest amplification factor of the linearised step (collision
     Jacobian by central differences of the oracle's node collision, pair
     force through the neighbour densities, streaming as a phase) over a
-    grid of wave vectors, around the uniform rest state at density rho0."""
+    grid of wave vectors, around the uniform state at density rho0 moving
+    along x at U c_s (at rest for U = 0)."""
     p = o.p
     n = 4
-    o.init_fields(np.full((n, n), rho0), np.zeros((n, n)), np.zeros((n, n)), np.full((n, n), p.T0))
+    o.init_fields(np.full((n, n), rho0), np.full((n, n), U * p.cs), np.zeros((n, n)), np.full((n, n), p.T0))
     x0 = np.concatenate([o.f[:, 0, 0], o.g[:, 0, 0], np.full(9, rho0)])
 
     def col(x):
@@ -240,6 +241,17 @@ def test_bulk_phases_linearly_stable(Tr):
     o = Oracle(thermo.Config(nx=4, ny=4, Tr0=Tr))
     assert _growth(o, o.p.rho_l) < 1 + 1e-7
     assert _growth(o, o.p.rho_v) < 1 + 1e-7
+
+
+def test_moving_vapour_linearly_stable():
+    # the uniform vapour at T_r = 0.8 moving at 0.1 and 0.2 c_s stays linearly
+    # stable with the coupling k s_eps omega_e of S (row e, column eps; SM
+    # Eq. S5a); dropping that coefficient (growth 1e-3 at 0.1 c_s), halving
+    # it (3e-4 at 0.2 c_s), doubling it (0.31 at rest) or flipping its sign
+    # (0.05 at rest) makes it unstable
+    o = Oracle(thermo.Config(nx=4, ny=4))
+    for U in (0.0, 0.1, 0.2):
+        assert _growth(o, o.p.rho_v, U=U) < 1 + 1e-7, U
 
 
 def test_bulk_liquid_unstable_at_low_temperature():
