@@ -7,11 +7,11 @@ and the CPU-baseline leg of ``bench.py``; never by the product package.
 ``lbm_oracle.c`` holds one time step, initialisation and moments (plain C,
 FP64), built here with gcc and called through ctypes.
 
-Parity status of each function is stated in its docstring; the parts the
-paper gives no independent check for are the sign of the 3 rho |u^|^2 term of
-m^eq row eps (SM Eq. S3a) and the wall treatment: "parity unpinned" beyond
-GPU-vs-oracle. The coefficient k s_eps omega_e of S (row e, column eps; SM
-Eq. S5a) is pinned only through the linear stability of the moving vapour.
+Parity status of each function is stated in its docstring; the part the
+paper gives no independent check for is the wall treatment: "parity
+unpinned" beyond GPU-vs-oracle. The coefficient k s_eps omega_e of S (row e,
+column eps; SM Eq. S5a) is pinned only through the linear stability of the
+moving vapour.
 """
 from __future__ import annotations
 

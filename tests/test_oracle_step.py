@@ -39,6 +39,36 @@ def test_M_orthogonal_and_inverse():
     assert np.array_equal(M[3], EX) and np.array_equal(M[5], EY)
 
 
+def test_equilibrium_velocity_terms_are_the_discrete_maxwellians():
+    # At fixed rho and T (eta depends on nothing else), the velocity dependence
+    # of m^eq (SM Eq. S3a) is that of the textbook second-order D2Q9
+    # equilibrium w_i rho (1 + 3 e_i.u + 9/2 (e_i.u)^2 - 3/2 |u|^2) (u over the
+    # lattice speed) projected with M: +3 rho |u|^2 in row e, -3 rho |u|^2 in
+    # row eps (a sign no dynamic pin separates), -rho u in rows q, rho (ux^2 -
+    # uy^2) and rho ux uy in rows p. The oracle's m^eq is read back from its
+    # initialisation of a uniform state (no force, so f = M^-1 m^eq).
+    M, _ = M_and_inverse()
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    o = Oracle(thermo.Config(nx=4, ny=4))
+    p = o.p
+    rho0 = p.rho_v
+    one = np.ones((4, 4))
+
+    def m_eq(uxh, uyh):
+        o.init_fields(rho0 * one, uxh * p.c * one, uyh * p.c * one, p.T0 * one)
+        return M @ o.f[:, 1, 1]
+
+    def maxwellian(uxh, uyh):
+        eu = EX * uxh + EY * uyh
+        return w * rho0 * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (uxh ** 2 + uyh ** 2))
+
+    m0 = m_eq(0.0, 0.0)
+    for uxh, uyh in [(0.1, 0.0), (0.07, -0.05), (0.0, 0.12)]:
+        dm = m_eq(uxh, uyh) - m0
+        dref = M @ (maxwellian(uxh, uyh) - maxwellian(0.0, 0.0))
+        assert np.abs(dm - dref).max() < 1e-13 * rho0, (uxh, uyh, dm - dref)
+
+
 def test_init_recovers_prescribed_fields():
     o = random_state(seed=4)
     n = o.nx
