@@ -7,11 +7,10 @@ and the CPU-baseline leg of ``bench.py``; never by the product package.
 ``lbm_oracle.c`` holds one time step, initialisation and moments (plain C,
 FP64), built here with gcc and called through ctypes.
 
-Parity status of each function is stated in its docstring; the part the
-paper gives no independent check for is the wall treatment: "parity
-unpinned" beyond GPU-vs-oracle. The coefficient k s_eps omega_e of S (row e,
-column eps; SM Eq. S5a) is pinned only through the linear stability of the
-moving vapour.
+Parity status of each function is stated in its docstring. The coefficient
+k s_eps omega_e of S (row e, column eps; SM Eq. S5a) is pinned only through
+the linear stability of the moving vapour, and the walls (not in the paper)
+only through textbook flows (Poiseuille, steady conduction).
 """
 from __future__ import annotations
 

@@ -64,3 +64,41 @@ def shear_wave_viscous_work_factor(make, nx=4, N=128, amp=0.1):
     lat.step(5)
     e1, k1 = coefficients()
     return (e1 - e0) / (2 * (k1 - k0))
+
+
+def poiseuille_deviation(make, nx=4, ny=16, g=1e-5, steps=6000):
+    """Force-driven flow of the uniform vapour between the half-way
+    bounce-back walls (y = -1/2 and ny - 1/2, periodic in x), run to its
+    steady state: the largest deviation of u_x from the parabola
+    g / (2 nu) (y + 1/2) (ny - 1/2 - y), nu = c_s^2 (1/s_p - 1/2) dt, over
+    the parabola's peak. make(nx, ny, **cfg) returns a lattice with .p (cs,
+    dt, rho_v, T0), .s_p, set_fields, step and moments."""
+    lat = make(nx, ny, walls=1, accel_x=g)
+    p = lat.p
+    one = np.ones((ny, nx))
+    lat.set_fields(p["rho_v"] * one, 0 * one, 0 * one, p["T0"] * one)
+    lat.step(steps)
+    u = lat.moments()["ux"].mean(axis=1)
+    nu = p["cs"] ** 2 * (1 / lat.s_p - 0.5) * p["dt"]
+    y = np.arange(ny) + 0.0
+    ref = g / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    return float(np.abs(u - ref).max() / ref.max())
+
+
+def conduction_wall_errors(make, nx=4, ny=16, tb=0.81, tt=0.79, steps=10000):
+    """Steady conduction through the vapour between fixed-temperature walls
+    (reduced temperatures tb at the bottom, tt at the top, half-way between
+    the wall rows and their ghosts), no flow: the straight line fitted to the
+    interior temperature extrapolated to y = -1/2 and y = ny - 1/2, and the
+    largest deviation from that line, each over tb - tt."""
+    lat = make(nx, ny, walls=1, Tr_bottom=tb, Tr_top=tt)
+    p = lat.p
+    one = np.ones((ny, nx))
+    lat.set_fields(p["rho_v"] * one, 0 * one, 0 * one, p["T0"] * one)
+    lat.step(steps)
+    T = lat.moments()["T"].mean(axis=1) / p["Tc"]
+    y = np.arange(ny) + 0.0
+    a, b = np.polyfit(y[3:-3], T[3:-3], 1)
+    dT = tb - tt
+    return (abs(a * -0.5 + b - tb) / dT, abs(a * (ny - 0.5) + b - tt) / dT,
+            float(np.abs(T - (a * y + b)).max() / dT))

@@ -58,3 +58,24 @@ def test_viscous_work_on_gpu(gpu_lib):
             self.moments, self.step, self.set_fields = self.g.moments, self.g.step, self.g.set_fields
 
     assert shear_wave_viscous_work_factor(_Lat, nx=8) == pytest.approx(1.0, abs=0.05)
+
+
+class _GpuLattice:
+    """An FP64 GPU lattice behind the interface of the shared physics checks."""
+
+    def __init__(self, nx, ny, **cfg):
+        from gpu_common import gpu_case
+        self.g = gpu_case(nx, ny, "f64", **cfg)
+        self.p = self.g.params()
+        from paper_2106_01557_gb300 import lbm
+        self.s_p = lbm.default_config(nx, ny).s_p
+        self.moments, self.step, self.set_fields = self.g.moments, self.g.step, self.g.set_fields
+
+
+def test_wall_pins_on_gpu(gpu_lib):
+    # the oracle's pins of the walls (Poiseuille parabola, steady conduction)
+    # on the FP64 GPU path
+    from gpu_common import conduction_wall_errors, poiseuille_deviation
+    assert poiseuille_deviation(_GpuLattice, nx=8) < 0.01
+    eb, et, dev = conduction_wall_errors(_GpuLattice, nx=8)
+    assert eb < 0.01 and et < 0.01 and dev < 0.01
