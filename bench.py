@@ -10,6 +10,12 @@ reduction. The state (2 x 302 MB) is larger than L2, so no flush is needed
 between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision f64|f32|f16s|bf16s] [--rounding 1|0]
+
+Studies (one JSON line each, no timing contract):
+  --batch-study STEPS      the 256-case sweep against the Maxwell densities
+  --precision-study STEPS  the storage formats (16-bit with stochastic and
+                           nearest rounding) side by side against FP64
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload (the method has no exchange between independent cases); the value
