@@ -69,6 +69,31 @@ def test_equilibrium_velocity_terms_are_the_discrete_maxwellians():
         assert np.abs(dm - dref).max() < 1e-13 * rho0, (uxh, uyh, dm - dref)
 
 
+def test_forcing_moments_are_those_of_the_second_order_forcing_term():
+    # The discrete force F_m (SM Eq. S3b) is the moment projection of the
+    # textbook second-order forcing term w_i [3 e_i.F + 9 (e_i.u)(e_i.F) -
+    # 3 u.F] (F and u over the lattice speed): F.u enters rows e and eps as
+    # +-6 F.u, the momentum rows as F, and rows p as 2 (Fx ux - Fy uy) and
+    # Fx uy + Fy ux. The oracle's F_m is read back from its initialisation of a
+    # uniform state with and without a body force (m = m^eq - dt/2 F_m).
+    M, _ = M_and_inverse()
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    one = np.ones((4, 4))
+    for ax, ay, uxh, uyh in [(2e-3, 0.0, 0.1, 0.0), (1e-3, -2e-3, 0.07, -0.05), (0.0, 3e-3, 0.03, 0.11)]:
+        ms = []
+        for a in ((0.0, 0.0), (ax, ay)):
+            o = Oracle(thermo.Config(nx=4, ny=4, accel_x=a[0], accel_y=a[1]))
+            p = o.p
+            o.init_fields(p.rho_v * one, uxh * p.c * one, uyh * p.c * one, p.T0 * one)
+            ms.append(M @ o.f[:, 1, 1])
+        Fm = 2.0 * (ms[0] - ms[1]) / p.dt
+        Fxh, Fyh = p.rho_v * ax / p.c, p.rho_v * ay / p.c
+        eu, eF = EX * uxh + EY * uyh, EX * Fxh + EY * Fyh
+        ref = M @ (w * (3 * eF + 9 * eu * eF - 3 * (uxh * Fxh + uyh * Fyh)))
+        scale = abs(Fxh) + abs(Fyh)
+        assert np.abs(Fm - ref).max() < 1e-9 * scale, (ax, ay, Fm - ref)
+
+
 def test_init_recovers_prescribed_fields():
     o = random_state(seed=4)
     n = o.nx
