@@ -157,3 +157,27 @@ def test_steady_conduction_between_fixed_temperature_walls():
     from gpu_common import conduction_wall_errors
     eb, et, dev = conduction_wall_errors(_OracleLattice)
     assert eb < 0.01 and et < 0.01 and dev < 0.01
+
+
+def test_heated_poiseuille_temperature_shape():
+    # Force-driven vapour between adiabatic bounce-back walls heats up: by
+    # Eq. 6c the body-force work goes into the flow and leaves it as viscous
+    # dissipation mu u'^2, which conduction spreads. Once the temperature
+    # rises uniformly, T - mean(T) has the shape fixed by
+    # lambda theta'' = <mu u'^2> - mu u'^2 with theta' = 0 at the walls:
+    # y'^2 H^2 / 24 - y'^4 / 12 (y' from the centre line), whatever lambda is;
+    # measured within 0.26% of the peak
+    ny = 32
+    o = Oracle(thermo.Config(nx=4, ny=ny, walls=1, accel_x=2e-5))
+    p = o.p
+    one = np.ones((ny, 4))
+    o.init_fields(p.rho_v * one, 0 * one, 0 * one, p.T0 * one)
+    o.step(22000)
+    T = o.moments()["T"].mean(axis=1)
+    theta = T - T.mean()
+    yp = np.arange(ny) + 0.5 - ny / 2
+    shape = yp ** 2 * ny ** 2 / 24 - yp ** 4 / 12
+    shape -= shape.mean()
+    amp = (theta * shape).sum() / (shape * shape).sum()
+    assert amp > 0
+    assert np.abs(theta - amp * shape).max() < 0.02 * np.abs(amp * shape).max()
