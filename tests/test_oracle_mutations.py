@@ -5,10 +5,15 @@ flags, points the oracle module at the copy, and requires that at least one
 of the fast pins fails. The planted copies live in pytest's temporary
 directory; the oracle itself is untouched.
 
-Not caught by any pin tried (and therefore not listed): swapping gamma1 and
-gamma2 in the e and eps rows of the g source q_m (SM Eq. S4b); these source
-terms of non-conserved moments leave the flows checked here unchanged (a
-heated Poiseuille flow's temperature shape moves by 0.16%)."""
+Not caught by these fast pins (and therefore not listed): swapping gamma1 and
+gamma2 in the e and eps rows of the g source q_m (SM Eq. S4b; a heated
+Poiseuille flow's temperature shape moves by 0.16%), flipping the sign of
+its heat-flux rows q u, and dropping the velocity couplings of S in row e
+(h u s_q omega_e) or one entry of row pxy (b u s_q omega_p): these act on
+non-conserved moments at an order the flows checked here do not resolve
+(shear waves in a moving vapour decay 9% faster at 0.2 c_s with or without
+them, the D2Q9 lattice's own defect). Dropping Q_m is caught by the slower
+slab width and coexistence pin."""
 import os
 import subprocess
 
@@ -44,6 +49,15 @@ MUTATIONS = [
      "t->S[7][4] = 2.0 * P->bS * uxh * P->sq * wp;", "t->S[7][4] = -2.0 * P->bS * uxh * P->sq * wp;"),
     ("n^eq heat flux with rho e_k instead of rho h_k",
      "rhk * uxh, -rhk * uxh, rhk * uyh, -rhk * uyh, 0.0, 0.0};", "E * uxh, -E * uxh, E * uyh, -E * uyh, 0.0, 0.0};"),
+    ("n^eq row e: 4 + gamma1 written 4 - gamma1",
+     "(4.0 + P->gamma1) * CT, 4.0 * E - (4.0 - P->gamma2) * CT,\n                     rhk * uxh",
+     "(4.0 - P->gamma1) * CT, 4.0 * E - (4.0 - P->gamma2) * CT,\n                     rhk * uxh"),
+    ("L coupling sigma_q omega_j doubled in row jx",
+     "t->L[3][4] = sigq * wj;", "t->L[3][4] = 2.0 * sigq * wj;"),
+    ("force term dt F_m halved in m_bar (Eq. 12b)",
+     "mb[k] = m[k] + P->dt * t.Fm[k] - Sx[k] + SQ[k];", "mb[k] = m[k] + 0.5 * P->dt * t.Fm[k] - Sx[k] + SQ[k];"),
+    ("velocity without the half force (Eq. 14)",
+     "s->ux = (jx + 0.5 * P->dt * s->Fx) / rho;", "s->ux = jx / rho;"),
 ]
 
 PINS = [
