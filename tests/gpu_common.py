@@ -102,3 +102,50 @@ def conduction_wall_errors(make, nx=4, ny=16, tb=0.81, tt=0.79, steps=10000):
     dT = tb - tt
     return (abs(a * -0.5 + b - tb) / dT, abs(a * (ny - 0.5) + b - tt) / dT,
             float(np.abs(T - (a * y + b)).max() / dT))
+
+
+def strip_reference(fields, cfg, x0, w, margin, steps):
+    """The oracle's state after `steps` steps on columns x0 .. x0 + w - 1 (all
+    rows) of a lattice periodic in x, from a strip of the initial fields
+    `margin` columns wider on each side (periodic crop). A node's update
+    reads the previous state within two nodes, so with margin > 2 steps the
+    strip's centre is exact; walls (in y) are kept whole, and the hot wall
+    segment is cut to the strip (the parts beyond the margin cannot reach the
+    centre). cfg: the thermo.Config keyword arguments of the full lattice
+    (nx, ny, walls, accel_*, Tr_*, hot_x0, hot_len). Returns the strip's
+    centre moments {rho, ux, uy, T}, each (ny, w)."""
+    assert margin > 2 * steps
+    nx, ny = cfg["nx"], cfg["ny"]
+    n = w + 2 * margin
+    lo = x0 - margin
+    crop = [np.roll(a, -lo, axis=1)[:, :n] for a in fields]
+    c = dict(cfg)
+    c["nx"] = n
+    if cfg.get("hot_len", 0) > 0:
+        # the hot segment in strip coordinates, clipped to the strip
+        a = (cfg["hot_x0"] - lo) % nx
+        b = a + cfg["hot_len"]
+        if a >= n:   # starts beyond the strip: maybe wraps into it from the left
+            a, b = a - nx, b - nx
+        a, b = max(a, 0), min(b, n)
+        if b > a:
+            c["hot_x0"], c["hot_len"] = a, b - a
+        else:
+            c["hot_x0"], c["hot_len"] = 0, 0
+            c["Tr_hot"] = 0.0
+    o = Oracle(thermo.Config(**c))
+    o.init_fields(*crop)
+    o.step(steps)
+    mo = o.moments()
+    return {k: mo[k][:, margin:margin + w] for k in ("rho", "ux", "uy", "T")}
+
+
+def boiling_fields(nx, ny, p, seed):
+    """The boiling layout's initial state (liquid below 3 ny / 4, vapour above,
+    tanh edge of width 4) with seeded perturbations of rho, u and T so that
+    every term of the step is active."""
+    rho = inputs.layer(nx, ny, p.rho_v, p.rho_l, 0.75 * ny, 4.0)
+    rho = inputs.perturbed(rho, 0.02, seed)
+    ux, uy = inputs.random_velocity((ny, nx), 0.01 * p.c, seed + 1)
+    T = inputs.perturbed(np.full((ny, nx), p.T0), 0.02, seed + 2)
+    return rho, ux, uy, T

@@ -9,7 +9,7 @@ than that reproduces the crop's centre exactly."""
 import numpy as np
 import pytest
 
-from gpu_common import gpu_case, oracle_case, rel_err, slab_fields
+from gpu_common import boiling_fields, gpu_case, oracle_case, rel_err, slab_fields, strip_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -65,3 +65,31 @@ def test_large_lattice_windows_match_oracle(gpu_lib):
             got = np.roll(m[k], (-y0, -x0), axis=(0, 1))[:w, :w]
             ref = mo[k][margin:margin + w, margin:margin + w]
             assert np.abs(got - ref).max() < TOL["f32"] * p.c, (y0, x0, k)
+
+
+def test_boiling_workload_full_size_strips_match_oracle(gpu_lib):
+    # the benchmark's own configuration at its full size (4096 x 1024, walls,
+    # body force, a 32-cell hot wall segment at the benchmark's seeded place),
+    # FP32 storage, from a perturbed boiling layout so every term acts: after
+    # 10 steps, three full-height strips of 48 columns (one over the hot
+    # segment's start, one across the periodic seam, one seeded) against the
+    # oracle run on the periodic crops (tests/gpu_common.strip_reference)
+    from paper_2106_01557_gb300 import inputs
+    nx, ny, steps = 4096, 1024, 10
+    hot_x0 = inputs.hot_spot_x0(nx, 32, seed=3)
+    cfg = dict(nx=nx, ny=ny, walls=1, accel_y=-1e-5, Tr_bottom=0.8, Tr_hot=0.95, hot_x0=hot_x0, hot_len=32)
+    p = oracle_case(64, 64).p
+    fields = boiling_fields(nx, ny, p, seed=31)
+    g = gpu_case(nx, ny, "f32", **{k: v for k, v in cfg.items() if k not in ("nx", "ny")})
+    g.set_fields(*fields)
+    g.step(steps)
+    m = g.moments()
+    rng = np.random.default_rng(32)
+    for x0 in ((hot_x0 - 20) % nx, nx - 24, int(rng.integers(0, nx))):
+        ref = strip_reference(fields, cfg, x0, 48, 24, steps)
+        for k in ("rho", "T"):
+            got = np.roll(m[k], -x0, axis=1)[:, :48]
+            assert rel_err(got, ref[k]) < TOL["f32"], (x0, k)
+        for k in ("ux", "uy"):
+            got = np.roll(m[k], -x0, axis=1)[:, :48]
+            assert np.abs(got - ref[k]).max() < TOL["f32"] * p.c, (x0, k)

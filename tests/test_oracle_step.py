@@ -315,3 +315,22 @@ def test_bulk_liquid_unstable_at_low_temperature():
     # temperatures start at 0.75
     o = Oracle(thermo.Config(nx=4, ny=4, Tr0=0.6))
     assert _growth(o, o.p.rho_l) > 1.01
+
+
+def test_strip_reference_reproduces_the_full_lattice():
+    # the periodic-crop reference that the full-size GPU parity test uses,
+    # checked against the oracle on the whole lattice: walls, body force and a
+    # hot wall segment that the strips cut at either end, and a strip across
+    # the periodic seam
+    from gpu_common import boiling_fields, strip_reference
+    cfg = dict(nx=192, ny=40, walls=1, accel_y=-1e-5, Tr_bottom=0.8, Tr_hot=0.95, hot_x0=100, hot_len=32)
+    o = Oracle(thermo.Config(**cfg))
+    fields = boiling_fields(192, 40, o.p, seed=21)
+    o.init_fields(*fields)
+    o.step(10)
+    full = o.moments()
+    for x0 in (80, 120, 0, 170):
+        ref = strip_reference(fields, cfg, x0, 48, 24, 10)
+        for k in ("rho", "ux", "uy", "T"):
+            got = np.roll(full[k], -x0, axis=1)[:, :48]
+            assert np.abs(got - ref[k]).max() <= 1e-12 * np.abs(full[k]).max(), (x0, k)
