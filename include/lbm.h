@@ -239,7 +239,7 @@ int lbm_batch_destroy(lbm_batch* b);
 /* ---- Learned surrogate ---------------------------------------------------
  * A convolutional neural operator that advances the macroscopic fields
  * (rho, u_x, u_y, T) of a periodic case by K lattice steps in one jump, with
- * the LB step as its fallback and judge. Not in the paper: an extension of
+ * the LB step as its fallback and arbiter. Not in the paper: an extension of
  * the method for faster time-to-solution. Network (3x3 convolutions,
  * periodic padding, bias; BF16 tensor-core kernels, FP32 accumulation):
  *   h0 = lift(x); h_{b+1} = h_b + conv_b2(relu(conv_b1(relu(h_b))));
@@ -288,7 +288,7 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
 /* Rollout on a periodic FP32/FP64 case: njumps times, snapshot the state,
  * predict K steps ahead, re-initialise the populations from the predicted
  * fields, and let the LB run verify_steps steps from that surrogate state
- * (the LB as judge: a state it cannot advance counts as a rejected jump);
+ * (the LB as arbiter: a state it cannot advance counts as a rejected jump);
  * then compare before and after the two quantities the model conserves, mass and total
  * energy (lbm_conservation out[0] and out[4]; sum rho e_k is not one of
  * them, it exchanges latent heat with the pair potential as liquid

@@ -23,7 +23,7 @@ What it computes, in the paper's notation (Huang, Wu & Adams, PRL 2021,
   psi + kappa/2 |grad rho|^2), used to pin K_EOS, K_INT against the paper's
   sigma = 0.01, W = 10 at T_r = 0.8 (Sec. "simulations", after Eq. 19).
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent:
 * c_v = 3R/2 (the Maxwellian of Eq. 3 is three-dimensional);
 * C_ref = rho_v(T_r0) c_v (C_ref / (rho c_v) above about 2 makes the heat-
   conduction part linearly unstable, so the smallest bulk capacity is used);

@@ -494,10 +494,10 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
     cudaStream_t hs = lbm_internal_stream(h);
     using clk = std::chrono::steady_clock;
     auto ms = [](clk::time_point a, clk::time_point b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
-    double t_prep = 0, t_net = 0, t_judge = 0, t_ver = 0;
+    double t_prep = 0, t_net = 0, t_check = 0, t_ver = 0;
     // The state's fields and conservation record are read in one FP32 pass
     // (FP64 sums): the network sees BF16 inputs and the thresholds are far
-    // above FP32 rounding. After an accepted jump the read-out that judged it
+    // above FP32 rounding. After an accepted jump the read-out that checked it
     // is the next jump's input; a rejected jump keeps the state it read.
     double c0[6], c1[6];
     bool have_state = false;  // s->fields and c0 describe the current state
@@ -542,14 +542,14 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
         }
         auto t1 = clk::now();
         t_ver += ms(tv, t1);
-        t_judge += ms(tn, tv);
+        t_check += ms(tn, tv);
         if (physical && !diverged) {
-            // the prediction has been consumed: its buffer takes the judged state's fields
+            // the prediction has been consumed: its buffer takes the checked state's fields
             rc = lbm_internal_read_fast(h, s->pred, c1);
             if (rc == LBM_ERR_DIVERGED) diverged = true;
             else if (rc) return rc;
             const auto t2 = clk::now();
-            t_judge += ms(t1, t2);
+            t_check += ms(t1, t2);
             t1 = t2;
             if (!diverged) {
                 dm = std::fabs(c1[0] / c0[0] - 1.0);
@@ -587,11 +587,11 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
             have_state = true;
         }
     }
-    t_sur = t_net + t_judge + t_ver;
+    t_sur = t_net + t_check + t_ver;
     if (stats) {
         stats[0] = acc; stats[1] = fb; stats[2] = t_sur; stats[3] = t_lb; stats[4] = max_dm; stats[5] = max_de;
         stats[6] = all_dm; stats[7] = all_de; stats[8] = all_da; stats[9] = n_bad;
-        stats[10] = n_div; stats[11] = t_prep; stats[12] = t_net; stats[13] = t_judge; stats[14] = t_ver;
+        stats[10] = n_div; stats[11] = t_prep; stats[12] = t_net; stats[13] = t_check; stats[14] = t_ver;
     }
     return LBM_OK;
 }

@@ -466,7 +466,7 @@ class Surrogate:
         """drift_tol: largest relative change of mass and of total energy per
         jump; iface_tol: largest mean interface displacement per jump, in
         lattice units; verify_steps: LB steps run from each surrogate state
-        before it is judged (default K / 10). Every jump advances the lattice
+        before it is checked (default K / 10). Every jump advances the lattice
         by K + verify_steps steps."""
         import torch
         torch.cuda.current_stream().synchronize()
