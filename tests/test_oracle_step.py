@@ -309,6 +309,22 @@ def test_moving_vapour_linearly_stable():
         assert _growth(o, o.p.rho_v, U=U) < 1 + 1e-7, U
 
 
+def test_moving_liquid_stability_limit():
+    # with the default rates the uniform liquid is linearly stable at rest
+    # but not in motion: at T_r = 0.8 it grows above about 0.034 c_s (0.012
+    # at T_r = 0.75, 0.093 at 0.9; the vapour holds to 0.2 c_s), a thermal
+    # mode, as the rates of g move the limit most. sigma_eps = 1.4, a rate
+    # the paper leaves free, keeps both phases stable at rest and the liquid
+    # to 0.15 c_s
+    o = Oracle(thermo.Config(nx=4, ny=4))
+    assert _growth(o, o.p.rho_l, ngrid=20, U=0.03) < 1 + 1e-7
+    assert _growth(o, o.p.rho_l, ngrid=20, U=0.05) > 1 + 1e-3
+    o = Oracle(thermo.Config(nx=4, ny=4, sig_eps=1.4))
+    for rho0 in (o.p.rho_l, o.p.rho_v):
+        assert _growth(o, rho0, ngrid=20) < 1 + 1e-7
+    assert _growth(o, o.p.rho_l, ngrid=20, U=0.1) < 1 + 1e-7
+
+
 def test_bulk_liquid_unstable_at_low_temperature():
     # the same rates leave the dense liquid linearly unstable at T_r = 0.6
     # (thermo-acoustic growth of a long wave), the reason the sweep's
