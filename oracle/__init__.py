@@ -9,8 +9,8 @@ FP64), built here with gcc and called through ctypes.
 
 Parity status of each function is stated in its docstring. "Parity
 unpinned" beyond GPU-vs-oracle: which of gamma1, gamma2 goes to the e and eps
-rows of the g source q_m (SM Eq. S4b), the sign of its heat-flux rows, and
-the velocity couplings of S in row e (SM Eq. S5a). The coefficient k s_eps omega_e of S
+rows of the g source q_m (SM Eq. S4b) and the sign of its heat-flux rows.
+The coefficient k s_eps omega_e of S
 (row e, column eps; SM Eq. S5a) is pinned only through the linear stability
 of the moving vapour, and the walls (not in the paper) only through textbook
 flows (Poiseuille, steady conduction).

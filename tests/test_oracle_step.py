@@ -256,15 +256,16 @@ def test_single_node_collision_budget():
     assert gb.sum() == pytest.approx(gl.sum() + p.dt * q, rel=1e-14)
 
 
-def _growth(o, rho0, ngrid=10, U=0.0):
-    """Largest amplification factor of the linearised step (collision
-    Jacobian by central differences of the oracle's node collision, pair
-    force through the neighbour densities, streaming as a phase) over a
-    grid of wave vectors, around the uniform state at density rho0 moving
-    along x at U c_s (at rest for U = 0)."""
+def _linearised_step(o, rho0, ux=0.0, uy=0.0):
+    """The step linearised around the uniform state at density rho0, moving
+    at (ux, uy) c_s: collision Jacobian by central differences of the
+    oracle's node collision, pair force through the neighbour densities,
+    streaming as a phase. Returns (kx, ky) -> the 18 x 18 amplification
+    matrix of the Fourier mode exp(i(kx x + ky y)) of (f, g)."""
     p = o.p
     n = 4
-    o.init_fields(np.full((n, n), rho0), np.full((n, n), U * p.cs), np.zeros((n, n)), np.full((n, n), p.T0))
+    o.init_fields(np.full((n, n), rho0), np.full((n, n), ux * p.cs), np.full((n, n), uy * p.cs),
+                  np.full((n, n), p.T0))
     x0 = np.concatenate([o.f[:, 0, 0], o.g[:, 0, 0], np.full(9, rho0)])
 
     def col(x):
@@ -278,14 +279,26 @@ def _growth(o, rho0, ngrid=10, U=0.0):
         xp[j] += h
         xm[j] -= h
         J[:, j] = (col(xp) - col(xm)) / (2 * h)
-    worst = 0.0
     sel = np.concatenate([np.ones(9), np.zeros(9)])
+
+    def amplification(kx, ky):
+        ph = np.exp(1j * (kx * EX + ky * EY))
+        A = J[:, :18].astype(complex) + np.outer(J[:, 18:] @ ph, sel)
+        P = np.diag(np.concatenate([np.conj(ph), np.conj(ph)]))
+        return P @ A
+
+    return amplification
+
+
+def _growth(o, rho0, ngrid=10, U=0.0):
+    """Largest amplification factor of the linearised step over a grid of
+    wave vectors, around the uniform state at density rho0 moving along x at
+    U c_s (at rest for U = 0)."""
+    amplification = _linearised_step(o, rho0, ux=U)
+    worst = 0.0
     for kx in np.linspace(0, np.pi, ngrid):
         for ky in np.linspace(0, np.pi, ngrid):
-            ph = np.exp(1j * (kx * EX + ky * EY))
-            A = J[:, :18].astype(complex) + np.outer(J[:, 18:] @ ph, sel)
-            P = np.diag(np.concatenate([np.conj(ph), np.conj(ph)]))
-            worst = max(worst, np.abs(np.linalg.eigvals(P @ A)).max())
+            worst = max(worst, np.abs(np.linalg.eigvals(amplification(kx, ky))).max())
     return worst
 
 
@@ -307,6 +320,33 @@ def test_moving_vapour_linearly_stable():
     o = Oracle(thermo.Config(nx=4, ny=4))
     for U in (0.0, 0.1, 0.2):
         assert _growth(o, o.p.rho_v, U=U) < 1 + 1e-7, U
+
+
+def _sound_decay_asymmetry(o, rho0, U, k, along_x):
+    """(d_down - d_up) / (d_down + d_up) for the two sound modes of wave
+    number k travelling along the flow of the uniform state at density rho0
+    moving at U c_s (along x or y): d = -ln|lambda| per step, the modes being
+    the two hydrodynamic eigenvalues of the linearised step whose phases,
+    with the Doppler phase k U c_s dt taken off, are the extremes."""
+    amplification = _linearised_step(o, rho0, ux=U if along_x else 0.0, uy=0.0 if along_x else U)
+    ev = np.linalg.eigvals(amplification(k, 0.0) if along_x else amplification(0.0, k))
+    hyd = ev[np.abs(ev) > 0.8] * np.exp(1j * k * U * o.p.cs * o.p.dt)
+    down, up = hyd[np.argmin(np.angle(hyd))], hyd[np.argmax(np.angle(hyd))]
+    d_down, d_up = -np.log(abs(down)), -np.log(abs(up))
+    return (d_down - d_up) / (d_down + d_up)
+
+
+def test_sound_decays_alike_up_and_down_a_moving_vapour():
+    # Galilean invariance of the normal stress (Eq. 6b): in the frame of a
+    # uniform flow, sound going down- and upstream decays alike. Pins the
+    # velocity couplings of S in row e (SM Eq. S5a): h u_x s_q omega_e acts on
+    # waves along x in a flow along x, h u_y s_q omega_e along y. Vapour at
+    # 0.05 c_s, wavelength 64: measured 1.2e-4 (the residual grows as U^3:
+    # 2.1e-2 at 0.2 c_s, the D2Q9 lattice's missing cubic moments); dropping
+    # the coupling gives 1.9e-2, linear in U
+    o = Oracle(thermo.Config(nx=4, ny=4))
+    for along_x in (True, False):
+        assert abs(_sound_decay_asymmetry(o, o.p.rho_v, 0.05, 2 * np.pi / 64, along_x)) < 2e-3, along_x
 
 
 def test_moving_liquid_stability_limit():
