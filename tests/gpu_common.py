@@ -35,6 +35,32 @@ def rel_err(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
+def cross_flow_residual(make, phase, U, along_x, n=64, width=8, amp=1e-3, steps=400):
+    """A density wave of relative amplitude amp along one axis of a periodic
+    lattice (n nodes along the wave, `width` across) whose fluid, the bulk
+    liquid or vapour (phase "l" or "v"), moves uniformly at U c_s along the
+    other axis. With nothing varying along the flow, the Navier-Stokes
+    momentum equation along the flow (Eq. 6b) reduces to
+    d(rho u_par)/dt = U c_s d(rho)/dt, so the flow velocity stays exactly
+    U c_s everywhere. make(nx, ny) returns a lattice with .p (cs, rho_v,
+    rho_l, T0), set_fields, step and moments. Returns
+    max |u_par - U c_s| / (amp c_s) after `steps` steps."""
+    shape = (width, n) if along_x else (n, width)
+    lat = make(shape[1], shape[0])
+    p = lat.p
+    rho0 = p["rho_l"] if phase == "l" else p["rho_v"]
+    wave = np.sin(2 * np.pi * np.arange(n) / n)
+    rho = rho0 * (1 + amp * (wave[None, :] if along_x else wave[:, None])) * np.ones(shape)
+    flow = np.full(shape, U * p["cs"])
+    if along_x:
+        lat.set_fields(rho, 0 * rho, flow, 0 * rho + p["T0"])
+    else:
+        lat.set_fields(rho, flow, 0 * rho, 0 * rho + p["T0"])
+    lat.step(steps)
+    u_par = lat.moments()["uy" if along_x else "ux"]
+    return float(np.abs(u_par - U * p["cs"]).max() / (amp * p["cs"]))
+
+
 def shear_wave_viscous_work_factor(make, nx=4, N=128, amp=0.1):
     """A decaying shear wave u_x = A(t) sin(ky) in a uniform vapour, on a
     lattice make(nx, N) with .p (cs, rho_v, T0), set_fields, step and

@@ -72,6 +72,15 @@ class _GpuLattice:
         self.moments, self.step, self.set_fields = self.g.moments, self.g.step, self.g.set_fields
 
 
+def test_cross_flow_pin_on_gpu(gpu_lib):
+    # the oracle's Galilean-invariance pin of S's row-pxy velocity couplings
+    # (a density wave leaves a uniform cross-flow uniform) on the FP64 GPU path
+    from gpu_common import cross_flow_residual
+    for along_x in (True, False):
+        assert cross_flow_residual(_GpuLattice, "l", 0.03, along_x) < 5e-4, along_x
+        assert cross_flow_residual(_GpuLattice, "v", 0.1, along_x) < 3e-3, along_x
+
+
 def test_wall_pins_on_gpu(gpu_lib):
     # the oracle's pins of the walls (Poiseuille parabola, steady conduction)
     # on the FP64 GPU path

@@ -128,29 +128,6 @@ def test_viscous_dissipation_term_gives_the_viscous_work():
     assert shear_wave_viscous_work_factor(_Lat) == pytest.approx(1.0, abs=0.05)
 
 
-def _cross_flow_residual(rho0, U, along_x, n=64, amp=1e-3, steps=400):
-    """A density wave of relative amplitude amp along one axis of a periodic
-    n x 4 lattice whose fluid moves uniformly at U c_s along the other axis.
-    With nothing varying along the flow, the Navier-Stokes momentum equation
-    along the flow (Eq. 6b) reduces to d(rho u_par)/dt = U c_s d(rho)/dt, so
-    the flow velocity stays exactly U c_s everywhere. Returns
-    max |u_par - U c_s| / (amp c_s) after `steps` steps."""
-    shape = (4, n) if along_x else (n, 4)
-    o = Oracle(thermo.Config(nx=shape[1], ny=shape[0]))
-    p = o.p
-    s = np.arange(n, dtype=float)
-    wave = np.sin(2 * np.pi * s / n)
-    rho = rho0 * (1 + amp * (wave[None, :] if along_x else wave[:, None])) * np.ones(shape)
-    flow = np.full(shape, U * p.cs)
-    if along_x:
-        o.init_fields(rho, 0 * rho, flow, 0 * rho + p.T0)
-    else:
-        o.init_fields(rho, flow, 0 * rho, 0 * rho + p.T0)
-    o.step(steps)
-    u_par = o.moments()["uy" if along_x else "ux"]
-    return np.abs(u_par - U * p.cs).max() / (amp * p.cs)
-
-
 def test_density_wave_leaves_a_uniform_cross_flow_uniform():
     # Galilean invariance of the shear stress: pins the velocity couplings of
     # S in row pxy (SM Eq. S5a), b u_y s_q omega_p (wave along x, flow along
@@ -160,10 +137,10 @@ def test_density_wave_leaves_a_uniform_cross_flow_uniform():
     # vapour at 0.1 c_s; dropping either coupling gives 3.2e-3 and 2.3e-2,
     # flipping its sign twice that. The liquid moves below its stability
     # limit (test_moving_liquid_stability_limit).
-    p = Oracle(thermo.Config(nx=4, ny=4)).p
+    from gpu_common import cross_flow_residual
     for along_x in (True, False):
-        assert _cross_flow_residual(p.rho_l, 0.03, along_x) < 5e-4, along_x
-        assert _cross_flow_residual(p.rho_v, 0.1, along_x) < 3e-3, along_x
+        assert cross_flow_residual(_OracleLattice, "l", 0.03, along_x) < 5e-4, along_x
+        assert cross_flow_residual(_OracleLattice, "v", 0.1, along_x) < 3e-3, along_x
 
 
 class _OracleLattice:
@@ -173,7 +150,7 @@ class _OracleLattice:
         c = thermo.Config(nx=nx, ny=ny, **cfg)
         self.o = Oracle(c)
         p = self.o.p
-        self.p = {"cs": p.cs, "dt": p.dt, "rho_v": p.rho_v, "T0": p.T0, "Tc": p.Tc}
+        self.p = {"cs": p.cs, "dt": p.dt, "rho_v": p.rho_v, "rho_l": p.rho_l, "T0": p.T0, "Tc": p.Tc}
         self.s_p = c.s_p
         self.moments, self.step, self.set_fields = self.o.moments, self.o.step, self.o.init_fields
 
