@@ -16,6 +16,10 @@
  *   - status: every function returns 0 (LBM_OK) or a negative LBM_ERR_*.
  *     lbm_last_error() returns a message for the calling thread's last
  *     failure. No call aborts the process.
+ *   - NULL: a NULL handle or required pointer returns LBM_ERR_ARG before any
+ *     device work; the *_destroy calls take NULL as a no-op (LBM_OK); the
+ *     queries return -1 (lbm_step_count) or 0 (the node, byte and parameter
+ *     counts) for a NULL handle; lbm_default_config(NULL, ...) does nothing.
  *   - units: lattice spacing dx = 1 and R, a~, b~ as configured; the lattice
  *     speed is c = sqrt(3) c_s with c_s from Eq. 19, so the time step is
  *     dt = 1 / c (not 1).

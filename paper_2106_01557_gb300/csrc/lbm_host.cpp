@@ -182,6 +182,7 @@ extern "C" {
 const char* lbm_last_error(void) { return g_err.c_str(); }
 
 void lbm_default_config(lbm_config* c, int32_t nx, int32_t ny) {
+    if (!c) return;
     std::memset(c, 0, sizeof(*c));
     c->nx = nx;
     c->ny = ny;

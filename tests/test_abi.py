@@ -112,3 +112,36 @@ def test_library_maxwell_matches_oracle_on_host(lib):
         assert ps == pytest.approx(cfg.K_EOS * ops, rel=1e-12)
     with pytest.raises(lbm.LbmError):
         lbm.maxwell(cfg, 1.1)
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    # every entry point checks its handle and required pointers before any
+    # device work: LBM_ERR_ARG, a no-op for the destroy calls, -1 or 0 for the
+    # count queries, and lbm_default_config(NULL) returns without writing
+    from paper_2106_01557_gb300 import lbm
+    l = lbm.load()
+    skip = {"lbm_last_error"}
+    noop = {"lbm_destroy", "lbm_batch_destroy", "lbm_surrogate_destroy"}
+    queries = {"lbm_step_count": -1, "lbm_bytes_per_step": 0.0, "lbm_batch_nodes": 0,
+               "lbm_batch_bytes_per_step": 0.0, "lbm_surrogate_num_params": 0}
+    for name, (args, res) in lbm.SIGNATURES.items():
+        if name in skip:
+            continue
+        vals = []
+        for a in args:
+            if a in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64):
+                vals.append(0)
+            elif a is ctypes.c_double:
+                vals.append(0.8)
+            else:
+                vals.append(None)
+        got = getattr(l, name)(*vals)
+        if name == "lbm_default_config":
+            assert got is None
+        elif name in noop:
+            assert got == 0, name
+        elif name in queries:
+            assert got == queries[name], name
+        else:
+            assert got == -1, name
+            assert l.lbm_last_error(), name
