@@ -353,16 +353,18 @@ def test_moving_liquid_stability_limit():
     # with the default rates the uniform liquid is linearly stable at rest
     # but not in motion: at T_r = 0.8 it grows above about 0.034 c_s (0.012
     # at T_r = 0.75, 0.093 at 0.9; the vapour holds to 0.2 c_s), a thermal
-    # mode, as the rates of g move the limit most. sigma_eps = 1.4, a rate
-    # the paper leaves free, keeps both phases stable at rest and the liquid
-    # to 0.15 c_s
+    # mode, as the rates of g move the limit most. Two rates of g that the
+    # paper leaves free, sigma_eps = 1.4 and sigma_p = 1.8, keep both phases
+    # stable at rest down to T_r = 0.65 (the defaults: 0.75) and the moving
+    # liquid to 0.157 c_s at T_r = 0.8 (0.106 at 0.75, 0.074 at 0.7)
     o = Oracle(thermo.Config(nx=4, ny=4))
     assert _growth(o, o.p.rho_l, ngrid=20, U=0.03) < 1 + 1e-7
     assert _growth(o, o.p.rho_l, ngrid=20, U=0.05) > 1 + 1e-3
-    o = Oracle(thermo.Config(nx=4, ny=4, sig_eps=1.4))
-    for rho0 in (o.p.rho_l, o.p.rho_v):
-        assert _growth(o, rho0, ngrid=20) < 1 + 1e-7
-    assert _growth(o, o.p.rho_l, ngrid=20, U=0.1) < 1 + 1e-7
+    for Tr in (0.65, 0.8):
+        o = Oracle(thermo.Config(nx=4, ny=4, Tr0=Tr, sig_eps=1.4, sig_p=1.8))
+        for rho0 in (o.p.rho_l, o.p.rho_v):
+            assert _growth(o, rho0, ngrid=20) < 1 + 1e-7, Tr
+    assert _growth(o, o.p.rho_l, ngrid=20, U=0.12) < 1 + 1e-7
 
 
 def test_bulk_liquid_unstable_at_low_temperature():
