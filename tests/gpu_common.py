@@ -5,7 +5,9 @@ import numpy as np
 from oracle import Oracle, thermo
 from paper_2106_01557_gb300 import inputs
 
-OPTS = ("walls", "accel_x", "accel_y", "Tr_bottom", "Tr_top", "Tr_hot", "hot_x0", "hot_len", "Tr0")
+OPTS = ("walls", "accel_x", "accel_y", "Tr_bottom", "Tr_top", "Tr_hot", "hot_x0", "hot_len", "Tr0",
+        "varpi", "gamma1", "gamma2", "s_p", "s_eps", "sig_e", "sig_eps", "sig_p", "tau_j_v", "tau_j_l",
+        "c_v", "C_ref")
 
 
 def oracle_case(nx, ny, **kw):

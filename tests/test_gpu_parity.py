@@ -69,6 +69,25 @@ def test_walls_body_force_hot_spot_match_oracle(gpu_lib, prec):
     assert rel_err(gg, o.g) < TOL[prec]
 
 
+# every model coefficient and relaxation rate away from its default, so that
+# a kernel that kept one fixed, or took one from the wrong slot, fails
+RATES = dict(Tr0=0.85, varpi=0.2, gamma1=-1.5, gamma2=2.5, s_p=1.2, s_eps=1.3, sig_e=0.9, sig_eps=1.4,
+             sig_p=1.8, tau_j_v=0.3, tau_j_l=2.0, c_v=2.0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_non_default_rates_match_oracle(gpu_lib, prec):
+    o, g = _pair(100, 37, prec, seed=7, **RATES)
+    p = g.params()
+    for k in ("T0", "rho_v", "rho_l", "cs", "Cref", "beta", "kS", "hS", "bS", "se", "sq"):
+        assert p[k] == pytest.approx(getattr(o.p, k), rel=1e-13), k
+    o.step(10)
+    g.step(10)
+    f, gg = g.get_populations()
+    assert rel_err(f, o.f) < TOL[prec]
+    assert rel_err(gg, o.g) < TOL[prec]
+
+
 def test_rest_state_stays_at_rest(gpu_lib):
     g = gpu_case(64, 64, "f64")
     p = g.params()
