@@ -53,15 +53,21 @@ def test_batch_equals_single_cases(gpu_lib, prec):
             b.close()
 
 
+# per-case model coefficients and relaxation rates, so that a batch kernel
+# that took one from another case's parameter block would fail
+CASE_RATES = [{}, dict(sig_eps=1.4, sig_p=1.8), dict(s_p=1.2, varpi=0.2, gamma1=-1.5, gamma2=2.5),
+              dict(tau_j_v=0.3, tau_j_l=2.0, sig_e=0.9, s_eps=1.3, c_v=2.0)]
+
+
 def test_batch_matches_oracle_and_records(gpu_lib):
     from oracle import Oracle, thermo
     from paper_2106_01557_gb300 import lbm
     cases = _cases()
-    cfgs = [lbm.default_config(nx, ny, precision="f32", Tr0=tr) for nx, ny, tr, _ in cases]
+    cfgs = [lbm.default_config(nx, ny, precision="f32", Tr0=tr, **r) for (nx, ny, tr, _), r in zip(cases, CASE_RATES)]
     b = lbm.Batch(cfgs)
     ors = []
     for i, (nx, ny, tr, R) in enumerate(cases):
-        o = Oracle(thermo.Config(nx=nx, ny=ny, Tr0=tr))
+        o = Oracle(thermo.Config(nx=nx, ny=ny, Tr0=tr, **CASE_RATES[i]))
         p = {"rho_v": o.p.rho_v, "rho_l": o.p.rho_l, "c": o.p.c, "T0": o.p.T0}
         fl = _fields(nx, ny, p, R, 60 + i)
         o.init_fields(*fl)
