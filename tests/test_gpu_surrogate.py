@@ -164,6 +164,25 @@ def test_training_reduces_loss(gpu_lib):
     assert np.mean(last) < 0.1 * np.mean(first)
 
 
+def test_first_adam_step_is_the_textbook_update(gpu_lib):
+    # from zero moments the bias-corrected Adam update (beta1 0.9, beta2
+    # 0.999, eps 1e-8) is -lr g / (|g| + eps): a step of lr against the sign
+    # of the gradient wherever |g| >> eps, and never longer than lr
+    S, p, s = _make(blocks=2, seed=11)
+    x = _fields(2, 16, 32, 30)
+    t = x + 0.3 * _fields(2, 16, 32, 31)
+    a, b = _to_dev(x), _to_dev(t)
+    w0 = s.get_params().astype(np.float64)
+    _, g = s.loss_grad(a, b)
+    lr = 1e-3
+    s.train_step(a, b, lr=lr)
+    dw = s.get_params().astype(np.float64) - w0
+    big = np.abs(g) > 1e-4
+    assert big.sum() > 1000
+    assert np.abs(dw[big] / lr + np.sign(g[big])).max() < 1e-2
+    assert np.abs(dw).max() <= lr * (1 + 1e-3)
+
+
 def test_rollout_falls_back_and_accepts(gpu_lib):
     from oracle import Oracle, thermo
     from paper_2106_01557_gb300 import inputs, lbm
