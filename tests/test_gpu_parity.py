@@ -156,6 +156,38 @@ def test_checkpoint_resume_is_bitwise(gpu_lib, tmp_path):
         assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
 
 
+def test_checkpoint_of_another_lattice_or_a_short_file_is_refused(gpu_lib, tmp_path):
+    # the header names the lattice (nx, ny, precision, walls): a checkpoint
+    # of another one is refused with LBM_ERR_ARG, a short or missing file
+    # with LBM_ERR_IO, before any device copy, and the handle stays usable
+    from paper_2106_01557_gb300 import lbm
+    o = oracle_case(72, 40)
+    fields = slab_fields(o, seed=13)
+    a = gpu_case(72, 40, "f32")
+    a.set_fields(*fields)
+    a.step(3)
+    path = tmp_path / "ck.bin"
+    a.save(str(path))
+    short = tmp_path / "short.bin"
+    short.write_bytes(path.read_bytes()[: path.stat().st_size // 2])
+    for other, code in ((gpu_case(72, 48, "f32"), -1), (gpu_case(72, 40, "f16s"), -1),
+                        (gpu_case(72, 40, "f32", walls=1), -1)):
+        with pytest.raises(lbm.LbmError) as e:
+            other.load(str(path))
+        assert e.value.code == code
+    b = gpu_case(72, 40, "f32")
+    b.set_fields(*fields)
+    for bad in (short, tmp_path / "missing.bin"):
+        with pytest.raises(lbm.LbmError) as e:
+            b.load(str(bad))
+        assert e.value.code == -7
+    assert b.steps == 0
+    b.step(3)
+    fa, ga = a.get_populations()
+    fb, gb = b.get_populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
 def test_divergence_is_reported(gpu_lib):
     from paper_2106_01557_gb300 import lbm
     o = oracle_case(64, 64)
