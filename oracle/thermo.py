@@ -156,6 +156,35 @@ def equal_area_residual(T, rho_v, rho_l, ps, a_t, b_t, R):
     return val
 
 
+def latent_heat(T, a_t, b_t, R, K_EOS=1.0):
+    """Latent heat of vaporisation per unit mass on the coexistence curve of
+    Eq. 17 at temperature T. The internal energy per unit mass of the EOS
+    fluid is c_v T - K_EOS a~ rho (the repulsive part of Eq. 17 is linear in
+    T and stores no energy), and T, p are equal across coexistence, so
+    h_v - h_l = K_EOS a~ (rho_l - rho_v) + p_s (1/rho_v - 1/rho_l)."""
+    rv, rl, ps = maxwell(T, a_t, b_t, R)
+    return K_EOS * (a_t * (rl - rv) + ps * (1.0 / rv - 1.0 / rl))
+
+
+def stefan_number(Tr0, Tr1, cv, a_t, b_t, R, K_EOS):
+    """The Stefan number of the one-dimensional Stefan problem (text after
+    Eq. 21): rho_v c_v T_c (T_r1 - T_r0) / (rho_l h_lv), with the coexistence
+    densities and latent heat at T_r0; cv is the heat capacity per unit mass."""
+    Tc, _ = critical_point(a_t, b_t, R)
+    rv, rl, _ = maxwell(Tr0 * Tc, a_t, b_t, R)
+    return rv * cv * Tc * (Tr1 - Tr0) / (rl * latent_heat(Tr0 * Tc, a_t, b_t, R, K_EOS))
+
+
+def stefan_root(Ste):
+    """k > 0 with Ste / (exp(k^2) erf(k)) = k sqrt(pi) (Eq. 21): the interface
+    of the one-phase Stefan problem is at X = 2 k sqrt(alpha_v t) (Eq. 20)."""
+    f = lambda k: k * math.sqrt(math.pi) * math.exp(k * k) * math.erf(k) - Ste
+    hi = 1.0
+    while f(hi) < 0:
+        hi *= 2.0
+    return brentq(f, 1e-300, hi, xtol=1e-16, rtol=1e-15)
+
+
 # --------------------------------------------------------------------------
 # Square-gradient interface (pressure tensor of Eq. 11, kappa of Eq. 16)
 # --------------------------------------------------------------------------

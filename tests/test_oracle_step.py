@@ -369,8 +369,8 @@ def test_moving_liquid_stability_limit():
 
 def test_bulk_liquid_unstable_at_low_temperature():
     # the same rates leave the dense liquid linearly unstable at T_r = 0.6
-    # (thermo-acoustic growth of a long wave), the reason the sweep's
-    # temperatures start at 0.75
+    # (2% per step, fastest near the grid scale; below T_r = 0.75 a band of
+    # short waves grows), the reason the sweep's temperatures start at 0.75
     o = Oracle(thermo.Config(nx=4, ny=4, Tr0=0.6))
     assert _growth(o, o.p.rho_l) > 1.01
 

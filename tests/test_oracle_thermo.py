@@ -4,6 +4,7 @@ import json
 import math
 import os
 
+import numpy as np
 import pytest
 
 from oracle import thermo
@@ -123,3 +124,47 @@ def test_sound_speed_reduces_to_repulsive_stiffness():
     h = 1e-7
     fd = (thermo.p_cs(p.rho_l + h, p.T0, cfg.b_t, cfg.R) - thermo.p_cs(p.rho_l - h, p.T0, cfg.b_t, cfg.R)) / (2 * h)
     assert p.cs ** 2 == pytest.approx(cfg.K_INT ** 2 * cfg.K_EOS * fd, rel=1e-8)
+
+
+@pytest.mark.parametrize("Tr", [0.7, 0.8, 0.9])
+def test_latent_heat_obeys_clausius_clapeyron(Tr):
+    # h_lv = T (dp_s/dT) (1/rho_v - 1/rho_l), dp_s/dT by central differences
+    # of the coexistence pressure: a thermodynamic identity the enthalpy
+    # difference must satisfy
+    Tc, _ = thermo.critical_point(1.0, 4.0, 1.0)
+    T = Tr * Tc
+    rv, rl, _ = thermo.maxwell(T, 1.0, 4.0, 1.0)
+    d = 1e-5 * T
+    dps = (thermo.maxwell(T + d, 1.0, 4.0, 1.0)[2] - thermo.maxwell(T - d, 1.0, 4.0, 1.0)[2]) / (2 * d)
+    assert thermo.latent_heat(T, 1.0, 4.0, 1.0) == pytest.approx(T * dps * (1 / rv - 1 / rl), rel=1e-7)
+    assert thermo.latent_heat(T, 1.0, 4.0, 1.0, K_EOS=0.5) == pytest.approx(
+        0.5 * thermo.latent_heat(T, 1.0, 4.0, 1.0), rel=1e-14)
+
+
+def _enthalpy_front(Ste, t_end, N=200):
+    """Brute-force one-phase Stefan problem on [0, 1] (alpha = 1), the fixed-
+    grid enthalpy method: energy per cell in units of the vapour's
+    rho c_v (T_wall - T_sat); liquid at saturation holds -1/Ste (its latent
+    heat), vapour holds its temperature theta >= 0; theta = 1 at x = 0.
+    Returns the vaporised length after t_end."""
+    dx = 1.0 / N
+    dt = 0.4 * dx * dx
+    E = np.full(N, -1.0 / Ste)
+    for _ in range(int(round(t_end / dt))):
+        th = np.maximum(E, 0.0)
+        left = np.concatenate(([2.0 - th[0]], th[:-1]))
+        right = np.concatenate((th[1:], [th[-1]]))
+        E += dt * (left - 2 * th + right) / (dx * dx)
+    return dx * np.clip(1.0 + Ste * E, 0.0, 1.0).sum()
+
+
+@pytest.mark.parametrize("Ste", [0.1, 1.0])
+def test_stefan_root_gives_the_front_of_the_stefan_problem(Ste):
+    # Eq. 20, 21 against a brute-force solution of the problem they solve:
+    # measured 3e-5 (Ste 0.1) and 7e-5 (Ste 1); a root without the sqrt(pi)
+    # misses the front by 20-24%
+    k = thermo.stefan_root(Ste)
+    t = (0.6 / (2 * k)) ** 2
+    assert _enthalpy_front(Ste, t) == pytest.approx(2 * k * np.sqrt(t), rel=0.005)
+    # small-Ste limit: exp(k^2) erf(k) -> 2 k / sqrt(pi), so k -> sqrt(Ste / 2)
+    assert thermo.stefan_root(1e-6) == pytest.approx(np.sqrt(0.5e-6), rel=1e-6)
