@@ -169,7 +169,10 @@ def latent_heat(T, a_t, b_t, R, K_EOS=1.0):
 def stefan_number(Tr0, Tr1, cv, a_t, b_t, R, K_EOS):
     """The Stefan number of the one-dimensional Stefan problem (text after
     Eq. 21): rho_v c_v T_c (T_r1 - T_r0) / (rho_l h_lv), with the coexistence
-    densities and latent heat at T_r0; cv is the heat capacity per unit mass."""
+    densities at T_r0 and h_lv the EOS's latent heat there (`latent_heat`);
+    cv is the heat capacity per unit mass. The model's own energy balance
+    carries a larger latent heat when K_INT != 1, so which h_lv the paper
+    means is a reading."""
     Tc, _ = critical_point(a_t, b_t, R)
     rv, rl, _ = maxwell(Tr0 * Tc, a_t, b_t, R)
     return rv * cv * Tc * (Tr1 - Tr0) / (rl * latent_heat(Tr0 * Tc, a_t, b_t, R, K_EOS))

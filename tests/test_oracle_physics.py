@@ -195,3 +195,51 @@ def test_heated_poiseuille_temperature_shape():
     amp = (theta * shape).sum() / (shape * shape).sum()
     assert amp > 0
     assert np.abs(theta - amp * shape).max() < 0.02 * np.abs(amp * shape).max()
+
+
+def test_closed_box_heating_carries_the_models_latent_heat():
+    # A flat slab in a closed periodic box, heated uniformly by 0.005 T_c,
+    # evaporates part of its liquid and settles at a slightly higher
+    # temperature. The total energy of Eq. 8 (rho e_k + rho eps_p) stays
+    # conserved through the phase change (1.6e-7), so the final temperature
+    # follows the lever rule with the model's attraction energy a = G^2 / 2
+    # (rise 0.00032 T_c against 0.00042 predicted; the interfaces' own energy
+    # makes the rest), not with the EOS's K_EOS a~ (0.0016). With K_INT != 1
+    # the model's latent heat a (rho_l - rho_v) + p_s (1/rho_v - 1/rho_l) is
+    # 4.6 times the one Clausius-Clapeyron gives for Eq. 17 at T_r = 0.8.
+    from scipy.optimize import brentq
+    ny, nx = 128, 4
+    cfg = thermo.Config(nx=nx, ny=ny)
+    o = Oracle(cfg)
+    p = o.p
+    y = np.arange(ny, dtype=float)
+    r1 = thermo.planar_profile(p.T0, cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS, cfg.K_INT,
+                               np.minimum(y - ny / 4, 3 * ny / 4 - y))
+    rho = np.repeat(r1[:, None], nx, axis=1)
+    o.init_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+    o.step(10000)
+    m = o.moments()
+    T_before = m["T"].mean()
+    c0 = o.conservation()
+    o.init_fields(m["rho"], m["ux"], m["uy"], m["T"] + 0.005 * p.Tc)
+    c1 = o.conservation()
+    o.step(60000)
+    c2 = o.conservation()
+    rise = o.moments()["T"].mean() - T_before
+    assert abs(c2[4] / c1[4] - 1) < 1e-5
+    mass, heat = c0[0] / nx, (c1[4] - c0[4]) / nx
+
+    def energy(T, a):
+        rv, rl, _ = thermo.maxwell(T, cfg.a_t, cfg.b_t, cfg.R)
+        Ll = (mass - rv * ny) / (rl - rv)
+        return (ny - Ll) * (rv * p.cv * T - a * rv * rv) + Ll * (rl * p.cv * T - a * rl * rl)
+
+    def predicted_rise(a):
+        e0 = energy(T_before, a)
+        return brentq(lambda T: energy(T, a) - e0 - heat, T_before, T_before + 0.005 * p.Tc) - T_before
+
+    assert rise == pytest.approx(predicted_rise(p.a), rel=0.35)
+    assert rise < 0.5 * predicted_rise(cfg.K_EOS * cfg.a_t)
+    assert thermo.latent_heat(p.T0, cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS) * 4.5 < (
+        p.a * (p.rho_l - p.rho_v)
+        + cfg.K_EOS * thermo.maxwell(p.T0, cfg.a_t, cfg.b_t, cfg.R)[2] * (1 / p.rho_v - 1 / p.rho_l))
