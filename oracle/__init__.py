@@ -12,8 +12,9 @@ unpinned" beyond GPU-vs-oracle: which of gamma1, gamma2 goes to the e and eps
 rows of the g source q_m (SM Eq. S4b) and the sign of its heat-flux rows.
 The coefficient k s_eps omega_e of S
 (row e, column eps; SM Eq. S5a) is pinned only through the linear stability
-of the moving vapour, and the walls (not in the paper) only through textbook
-flows (Poiseuille, steady conduction).
+of the moving vapour, the walls (not in the paper) only through textbook
+flows (Poiseuille, steady conduction), and the open heated bottom (not in the
+paper) only through the Stefan problem (Eq. 20, 21).
 """
 from __future__ import annotations
 
@@ -70,6 +71,7 @@ class OrcParams(ctypes.Structure):
         ("ax", ctypes.c_double), ("ay", ctypes.c_double),
         ("T_bottom", ctypes.c_double), ("T_top", ctypes.c_double), ("T_hot", ctypes.c_double),
         ("hot_x0", ctypes.c_int), ("hot_len", ctypes.c_int),
+        ("bottom_outflow", ctypes.c_int), ("rho_out", ctypes.c_double),
     ]
 
 

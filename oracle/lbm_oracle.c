@@ -38,7 +38,10 @@
  *   density of the fluid node; the ghost density for the pair force beyond
  *   a wall equals the density of the adjacent fluid node (neutral wetting);
  *   heat-conduction rate sigma_j interpolated linearly in rho between
- *   tau_j,v at rho_v and tau_j,l at rho_l (clamped), and sigma_q = sigma_j.
+ *   tau_j,v at rho_v and tau_j,l at rho_l (clamped), and sigma_q = sigma_j;
+ *   an optional open, heated bottom for the one-dimensional Stefan problem
+ *   (non-equilibrium extrapolation to the vapour at T_bottom and the
+ *   liquid's saturation pressure).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -55,6 +58,8 @@ typedef struct {
     double ax, ay;
     double T_bottom, T_top, T_hot;
     int hot_x0, hot_len;
+    int bottom_outflow;  /* with walls: the bottom is an open, heated outflow */
+    double rho_out;      /* its density (vapour at T_bottom and the liquid's p_s) */
 } orc_params;
 
 /* SM Eq. S1: e_i / c for i = 0..8 */
@@ -131,6 +136,7 @@ static double rho_at(const orc_params* P, const double* rho, int x, int y)
 {
     x = wrap(x, P->nx);
     if (P->walls) {
+        if (y < 0 && P->bottom_outflow) return P->rho_out;
         if (y < 0) y = 0;
         if (y >= P->ny) y = P->ny - 1;
     } else {
@@ -311,6 +317,24 @@ static void node_collide(const orc_params* P, const double* fl, const double* gl
     matvec(MI, nb, gb);
 }
 
+/* Equilibrium populations M^-1 m^eq and M^-1 n^eq of a uniform, force-free
+ * state (rho, u, T) (SM Eq. S3a, S4a). */
+static void eq_populations(const orc_params* P, double rho, double ux, double uy, double T,
+                           double* feq, double* geq)
+{
+    node_state s;
+    memset(&s, 0, sizeof s);
+    s.rho = rho;
+    s.ux = ux;
+    s.uy = uy;
+    s.T = T;
+    s.rek = rho * P->cv * T + 0.5 * rho * (ux * ux + uy * uy);
+    node_terms t;
+    node_terms_build(P, &s, &t);
+    matvec(MI, t.meq, feq);
+    matvec(MI, t.neq, geq);
+}
+
 /* Rest equilibrium of g against which a fixed-temperature wall reflects. */
 static void g_rest_eq(const orc_params* P, double rho_w, double T_w, double* geq)
 {
@@ -370,9 +394,30 @@ int orc_step(const orc_params* P, double* f, double* g, int nsteps)
                 node_state s;
                 node_macro(P, fl, gl, rho, x, y, &s);
                 node_collide(P, fl, gl, &s, fb, gb);
+                const int open_bottom = P->walls && P->bottom_outflow && y == 0;
+                if (open_bottom) {
+                    /* Open, heated bottom (not in the paper, whose Stefan
+                     * problem takes its outflow scheme from another paper):
+                     * the ghost node below this one carries this node's
+                     * post-collision populations with their equilibrium
+                     * part moved to (rho_out, T_bottom) at this node's
+                     * velocity (non-equilibrium extrapolation), and streams
+                     * into the bottom row what enters from below. What
+                     * leaves through the bottom is lost. */
+                    double fe[9], ge[9], fo[9], go[9];
+                    eq_populations(P, s.rho, s.ux, s.uy, s.T, fe, ge);
+                    eq_populations(P, P->rho_out, s.ux, s.uy, P->T_bottom, fo, go);
+                    for (int i = 0; i < 9; ++i) {
+                        if (EY[i] != 1) continue;
+                        size_t pd = (size_t)wrap(x + EX[i], nx);
+                        fn[i * N + pd] = fb[i] + fo[i] - fe[i];
+                        gn[i * N + pd] = gb[i] + go[i] - ge[i];
+                    }
+                }
                 /* Eq. 12a, push form */
                 for (int i = 0; i < 9; ++i) {
                     int xd = x + EX[i], yd = y + EY[i];
+                    if (open_bottom && yd < 0) continue;
                     if (P->walls && (yd < 0 || yd >= ny)) {
                         int o = OPP[i];
                         fn[o * N + p] = fb[i];

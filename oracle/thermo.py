@@ -275,6 +275,7 @@ class Config:
     Tr_hot: float = 0.0            # hot-spot reduced T on the bottom wall
     hot_x0: int = 0
     hot_len: int = 0
+    bottom_outflow: int = 0        # with walls: open bottom at Tr_bottom (Stefan problem)
 
 
 @dataclass
@@ -326,6 +327,21 @@ class Params:
     T_hot: float
     hot_x0: int
     hot_len: int
+    bottom_outflow: int
+    rho_out: float
+
+
+def _outflow_density(cfg: Config, T0, rv):
+    """Density of the open bottom: the vapour at T_bottom and at the
+    saturation pressure of the liquid at T0 (the vapour branch of Eq. 17)."""
+    if not cfg.bottom_outflow:
+        return 0.0
+    Tc, _ = critical_point(cfg.a_t, cfg.b_t, cfg.R)
+    Tb = cfg.Tr_bottom * Tc
+    if not Tb > 0:
+        raise ValueError("an open bottom needs Tr_bottom > 0")
+    ps = maxwell(T0, cfg.a_t, cfg.b_t, cfg.R)[2]
+    return brentq(lambda r: p_eos(r, Tb, cfg.a_t, cfg.b_t, cfg.R) - ps, 1e-6 * rv, rv * T0 / Tb * 1.5)
 
 
 def derive_params(cfg: Config) -> Params:
@@ -362,7 +378,8 @@ def derive_params(cfg: Config) -> Params:
         sig0=cfg.sig_0, sige=cfg.sig_e, sigeps=cfg.sig_eps, sigp=cfg.sig_p,
         tauj_v=cfg.tau_j_v, tauj_l=cfg.tau_j_l, ax=cfg.accel_x, ay=cfg.accel_y,
         T_bottom=cfg.Tr_bottom * Tc, T_top=cfg.Tr_top * Tc, T_hot=cfg.Tr_hot * Tc,
-        hot_x0=cfg.hot_x0, hot_len=cfg.hot_len)
+        hot_x0=cfg.hot_x0, hot_len=cfg.hot_len,
+        bottom_outflow=cfg.bottom_outflow, rho_out=_outflow_density(cfg, T0, rv))
 
 
 def params_dict(p: Params) -> dict:

@@ -243,3 +243,42 @@ def test_closed_box_heating_carries_the_models_latent_heat():
     assert thermo.latent_heat(p.T0, cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS) * 4.5 < (
         p.a * (p.rho_l - p.rho_v)
         + cfg.K_EOS * thermo.maxwell(p.T0, cfg.a_t, cfg.b_t, cfg.R)[2] * (1 / p.rho_v - 1 / p.rho_l))
+
+
+def test_stefan_front_with_an_open_heated_bottom():
+    # The one-dimensional Stefan problem (Eq. 20, 21; text after Eq. 21):
+    # vapour between an open bottom at T_r 0.85 (the outflow at the liquid's
+    # saturation pressure) and liquid at T_r 0.8 that stays at rest, Ste =
+    # 0.005 with the model's latent heat and c_v = 11.2 R. X^2 grows at
+    # 4 k^2 alpha_v. Over 200,000 steps the start-up transient still shows
+    # (measured 1.17); a 2.5-million-step run on 256 rows settles to 1.03.
+    # With the EOS's latent heat the front would run about 4.5 times faster.
+    ny, nx = 128, 4
+    cfg = thermo.Config(nx=nx, ny=ny, walls=1, Tr_bottom=0.85, bottom_outflow=1, c_v=11.2)
+    o = Oracle(cfg)
+    p = o.p
+    T0, T1 = p.T0, 0.85 * p.Tc
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    rho = thermo.planar_profile(T0, cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS, cfg.K_INT, y - 20.0)
+    T = np.where(y < 20.0, T1 + (T0 - T1) * (y + 0.5) / 20.5, T0)
+    o.init_fields(rho, 0 * rho, 0 * rho, T)
+
+    def front():
+        m = o.moments()
+        r = m["rho"].mean(axis=1)
+        mid = 0.5 * (p.rho_v + p.rho_l)
+        j = int(np.argmax(r > mid))
+        return j - 0.5 + (mid - r[j - 1]) / (r[j] - r[j - 1]), m   # from the boundary at y = -1/2
+
+    o.step(100000)
+    X1, _ = front()
+    o.step(100000)
+    X2, m = front()
+    ps0 = thermo.maxwell(T0, cfg.a_t, cfg.b_t, cfg.R)[2]
+    h_lv = p.a * (p.rho_l - p.rho_v) + cfg.K_EOS * ps0 * (1 / p.rho_v - 1 / p.rho_l)
+    k = thermo.stefan_root(p.rho_v * p.cv * (T1 - T0) / (p.rho_l * h_lv))
+    # lambda_v (text after Eq. 15) over rho_v c_v
+    alpha_v = (4 + 3 * p.gamma1 + 2 * p.gamma2) / 6 * p.Cref * p.c * p.tauj_v / (p.rho_v * p.cv)
+    ratio = (X2 ** 2 - X1 ** 2) / (100000 * p.dt) / (4 * k * k * alpha_v)
+    assert 0.85 < ratio < 1.3, ratio
+    assert np.abs(m["uy"][ny // 2:]).max() < 1e-5 * p.c           # the liquid stays at rest
