@@ -245,6 +245,25 @@ def test_closed_box_heating_carries_the_models_latent_heat():
         + cfg.K_EOS * thermo.maxwell(p.T0, cfg.a_t, cfg.b_t, cfg.R)[2] * (1 / p.rho_v - 1 / p.rho_l))
 
 
+def test_open_heated_bottom_keeps_its_own_state_at_rest():
+    # a uniform vapour at the open bottom's own state (rho_out, T_bottom),
+    # at rest under an adiabatic top wall, is a fixed point: the ghost row
+    # then carries exactly the bottom row's populations
+    o = Oracle(thermo.Config(nx=4, ny=32, walls=1, Tr_bottom=0.85, bottom_outflow=1))
+    p = o.p
+    one = np.ones((32, 4))
+    o.init_fields(p.rho_out * one, 0 * one, 0 * one, p.T_bottom * one)
+    f0, g0 = o.f.copy(), o.g.copy()
+    o.step(500)
+    assert np.abs(o.f - f0).max() < 1e-14 * np.abs(f0).max()
+    assert np.abs(o.g - g0).max() < 1e-14 * np.abs(g0).max()
+    # the open bottom's density: the vapour branch of Eq. 17 at T_bottom
+    # and the liquid's saturation pressure
+    ps = thermo.maxwell(p.T0, p.a_t, p.b_t, p.R)[2]
+    assert thermo.p_eos(p.rho_out, p.T_bottom, p.a_t, p.b_t, p.R) == pytest.approx(ps, rel=1e-12)
+    assert p.rho_out < p.rho_v
+
+
 def test_stefan_front_with_an_open_heated_bottom():
     # The one-dimensional Stefan problem (Eq. 20, 21; text after Eq. 21):
     # vapour between an open bottom at T_r 0.85 (the outflow at the liquid's
