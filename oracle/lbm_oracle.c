@@ -136,13 +136,20 @@ static double rho_at(const orc_params* P, const double* rho, int x, int y)
 {
     x = wrap(x, P->nx);
     if (P->walls) {
-        if (y < 0 && P->bottom_outflow) return P->rho_out;
         if (y < 0) y = 0;
         if (y >= P->ny) y = P->ny - 1;
     } else {
         y = wrap(y, P->ny);
     }
     return rho[(size_t)y * P->nx + x];
+}
+
+/* The density the pair force sees at (x, y): beyond an open bottom it is
+ * the fixed density rho_out, elsewhere rho_at's. */
+static double rho_seen(const orc_params* P, const double* rho, int x, int y)
+{
+    if (y < 0 && P->walls && P->bottom_outflow) return P->rho_out;
+    return rho_at(P, rho, x, y);
 }
 
 /* Eq. 17 */
@@ -183,7 +190,7 @@ static void node_macro(const orc_params* P, const double* fl, const double* gl,
     /* Eq. 13 with e_i dt = (EX, EY) dx, dx = 1 */
     double sx = 0.0, sy = 0.0;
     for (int i = 1; i < 9; ++i) {
-        double rn = rho_at(P, rho_f, x + EX[i], y + EY[i]);
+        double rn = rho_seen(P, rho_f, x + EX[i], y + EY[i]);
         sx += pair_weight(i) * rn * EX[i];
         sy += pair_weight(i) * rn * EY[i];
     }
@@ -489,7 +496,7 @@ int orc_init(const orc_params* P, const double* rho_in, const double* ux_in,
             double rho = rho_in[p];
             double sx = 0.0, sy = 0.0;
             for (int i = 1; i < 9; ++i) {
-                double rn = rho_at(P, rho_in, x + EX[i], y + EY[i]);
+                double rn = rho_seen(P, rho_in, x + EX[i], y + EY[i]);
                 sx += pair_weight(i) * rn * EX[i];
                 sy += pair_weight(i) * rn * EY[i];
             }
