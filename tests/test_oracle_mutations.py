@@ -61,6 +61,9 @@ MUTATIONS = [
      "t->L[3][4] = sigq * wj;", "t->L[3][4] = 2.0 * sigq * wj;"),
     ("force term dt F_m halved in m_bar (Eq. 12b)",
      "mb[k] = m[k] + P->dt * t.Fm[k] - Sx[k] + SQ[k];", "mb[k] = m[k] + 0.5 * P->dt * t.Fm[k] - Sx[k] + SQ[k];"),
+    ("open heated bottom: the bottom row's temperature instead of T_bottom",
+     "eq_populations(P, P->rho_out, s.ux, s.uy, P->T_bottom, fo, go);",
+     "eq_populations(P, P->rho_out, s.ux, s.uy, s.T, fo, go);"),
     ("velocity without the half force (Eq. 14)",
      "s->ux = (jx + 0.5 * P->dt * s->Fx) / rho;", "s->ux = jx / rho;"),
 ]
@@ -83,6 +86,7 @@ PINS = [
     TP.test_density_wave_leaves_a_uniform_cross_flow_uniform,
     TP.test_poiseuille_flow_between_bounce_back_walls,
     TP.test_steady_conduction_between_fixed_temperature_walls,
+    TP.test_stefan_front_with_an_open_heated_bottom,
 ]
 
 
