@@ -273,10 +273,11 @@ def test_stefan_front_with_an_open_heated_bottom():
     # (measured 1.17); a 2.5-million-step run on 256 rows settles to 1.03.
     # With the EOS's latent heat the front would run about 4.5 times faster.
     ny, nx = 128, 4
-    cfg = thermo.Config(nx=nx, ny=ny, walls=1, Tr_bottom=0.85, bottom_outflow=1, c_v=11.2)
+    paper = GOLD["stefan_problem"]
+    cfg = thermo.Config(nx=nx, ny=ny, walls=1, Tr_bottom=paper["Tr1"], bottom_outflow=1, c_v=11.2)
     o = Oracle(cfg)
     p = o.p
-    T0, T1 = p.T0, 0.85 * p.Tc
+    T0, T1 = p.T0, paper["Tr1"] * p.Tc
     y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
     rho = thermo.planar_profile(T0, cfg.a_t, cfg.b_t, cfg.R, cfg.K_EOS, cfg.K_INT, y - 20.0)
     T = np.where(y < 20.0, T1 + (T0 - T1) * (y + 0.5) / 20.5, T0)
@@ -295,7 +296,9 @@ def test_stefan_front_with_an_open_heated_bottom():
     X2, m = front()
     ps0 = thermo.maxwell(T0, cfg.a_t, cfg.b_t, cfg.R)[2]
     h_lv = p.a * (p.rho_l - p.rho_v) + cfg.K_EOS * ps0 * (1 / p.rho_v - 1 / p.rho_l)
-    k = thermo.stefan_root(p.rho_v * p.cv * (T1 - T0) / (p.rho_l * h_lv))
+    Ste = p.rho_v * p.cv * (T1 - T0) / (p.rho_l * h_lv)
+    assert Ste == pytest.approx(paper["Ste"], rel=0.01)     # c_v = 11.2 R sets the paper's Ste
+    k = thermo.stefan_root(Ste)
     # lambda_v (text after Eq. 15) over rho_v c_v
     alpha_v = (4 + 3 * p.gamma1 + 2 * p.gamma2) / 6 * p.Cref * p.c * p.tauj_v / (p.rho_v * p.cv)
     ratio = (X2 ** 2 - X1 ** 2) / (100000 * p.dt) / (4 * k * k * alpha_v)
