@@ -7,9 +7,9 @@ and the CPU-baseline leg of ``bench.py``; never by the product package.
 ``lbm_oracle.c`` holds one time step, initialisation and moments (plain C,
 FP64), built here with gcc and called through ctypes.
 
-Parity status of each function is stated in its docstring. "Parity
-unpinned" beyond GPU-vs-oracle: which of gamma1, gamma2 goes to the e and eps
-rows of the g source q_m (SM Eq. S4b) and the sign of its heat-flux rows.
+Parity status of each function is stated in its docstring. The g source
+q_m (SM Eq. S4b) is pinned against the moments of the textbook second-order
+scalar source (rows 0, 1 and 3-8; row eps, gamma2 q, is a literal reading).
 The coefficient k s_eps omega_e of S
 (row e, column eps; SM Eq. S5a) is pinned only through the linear stability
 of the moving vapour, the walls (not in the paper) only through textbook

@@ -31,7 +31,7 @@
  *   T from rho e_k ............. rho e_k = rho c_v T + rho |u|^2 / 2 (text
  *                                after Eq. 11)
  *
- * Not in the paper (builder readings, listed in the design notes):
+ * Not in the paper (readings of this implementation):
  *   walls: half-way bounce-back of f and g at y = -1/2 and y = ny - 1/2;
  *   fixed-temperature wall segments: anti-bounce-back of g against the
  *   rest equilibrium M^-1 n^eq(rho_w c_v T_w, T_w, u = 0) with rho_w the

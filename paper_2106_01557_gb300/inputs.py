@@ -5,7 +5,7 @@ none of the model's arithmetic: coexistence densities, temperatures and
 every other physical number come in as arguments, computed by whichever
 side (oracle or library) is under test.
 
-Recipes (stated once here; the design notes repeat them):
+Recipes:
 * ``slab``: rho(x) = rho_v + (rho_l - rho_v)/2 [tanh(2(x - x1)/w) - tanh(2(x - x2)/w)]
   on a periodic box, evaluated with the periodic images of both edges.
 * ``droplets``: sum of tanh-edged discs rho_v + (rho_l - rho_v)/2 [1 - tanh(2(r - R)/w)],

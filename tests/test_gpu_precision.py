@@ -1,8 +1,8 @@
 """Reduced-precision storage (FP16 / BF16 shifted populations, FP32 collision)
 against the FP64 oracle, and the GPU path's physics on the flat-interface
 check. The shifted formats store l_i - l_i^rest; their error bounds per field
-are stated here and in the design notes (max |gpu - oracle| / max |oracle|,
-velocity against the lattice speed c)."""
+are stated in each test (max |gpu - oracle| / max |oracle|, velocity against
+the lattice speed c)."""
 import numpy as np
 import pytest
 

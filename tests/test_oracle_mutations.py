@@ -5,12 +5,8 @@ flags, points the oracle module at the copy, and requires that at least one
 of the fast pins fails. The planted copies live in pytest's temporary
 directory; the oracle itself is untouched.
 
-Not caught by these fast pins (and therefore not listed): swapping gamma1 and
-gamma2 in the e and eps rows of the g source q_m (SM Eq. S4b; a heated
-Poiseuille flow's temperature shape moves by 0.16%) and flipping the sign of
-its heat-flux rows q u: these act on non-conserved moments of g at an order
-the flows checked here do not resolve. Dropping Q_m is caught by the slower
-slab width and coexistence pin."""
+Dropping Q_m is caught by the slower slab width and coexistence pin, which
+is therefore not listed."""
 import os
 import subprocess
 
@@ -64,6 +60,10 @@ MUTATIONS = [
     ("open heated bottom: the bottom row's temperature instead of T_bottom",
      "eq_populations(P, P->rho_out, s.ux, s.uy, P->T_bottom, fo, go);",
      "eq_populations(P, P->rho_out, s.ux, s.uy, s.T, fo, go);"),
+    ("q_m: gamma1 and gamma2 swapped between rows e and eps (SM Eq. S4b)",
+     "{q, P->gamma1 * q, P->gamma2 * q,", "{q, P->gamma2 * q, P->gamma1 * q,"),
+    ("q_m: sign of the heat-flux rows flipped (SM Eq. S4b)",
+     "q * uxh, -q * uxh, q * uyh, -q * uyh, 0.0, 0.0};", "-q * uxh, q * uxh, -q * uyh, q * uyh, 0.0, 0.0};"),
     ("velocity without the half force (Eq. 14)",
      "s->ux = (jx + 0.5 * P->dt * s->Fx) / rho;", "s->ux = jx / rho;"),
 ]
@@ -72,6 +72,7 @@ PINS = [
     TS.test_init_recovers_prescribed_fields,
     TS.test_equilibrium_velocity_terms_are_the_discrete_maxwellians,
     TS.test_forcing_moments_are_those_of_the_second_order_forcing_term,
+    TS.test_energy_source_moments_are_those_of_the_second_order_scalar_source,
     TS.test_equilibrium_moments_give_the_recovered_eos,
     TS.test_pair_force_on_sinusoid_is_exact,
     TS.test_rest_state_is_a_fixed_point,
