@@ -569,11 +569,14 @@ def main():
                      "timing": "CUDA events over the timed steps on the launching stream / steps"},
         "gpu_launches": args.steps,
         "clocks": res["clocks"], "e2e": res["e2e"],
-        "variants": res["variants"],
+        "variants": sorted(res["variants"]),
         "conservation_last_step": res["stats"],
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    # the variants and studies first, one JSON line each; the headline last
+    for name, v in res["variants"].items():
+        print(json.dumps({"variant": name, "result": v}))
     print(json.dumps(line))
 
 

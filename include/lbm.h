@@ -178,8 +178,10 @@ int lbm_get_populations(lbm_handle* h, double* f, double* g);
 int lbm_set_populations(lbm_handle* h, const double* f, const double* g);
 
 /* Checkpoint: the raw stored state (both DFs, storage precision), the step
- * counter and the configuration, to a binary file; lbm_load requires a
- * handle created with the same nx, ny and precision. Resume is bitwise. */
+ * counter and a hash of the configuration (every lbm_config field but the
+ * stream and the device), to a binary file; lbm_load refuses, with
+ * LBM_ERR_ARG and the handle unchanged, a file whose lattice or
+ * configuration differs from the handle's. Resume is bitwise. */
 int lbm_save(lbm_handle* h, const char* path);
 int lbm_load(lbm_handle* h, const char* path);
 
@@ -189,6 +191,22 @@ int lbm_synchronize(lbm_handle* h);
 
 /* Steps taken since init (or restored by lbm_load). */
 int64_t lbm_step_count(const lbm_handle* h);
+
+/* Default bound on each wait of the step kernel for a tile's copies: 2 s. */
+#define LBM_TILE_WAIT_DEFAULT_NS 2000000000LL
+
+/* Bound, in nanoseconds, on each wait of the step kernel for the copies of
+ * a tile into shared memory (failure detection; not a parameter of the
+ * paper's method). A wait that runs out ends the launch early in every
+ * block that met it, sets the handle's status, and the next synchronising
+ * call returns LBM_ERR_TIMEOUT; the state is then undefined until the next
+ * lbm_set_fields, lbm_set_populations or lbm_load. 0 means no waiting: a
+ * tile whose copies have not landed when its turn comes times out, which a
+ * step from a fresh state always meets (its first copies were issued just
+ * before). The kernel never exits with a copy in flight: after a timeout it
+ * still waits, within the default bound, for the copies it has issued.
+ * ns < 0: LBM_ERR_ARG. Takes effect from the next lbm_step. */
+int lbm_set_tile_wait(lbm_handle* h, int64_t ns);
 
 /* Bytes of population traffic one time step moves at the algorithmic
  * minimum (one read and one write of 18 populations per node). */
@@ -300,13 +318,20 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
  * D / L in lattice units, with D the number of nodes whose phase (liquid:
  * rho above (rho_v + rho_l) / 2) the jump changed and L = (pi / 4) E the
  * interface length before the jump from its E liquid-vapour edges between
- * lattice neighbours. An unphysical
- * prediction (non-finite, rho <= 0 or T <= 0), a relative mass or energy
- * change above drift_tol, or a displacement above iface_tol restores the
- * snapshot and runs K + verify_steps LB steps instead. Every jump thus
- * advances the lattice by K + verify_steps steps. LBM_ERR_DIVERGED is
+ * lattice neighbours; and, node by node, what the verification steps did
+ * to the prediction: the largest change of a node's density and of its
+ * temperature between the predicted state and the verified one, each over
+ * that field's largest value in the prediction (a local defect that the
+ * global sums cannot see, such as a one-node temperature spike, is what
+ * the LB moves most). An unphysical prediction (non-finite, rho <= 0 or
+ * T <= 0), a relative mass or energy change above drift_tol, a
+ * displacement above iface_tol, or a local change above field_tol restores
+ * the snapshot and runs K + verify_steps LB steps instead. Every jump thus
+ * advances the lattice by K + verify_steps steps, and the handle's step
+ * count (lbm_step_count, and the device copy that keys stochastic
+ * rounding) by the same. LBM_ERR_DIVERGED is
  * returned only if those fallback LB steps diverge.
- * stats (may be NULL, >= 15): [0] jumps accepted, [1] fallbacks,
+ * stats (may be NULL, >= 17): [0] jumps accepted, [1] fallbacks,
  * [2] ms in surrogate jumps (prediction, checks, re-initialisation and
  * verification: [12] + [13] + [14]), [3] ms in fallback LB steps, [4]
  * largest accepted mass drift, [5] largest accepted energy drift, [6..7]
@@ -316,9 +341,10 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
  * before each jump (fields, conservation record, checks, snapshot), [12] ms
  * in the network, [13] ms in the checks of the prediction, the
  * re-initialisation of the populations and the conservation record, [14]
- * ms in the verification steps. Synchronous. */
+ * ms in the verification steps, [15] and [16] the largest local change of
+ * density and of temperature over all verified jumps. Synchronous. */
 int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32_t verify_steps, double drift_tol,
-                          double iface_tol, double* stats);
+                          double iface_tol, double field_tol, double* stats);
 int lbm_surrogate_destroy(lbm_surrogate* s);
 
 /* Largest lattice (nx * ny) lbm_conservation_noalloc accepts. */

@@ -478,6 +478,35 @@ __global__ void k_field_check(const double* __restrict__ f, const double* __rest
     }
 }
 
+// Largest per-node change between two field sets [4][P] (a, b) for the
+// density (plane 0) and the temperature (plane 3), and the largest |b| of
+// each: out[0] max |a_rho - b_rho|, out[1] max |b_rho|, out[2], out[3] the
+// same for T, as the bit patterns of non-negative doubles (their order is the
+// order of the values, so an integer maximum is exact and independent of the
+// order of the nodes; a NaN difference compares above every number).
+__global__ void k_field_change(const double* __restrict__ a, const double* __restrict__ b, long long P,
+                               unsigned long long* __restrict__ out) {
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const long long q = (k == 0 ? 0 : 3) * P + p;
+            const double d = fabs(a[q] - b[q]), v = fabs(b[q]);
+            m[2 * k] = (d > m[2 * k] || d != d) ? d : m[2 * k];
+            m[2 * k + 1] = (v > m[2 * k + 1] || v != v) ? v : m[2 * k + 1];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        unsigned long long u = (unsigned long long)__double_as_longlong(m[k]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_down_sync(0xffffffffu, u, o);
+            u = w > u ? w : u;
+        }
+        if (threadIdx.x % 32 == 0) atomicMax(&out[k], u);
+    }
+}
+
 template <int CIN, int COUT>
 cudaError_t conv_t(const ConvArgs& a, cudaStream_t s, int sms) {
     using SMc = ConvSmem<CIN, COUT>;
@@ -522,6 +551,16 @@ cudaError_t launch_field_check(const double* f, const double* prev, long long P,
     long long g = (P + 255) / 256;
     if (g > 2048) g = 2048;
     k_field_check<<<(unsigned)g, 256, 0, s>>>(f, prev, P, W, mid, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_change(const double* a, const double* b, long long P, unsigned long long* out,
+                                cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    long long g = (P + 255) / 256;
+    if (g > 2048) g = 2048;
+    k_field_change<<<(unsigned)g, 256, 0, s>>>(a, b, P, out);
     return cudaGetLastError();
 }
 

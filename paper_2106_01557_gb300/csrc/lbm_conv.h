@@ -60,5 +60,9 @@ cudaError_t launch_unpack(const float* y, long long P, const NormConsts& nc, dou
 // that in prev (a field set of the same shape, or null)
 cudaError_t launch_field_check(const double* f, const double* prev, long long P, int W, double mid,
                                unsigned long long* cnt, cudaStream_t s);
+// out[0..3] (bit patterns of doubles): max |a - b| and max |b| over the
+// density plane, then the same over the temperature plane of [4][P] field sets
+cudaError_t launch_field_change(const double* a, const double* b, long long P, unsigned long long* out,
+                                cudaStream_t s);
 
 }  // namespace lbm

@@ -124,10 +124,25 @@ __device__ __forceinline__ void moments9(const C l[9], C m[9]) {
     m[8] = l[5] - l[6] + l[7] - l[8];
 }
 
+// m0 / 9, the weight of moment 0 in every population. Each column of M^-1
+// but the first sums to zero over the nine populations, so the populations
+// sum to 9 (m0 / 9) whatever the other moments: a relative error e of this
+// one product is a gain of 9 e per step in mass (f) and energy (g). In FP32,
+// m0 * fl(1/9) has e = 9 fl(1/9) - 1 = +7.45e-9 at every node, a drift the
+// bulk phases cannot average out; the constant split into a rounded part
+// and its remainder (hi + lo = 1/9 to 48 bits) gives a correctly rounded
+// quotient in all but rare ties. FP64's e = -5.6e-17 needs no split.
+__device__ __forceinline__ double ninth(double m) { return m * (1.0 / 9.0); }
+__device__ __forceinline__ float ninth(float m) {
+    constexpr float hi = (float)(1.0 / 9.0);
+    constexpr float lo = (float)(1.0 / 9.0 - (double)(float)(1.0 / 9.0));
+    return __fmaf_rn(m, hi, m * lo);
+}
+
 // l = M^-1 m = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m
 template <class C>
 __device__ __forceinline__ void populations9(const C m[9], C l[9]) {
-    const C a0 = m[0] * C(1.0 / 9.0), a1 = m[1] * C(1.0 / 36.0), a2 = m[2] * C(1.0 / 36.0);
+    const C a0 = ninth(m[0]), a1 = m[1] * C(1.0 / 36.0), a2 = m[2] * C(1.0 / 36.0);
     const C a3 = m[3] * C(1.0 / 6.0), a4 = m[4] * C(1.0 / 12.0);
     const C a5 = m[5] * C(1.0 / 6.0), a6 = m[6] * C(1.0 / 12.0);
     const C a7 = m[7] * C(0.25), a8 = m[8] * C(0.25);

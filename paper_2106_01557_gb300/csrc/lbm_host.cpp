@@ -220,6 +220,7 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     if (c.walls != 0 && c.walls != 1) return fail(LBM_ERR_ARG, "walls must be 0 or 1");
     if (c.rounding != 0 && c.rounding != 1) return fail(LBM_ERR_ARG, "rounding must be 0 or 1");
     L.rounding = c.rounding;
+    L.tile_wait_ns = TILE_WAIT_NS_DEFAULT;
     if (!(c.a_t > 0 && c.b_t > 0 && c.R > 0 && c.K_EOS > 0 && c.K_INT > 0))
         return fail(LBM_ERR_ARG, "a~, b~, R, K_EOS, K_INT must be positive");
     if (!(c.Tr0 > 0.3 && c.Tr0 < 1.0)) return fail(LBM_ERR_ARG, "Tr0 must lie in (0.3, 1)");
@@ -653,14 +654,49 @@ int lbm_step_stats(lbm_handle* h, double out[8]) {
 
 int64_t lbm_step_count(const lbm_handle* h) { return h ? h->steps : -1; }
 
+int lbm_set_tile_wait(lbm_handle* h, int64_t ns) {
+    if (!h) return fail(LBM_ERR_ARG, "null handle");
+    if (ns < 0) return fail(LBM_ERR_ARG, "negative wait bound");
+    if (h->L.tile_wait_ns == (unsigned long long)ns) return LBM_OK;
+    // the captured graph holds the launch parameters: capture anew
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->L.tile_wait_ns = (unsigned long long)ns;
+    return LBM_OK;
+}
+
 double lbm_bytes_per_step(const lbm_handle* h) {
     if (!h) return 0.0;
     return 2.0 * 18.0 * (double)h->esize * (double)h->cfg.nx * (double)h->cfg.ny;
 }
 
-// Checkpoint layout: magic, version, nx, ny, precision, walls, steps, then
-// the raw stored buffer (18 ghost-padded planes).
-static const uint64_t CK_MAGIC = 0x4c424d4c56434b31ull;  // "LBMLVCK1"
+// Checkpoint layout: magic, nx, ny, precision, walls, a hash of the whole
+// configuration, steps, then the raw stored buffer (18 ghost-padded planes).
+static const uint64_t CK_MAGIC = 0x4c424d4c56434b32ull;  // "LBMLVCK2"
+
+// FNV-1a (Fowler, Noll, Vo) over every field of the configuration that
+// defines the case -- all but the stream and the device -- field by field
+// (so that struct padding never enters).
+static uint64_t config_hash(const lbm_config& c) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    };
+    const int32_t ints[] = {c.nx, c.ny, c.precision, c.walls, c.hot_x0, c.hot_len, c.rounding};
+    const double dbl[] = {c.a_t, c.b_t, c.R, c.K_EOS, c.K_INT, c.Tr0, c.varpi, c.gamma1, c.gamma2,
+                          c.s_p, c.s_eps, c.sig_e, c.sig_eps, c.sig_p, c.tau_j_v, c.tau_j_l, c.c_v,
+                          c.C_ref, c.accel_x, c.accel_y, c.Tr_bottom, c.Tr_top, c.Tr_hot, c.rho_ref};
+    mix(ints, sizeof ints);
+    mix(dbl, sizeof dbl);
+    return h;
+}
 
 int lbm_save(lbm_handle* h, const char* path) {
     if (!h || !path) return fail(LBM_ERR_ARG, "null argument");
@@ -672,8 +708,10 @@ int lbm_save(lbm_handle* h, const char* path) {
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
     int32_t hdr[4] = {h->cfg.nx, h->cfg.ny, h->cfg.precision, h->cfg.walls};
+    const uint64_t ch = config_hash(h->cfg);
     bool ok = std::fwrite(&CK_MAGIC, 8, 1, fp) == 1 && std::fwrite(hdr, sizeof hdr, 1, fp) == 1 &&
-              std::fwrite(&h->steps, 8, 1, fp) == 1 && std::fwrite(host.data(), 1, bytes, fp) == bytes;
+              std::fwrite(&ch, 8, 1, fp) == 1 && std::fwrite(&h->steps, 8, 1, fp) == 1 &&
+              std::fwrite(host.data(), 1, bytes, fp) == bytes;
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? LBM_OK : fail(LBM_ERR_IO, std::string("write failed: ") + path);
 }
@@ -682,17 +720,22 @@ int lbm_load(lbm_handle* h, const char* path) {
     if (!h || !path) return fail(LBM_ERR_ARG, "null argument");
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
-    uint64_t magic = 0;
+    uint64_t magic = 0, ch = 0;
     int32_t hdr[4];
     int64_t steps = 0;
     const size_t bytes = (size_t)18 * h->L.geo.plane * h->esize;
     std::vector<unsigned char> host(bytes);
     bool ok = std::fread(&magic, 8, 1, fp) == 1 && std::fread(hdr, sizeof hdr, 1, fp) == 1 &&
-              std::fread(&steps, 8, 1, fp) == 1;
+              std::fread(&ch, 8, 1, fp) == 1 && std::fread(&steps, 8, 1, fp) == 1;
     if (ok && (magic != CK_MAGIC || hdr[0] != h->cfg.nx || hdr[1] != h->cfg.ny || hdr[2] != h->cfg.precision ||
                hdr[3] != h->cfg.walls)) {
         std::fclose(fp);
         return fail(LBM_ERR_ARG, "checkpoint does not match this handle's lattice");
+    }
+    if (ok && ch != config_hash(h->cfg)) {
+        std::fclose(fp);
+        return fail(LBM_ERR_ARG, "checkpoint was written under another configuration (EOS, rates, forces, "
+                                 "walls or rounding differ)");
     }
     ok = ok && std::fread(host.data(), 1, bytes, fp) == bytes;
     std::fclose(fp);
@@ -1165,6 +1208,14 @@ int lbm_internal_restore(lbm_handle* h, const void* src) {
 }
 
 cudaStream_t lbm_internal_stream(const lbm_handle* h) { return h->stream; }
+
+int lbm_internal_set_steps(lbm_handle* h, int64_t steps) {
+    CK(cudaStreamSynchronize(h->stream));
+    const double st = (double)steps;
+    CK(cudaMemcpy(h->stats + 7, &st, sizeof st, cudaMemcpyHostToDevice));
+    h->steps = steps;
+    return LBM_OK;
+}
 
 void lbm_internal_rho_bounds(const lbm_handle* h, double* rho_v, double* rho_l, int* nx, int* ny) {
     *rho_v = h->prm.rho_v;

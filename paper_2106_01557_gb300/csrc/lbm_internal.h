@@ -58,7 +58,13 @@ struct Launch {
     KC<float> kf;
     KC<double> kd;
     int rounding;  // 16-bit storage: 0 nearest, 1 stochastic
+    // bound in ns on each wait of the step kernel for a tile's copies; 0: the
+    // copies must already have landed when the tile's turn comes (no waiting)
+    unsigned long long tile_wait_ns;
 };
+
+// default tile-wait bound: 2 s
+constexpr unsigned long long TILE_WAIT_NS_DEFAULT = 2000000000ull;
 
 // Storage kinds
 enum { S_F64 = 0, S_F32 = 1, S_F16 = 2, S_BF16 = 3 };
@@ -106,4 +112,7 @@ int lbm_internal_set_fields_fast(lbm_handle* h, const double* fields);
 // current state in one FP32 pass (sums in FP64), synchronous
 int lbm_internal_read_fast(lbm_handle* h, double* fields, double out[6]);
 cudaStream_t lbm_internal_stream(const lbm_handle* h);
+// the handle's step count, host and device copies (the device copy keys the
+// stochastic rounding of 16-bit storage); synchronous
+int lbm_internal_set_steps(lbm_handle* h, int64_t steps);
 void lbm_internal_rho_bounds(const lbm_handle* h, double* rho_v, double* rho_l, int* nx, int* ny);

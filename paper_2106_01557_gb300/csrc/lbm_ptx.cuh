@@ -8,7 +8,8 @@
 
 namespace lbm {
 
-// Bound on any wait for an mbarrier phase: 2 s of wall time.
+// Bound on any wait for an mbarrier phase: 2 s of wall time (the step
+// kernel's tile waits take theirs from the launch, with this as default).
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
 static __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -43,6 +44,19 @@ static __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t par
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// non-blocking test of an mbarrier phase
+static __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)

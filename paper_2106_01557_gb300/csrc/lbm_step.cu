@@ -225,9 +225,13 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
         bool timed_out = false;
         {
             const uint32_t parity = (uint32_t)(it / NS) & 1u;
-            const uint64_t t0 = globaltimer_ns();
-            while (!mbar_try_wait(&bar[stage], parity)) {
-                if (globaltimer_ns() - t0 > WAIT_NS) { timed_out = true; break; }
+            if (L.tile_wait_ns == 0) {
+                timed_out = !mbar_test_wait(&bar[stage], parity);  // no waiting at all
+            } else {
+                const uint64_t t0 = globaltimer_ns();
+                while (!mbar_try_wait(&bar[stage], parity)) {
+                    if (globaltimer_ns() - t0 > L.tile_wait_ns) { timed_out = true; break; }
+                }
             }
         }
         const S* sf = reinterpret_cast<const S*>(smem + stage * SM::STAGE);
@@ -304,7 +308,8 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     if (!ok && tid == 0) {
         atomicOr(status, ST_TIMEOUT);
         // give the copies in flight (this iteration's and those of the next
-        // NS - 1 tiles) a bounded chance to land before exiting
+        // NS - 1 tiles) a bounded chance to land before exiting; this drain
+        // keeps the full default bound whatever the tile-wait limit
         const int jend = it == 0 ? NS : it + NS - 1;  // tiles issued so far: 0 .. jend - 1
         for (int j = it; j < jend; ++j) {
             if ((int)blockIdx.x + j * (int)gridDim.x >= ntiles) break;

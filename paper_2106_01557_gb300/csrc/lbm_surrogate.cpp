@@ -71,6 +71,8 @@ struct lbm_surrogate {
     int* d_status = nullptr;         // bit 0: a tensor-core wait ran out of time
     double* fields = nullptr;        // 4 planes of the rollout case (device)
     double* pred = nullptr;
+    double* ver = nullptr;           // the verified state's fields
+    unsigned long long* d_chg = nullptr;  // field change of a verification (4 maxima)
     void* snapshot = nullptr;
     size_t snapshot_bytes = 0;
     long long step_count = 0;        // Adam steps
@@ -458,8 +460,8 @@ int lbm_surrogate_train_step(lbm_surrogate* s, const double* in, const double* t
 }
 
 int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32_t verify_steps, double drift_tol,
-                          double iface_tol, double* stats) {
-    if (!s || !h || njumps < 0 || verify_steps < 0 || !(drift_tol > 0) || !(iface_tol > 0))
+                          double iface_tol, double field_tol, double* stats) {
+    if (!s || !h || njumps < 0 || verify_steps < 0 || !(drift_tol > 0) || !(iface_tol > 0) || !(field_tol > 0))
         return sfail(LBM_ERR_ARG, "bad argument");
     double rho_v, rho_l;
     int nx, ny;
@@ -471,9 +473,11 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
     if (rc) return rc;
     const size_t sb = lbm_internal_state_bytes(h);
     if (!s->fields || s->snapshot_bytes < sb) {
-        s_free(s->fields); s_free(s->pred); s_free(s->snapshot);
-        s->fields = s->pred = nullptr; s->snapshot = nullptr;
+        s_free(s->fields); s_free(s->pred); s_free(s->ver); s_free(s->snapshot); s_free(s->d_chg);
+        s->fields = s->pred = s->ver = nullptr; s->snapshot = nullptr; s->d_chg = nullptr;
         if (cudaMalloc(&s->fields, 4 * P * 8) != cudaSuccess || cudaMalloc(&s->pred, 4 * P * 8) != cudaSuccess ||
+            cudaMalloc(&s->ver, 4 * P * 8) != cudaSuccess ||
+            cudaMalloc(&s->d_chg, 4 * sizeof(unsigned long long)) != cudaSuccess ||
             cudaMalloc(&s->snapshot, sb) != cudaSuccess) {
             cudaGetLastError();
             return sfail(LBM_ERR_OOM, "rollout buffers");
@@ -481,7 +485,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
         s->snapshot_bytes = sb;
     }
     double acc = 0, fb = 0, t_sur = 0, t_lb = 0, max_dm = 0, max_de = 0;
-    double all_dm = 0, all_de = 0, all_da = 0, n_bad = 0, n_div = 0;
+    double all_dm = 0, all_de = 0, all_da = 0, n_bad = 0, n_div = 0, all_dr = 0, all_dT = 0;
     const double mid = 0.5 * (rho_v + rho_l);
     // device counts: cnt[0] liquid nodes, cnt[1] unphysical nodes, cnt[2]
     // liquid-vapour edges, cnt[3] nodes whose phase changed from prev
@@ -512,6 +516,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
         if (rc) return rc;
         rc = lbm_internal_snapshot(h, s->snapshot);
         if (rc) return rc;
+        const int64_t steps0 = lbm_step_count(h);
         SCK(cudaStreamSynchronize(hs));
         auto t0 = clk::now();
         t_prep += ms(tp, t0);
@@ -523,7 +528,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
         rc = check(s->pred, s->fields, n1);
         if (rc) return rc;
         const bool physical = n1[1] == 0;
-        double dm = 0, de = 0, da = 0;
+        double dm = 0, de = 0, da = 0, dr = 0, dT = 0;
         bool diverged = false;
         auto tv = clk::now();
         if (physical) {
@@ -544,23 +549,36 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
         t_ver += ms(tv, t1);
         t_check += ms(tn, tv);
         if (physical && !diverged) {
-            // the prediction has been consumed: its buffer takes the checked state's fields
-            rc = lbm_internal_read_fast(h, s->pred, c1);
+            rc = lbm_internal_read_fast(h, s->ver, c1);
             if (rc == LBM_ERR_DIVERGED) diverged = true;
             else if (rc) return rc;
-            const auto t2 = clk::now();
-            t_check += ms(t1, t2);
-            t1 = t2;
             if (!diverged) {
                 dm = std::fabs(c1[0] / c0[0] - 1.0);
                 de = std::fabs(c1[4] / c0[4] - 1.0);
+                // the LB's local verdict on the prediction: the largest change
+                // of a node's density and temperature over the verification
+                // steps, relative to the field's largest value
+                unsigned long long chg[4];
+                SCK(launch_field_change(s->ver, s->pred, P, s->d_chg, s->stream));
+                SCK(cudaMemcpyAsync(chg, s->d_chg, sizeof chg, cudaMemcpyDeviceToHost, s->stream));
+                SCK(cudaStreamSynchronize(s->stream));
+                double v[4];
+                std::memcpy(v, chg, sizeof v);
+                dr = v[0] / std::max(v[1], 1e-300);
+                dT = v[2] / std::max(v[3], 1e-300);
             }
+            const auto t2 = clk::now();
+            t_check += ms(t1, t2);
+            t1 = t2;
             // mean interface displacement: the area that changed phase over the interface length
             const double len = 0.25 * 3.14159265358979323846 * (double)std::max(n0[2], 1ULL);
             da = (double)n1[3] / len;
         }
         n_div += diverged ? 1.0 : 0.0;
-        const bool bad = !physical || diverged || !(dm <= drift_tol) || !(de <= drift_tol) || !(da <= iface_tol);
+        const bool bad = !physical || diverged || !(dm <= drift_tol) || !(de <= drift_tol) || !(da <= iface_tol) ||
+                         !(dr <= field_tol) || !(dT <= field_tol);
+        all_dr = std::isfinite(dr) ? std::max(all_dr, dr) : INFINITY;
+        all_dT = std::isfinite(dT) ? std::max(all_dT, dT) : INFINITY;
         all_dm = std::max(all_dm, dm);
         all_de = std::max(all_de, de);
         all_da = std::max(all_da, da);
@@ -570,6 +588,9 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
                 rc = lbm_internal_restore(h, s->snapshot);
                 if (rc) return rc;
             }
+            // the snapshot's step count goes with its populations
+            rc = lbm_internal_set_steps(h, steps0);
+            if (rc) return rc;
             auto t2 = std::chrono::steady_clock::now();
             rc = lbm_step(h, s->cfg.K + verify_steps);
             if (rc) return rc;
@@ -579,11 +600,14 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
             fb += 1;
             have_state = false;
         } else {
+            // the jump and its verification advanced the lattice by K + verify_steps
+            rc = lbm_internal_set_steps(h, steps0 + s->cfg.K + verify_steps);
+            if (rc) return rc;
             acc += 1;
             max_dm = std::max(max_dm, dm);
             max_de = std::max(max_de, de);
             std::memcpy(c0, c1, sizeof c0);
-            std::swap(s->fields, s->pred);
+            std::swap(s->fields, s->ver);
             have_state = true;
         }
     }
@@ -592,6 +616,7 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
         stats[0] = acc; stats[1] = fb; stats[2] = t_sur; stats[3] = t_lb; stats[4] = max_dm; stats[5] = max_de;
         stats[6] = all_dm; stats[7] = all_de; stats[8] = all_da; stats[9] = n_bad;
         stats[10] = n_div; stats[11] = t_prep; stats[12] = t_net; stats[13] = t_check; stats[14] = t_ver;
+        stats[15] = all_dr; stats[16] = all_dT;
     }
     return LBM_OK;
 }
@@ -604,7 +629,7 @@ int lbm_surrogate_destroy(lbm_surrogate* s) {
         s_free(L.vb); s_free(L.w16); s_free(L.wflip);
     }
     release_acts(s);
-    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->d_status); s_free(s->d_msum); s_free(s->fields); s_free(s->pred); s_free(s->snapshot);
+    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->d_status); s_free(s->d_msum); s_free(s->fields); s_free(s->pred); s_free(s->ver); s_free(s->d_chg); s_free(s->snapshot);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return LBM_OK;

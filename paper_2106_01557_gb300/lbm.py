@@ -102,8 +102,9 @@ SIGNATURES = {
                                  _DP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "lbm_surrogate_train_step": ([_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_double, _DP], ctypes.c_int),
-    "lbm_surrogate_rollout": ([_H, _H, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _DP],
-                              ctypes.c_int),
+    "lbm_surrogate_rollout": ([_H, _H, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, _DP], ctypes.c_int),
+    "lbm_set_tile_wait": ([_H, ctypes.c_int64], ctypes.c_int),
     "lbm_surrogate_destroy": ([_H], ctypes.c_int),
     "lbm_conservation_noalloc": ([ctypes.POINTER(LbmConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p], ctypes.c_int),
@@ -279,6 +280,12 @@ class Lattice:
     def steps(self) -> int:
         return int(self.lib.lbm_step_count(self.h))
 
+    def set_tile_wait(self, ns: int):
+        """Bound (ns) on each wait of the step kernel for a tile's copies;
+        0: no waiting. A wait that runs out is reported by the next
+        synchronising call as LBM_ERR_TIMEOUT."""
+        _check(self.lib.lbm_set_tile_wait(self.h, int(ns)))
+
     def bytes_per_step(self) -> float:
         return float(self.lib.lbm_bytes_per_step(self.h))
 
@@ -405,6 +412,7 @@ class Surrogate:
         _check(self.lib.lbm_surrogate_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h
         self.K = K
+        self.channels, self.blocks = channels, blocks
 
     def close(self):
         if self.h:
@@ -462,27 +470,30 @@ class Surrogate:
                                                  ctypes.byref(loss)))
         return loss.value
 
-    def rollout(self, lattice, njumps, drift_tol=1e-3, iface_tol=0.5, verify_steps=None):
+    def rollout(self, lattice, njumps, drift_tol=1e-3, iface_tol=0.5, verify_steps=None, field_tol=0.02):
         """drift_tol: largest relative change of mass and of total energy per
         jump; iface_tol: largest mean interface displacement per jump, in
         lattice units; verify_steps: LB steps run from each surrogate state
-        before it is checked (default K / 10). Every jump advances the lattice
-        by K + verify_steps steps."""
+        before it is checked (default K / 10); field_tol: largest change of a
+        node's density or temperature over those steps, relative to the
+        field's largest value. Every jump advances the lattice by
+        K + verify_steps steps."""
         import torch
         torch.cuda.current_stream().synchronize()
         if verify_steps is None:
             verify_steps = max(1, self.K // 10)
         self.verify_steps = int(verify_steps)
-        stats = np.zeros(15)
+        stats = np.zeros(17)
         _check(self.lib.lbm_surrogate_rollout(self.h, lattice.h, int(njumps), int(verify_steps), float(drift_tol),
-                                              float(iface_tol), _host_ptr(stats)))
+                                              float(iface_tol), float(field_tol), _host_ptr(stats)))
         return {"accepted": int(stats[0]), "fallbacks": int(stats[1]), "ms_surrogate": stats[2],
                 "ms_fallback_lb": stats[3], "max_mass_drift": stats[4], "max_energy_drift": stats[5],
                 "max_mass_drift_all": stats[6], "max_energy_drift_all": stats[7],
                 "max_iface_displacement_all": stats[8], "unphysical": int(stats[9]),
                 "verify_diverged": int(stats[10]), "verify_steps": int(verify_steps),
                 "ms_read_state": stats[11], "ms_network": stats[12], "ms_check_reinit": stats[13],
-                "ms_verify": stats[14]}
+                "ms_verify": stats[14], "max_local_change_rho_all": stats[15],
+                "max_local_change_T_all": stats[16], "field_tol": float(field_tol)}
 
 
 def surrogate_params_from_oracle_layout(p):

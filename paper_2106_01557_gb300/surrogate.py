@@ -158,17 +158,36 @@ def lb_own_drift(cfg, fields, p, njumps, K):
     return {"mass": dm, "energy": de, "iface_displacement": da}
 
 
-def rollout_study(sur, p, size=1024, njumps=10, K=50, tol=1e-3, iface_tol=0.5, seed=99, n_drop=24):
+def identity_local_change(sur, cfg, fields, K, kv, njumps=2):
+    """The local change the verification steps make to an LB state that was
+    only read out and re-initialised (a network that predicts no change):
+    the floor under the rollout's local check."""
+    ident = lbm.Surrogate(sur.norm_off, sur.norm_scale, K=K, blocks=sur.blocks, conserve_mass=sur.conserve_mass)
+    prm = sur.get_params().copy()
+    nproj = 9 * 4 * sur.channels + 4
+    prm[-nproj:] = 0.0                        # zero projection: y = x
+    ident.set_params(prm)
+    lat = lbm.Lattice(cfg)
+    lat.set_fields(*fields)
+    st = ident.rollout(lat, njumps, 1.0, 1e3, verify_steps=kv, field_tol=1e3)
+    lat.close()
+    ident.close()
+    return {"rho": st["max_local_change_rho_all"], "T": st["max_local_change_T_all"]}
+
+
+def rollout_study(sur, p, size=1024, njumps=10, K=50, tol=1e-3, iface_tol=0.5, seed=99, n_drop=24,
+                  field_tol=0.02):
     """Surrogate rollout with LB fallback against the plain LB over the same
     njumps * (K + K/10) steps (each jump: K steps predicted, K/10 LB
     verification steps) on a size x size evaporation case: wall time of
     both, fallbacks, the field error of the surrogate path against the LB,
-    and the LB's own per-jump drift beside the thresholds."""
+    and the LB's own per-jump drift and local change beside the thresholds."""
     import torch
     kv = max(1, K // 10)
     cfg = lbm.default_config(size, size, precision="f32")
     fields = droplet_case(size, size, p, seed, n_drop=n_drop)
     own = lb_own_drift(cfg, fields, p, njumps, K + kv)
+    own_local = identity_local_change(sur, cfg, fields, K, kv)
     ref = lbm.Lattice(cfg)
     ref.set_fields(*fields)
     ref.step(2)
@@ -185,7 +204,7 @@ def rollout_study(sur, p, size=1024, njumps=10, K=50, tol=1e-3, iface_tol=0.5, s
     lat.synchronize()
     t0 = time.perf_counter()
     try:
-        st = sur.rollout(lat, njumps, tol, iface_tol, verify_steps=kv)
+        st = sur.rollout(lat, njumps, tol, iface_tol, verify_steps=kv, field_tol=field_tol)
     except lbm.LbmError as e:  # the fallback LB steps diverged from an accepted surrogate state
         lat.close()
         return {"size": size, "jumps": njumps, "K": K, "verify_steps": kv, "error": str(e),
@@ -233,7 +252,10 @@ def rollout_study(sur, p, size=1024, njumps=10, K=50, tol=1e-3, iface_tol=0.5, s
             "max_mass_drift_accepted": st["max_mass_drift"], "max_energy_drift_accepted": st["max_energy_drift"],
             "max_drift_all_jumps": {"mass": st["max_mass_drift_all"], "energy": st["max_energy_drift_all"],
                                     "iface_displacement": st["max_iface_displacement_all"]},
-            "lb_own_max_drift_per_jump": own, "unphysical": st["unphysical"], "err_vs_lb": err}
+            "max_local_change_all_jumps": {"rho": st["max_local_change_rho_all"],
+                                           "T": st["max_local_change_T_all"], "field_tol": field_tol},
+            "lb_own_max_drift_per_jump": own, "lb_own_local_change_after_reinit": own_local,
+            "unphysical": st["unphysical"], "err_vs_lb": err}
 
 
 def init_params(channels=64, blocks=6, seed=0):

@@ -69,6 +69,24 @@ def test_walls_body_force_hot_spot_match_oracle(gpu_lib, prec):
     assert rel_err(gg, o.g) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_walled_case_stays_with_the_oracle_over_1000_steps(gpu_lib, prec):
+    # the walled case (walls, body force, hot wall segment across the
+    # periodic seam) on 100 x 37, errors at 1, 10, 100 and 1,000 steps; the
+    # 1,000-step error stays within the parity bound
+    kw = dict(walls=1, accel_y=-1e-4, Tr_bottom=0.8, Tr_hot=0.95, hot_x0=90, hot_len=20, Tr_top=0.0)
+    o, g = _pair(100, 37, prec, seed=5, **kw)
+    errs, done = [], 0
+    for n in (1, 10, 100, 1000):
+        o.step(n - done)
+        g.step(n - done)
+        done = n
+        f, gg = g.get_populations()
+        errs.append(max(rel_err(f, o.f), rel_err(gg, o.g)))
+    print(prec, "error after 1, 10, 100, 1000 steps:", ["%.2e" % e for e in errs])
+    assert errs[-1] < TOL[prec], errs
+
+
 # every model coefficient and relaxation rate away from its default, so that
 # a kernel that kept one fixed, or took one from the wrong slot, fails
 RATES = dict(Tr0=0.85, varpi=0.2, gamma1=-1.5, gamma2=2.5, s_p=1.2, s_eps=1.3, sig_e=0.9, sig_eps=1.4,
@@ -170,8 +188,11 @@ def test_checkpoint_of_another_lattice_or_a_short_file_is_refused(gpu_lib, tmp_p
     a.save(str(path))
     short = tmp_path / "short.bin"
     short.write_bytes(path.read_bytes()[: path.stat().st_size // 2])
+    # the header also carries a hash of the configuration: the same lattice
+    # under another temperature or body force is refused too
     for other, code in ((gpu_case(72, 48, "f32"), -1), (gpu_case(72, 40, "f16s"), -1),
-                        (gpu_case(72, 40, "f32", walls=1), -1)):
+                        (gpu_case(72, 40, "f32", walls=1), -1), (gpu_case(72, 40, "f32", Tr0=0.85), -1),
+                        (gpu_case(72, 40, "f32", accel_x=1e-6), -1)):
         with pytest.raises(lbm.LbmError) as e:
             other.load(str(path))
         assert e.value.code == code
@@ -201,3 +222,36 @@ def test_divergence_is_reported(gpu_lib):
     with pytest.raises(lbm.LbmError) as e:
         g.synchronize()
     assert e.value.code == -4
+
+
+def test_tile_wait_that_runs_out_is_reported(gpu_lib):
+    # Failure detection of the step kernel's bounded waits, without a fault:
+    # with a zero bound a tile whose copies have not landed when its turn
+    # comes times out (the first tile of every block always does), the
+    # block ends its launch after its copies in flight have landed, and the
+    # next synchronising call reports LBM_ERR_TIMEOUT. The handle stays
+    # usable: with the default bound and the state set again it steps as a
+    # fresh handle does, bit for bit.
+    from paper_2106_01557_gb300 import lbm
+    o = oracle_case(256, 128)
+    fields = slab_fields(o, seed=21)
+    a = gpu_case(256, 128, "f32")
+    a.set_fields(*fields)
+    a.set_tile_wait(0)
+    a.step(3)
+    with pytest.raises(lbm.LbmError) as e:
+        a.synchronize()
+    assert e.value.code == -5
+    a.set_tile_wait(2_000_000_000)
+    a.set_fields(*fields)
+    a.step(25)                     # a captured graph of 20 steps and 5 single launches
+    a.synchronize()
+    b = gpu_case(256, 128, "f32")
+    b.set_fields(*fields)
+    b.step(25)
+    fa, ga = a.get_populations()
+    fb, gb = b.get_populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    with pytest.raises(lbm.LbmError) as e:
+        a.set_tile_wait(-1)
+    assert e.value.code == -1

@@ -207,9 +207,11 @@ def test_rollout_falls_back_and_accepts(gpu_lib):
     p["proj"] = (0 * p["proj"][0], 0 * p["proj"][1])
     s.set_params(lbm.surrogate_params_from_oracle_layout(p))
     st = s.rollout(lat, 3, drift_tol=1e-3, verify_steps=2)
-    # an accepted jump runs only its verification steps on the lattice
-    assert st["accepted"] == 3 and st["fallbacks"] == 0 and lat.steps == 36 + 3 * 2
+    # an accepted jump counts its K predicted steps and its verification steps
+    assert st["accepted"] == 3 and st["fallbacks"] == 0 and lat.steps == 36 + 3 * (10 + 2)
     assert st["max_mass_drift"] < 1e-6
+    # the device's copy of the count (it keys stochastic rounding) follows
+    assert lat.step_stats()[7] == lat.steps
 
 
 def test_trained_network_beats_no_change_on_held_out_runs(gpu_lib):
@@ -266,4 +268,48 @@ def test_rollout_rejects_a_moved_interface(gpu_lib):
     # the same jump passes a looser interface threshold
     lat.set_fields(rho, z, z, np.full_like(rho, pp.T0))
     st = s.rollout(lat, 1, drift_tol=1e-2, iface_tol=1.0)
+    assert st["accepted"] == 1
+
+
+def test_rollout_rejects_a_local_temperature_spike(gpu_lib):
+    # A network that sharpens the temperature field, y_T = x_T + A (8 x_T -
+    # sum of the 8 neighbours' x_T), turns a small warm node of a uniform
+    # vapour into a one-node spike with cold neighbours. Mass is untouched,
+    # the thermal energy of the spike and of its neighbours cancels and no
+    # node changes phase, so the global checks pass; the LB's verification
+    # steps spread the spike, and the local check rejects the jump. With the
+    # local check loosened the same jump is accepted.
+    from oracle import Oracle, thermo
+    from oracle import surrogate as S
+    from paper_2106_01557_gb300 import lbm
+    nx = ny = 32
+    pp = Oracle(thermo.Config(nx=nx, ny=ny)).p
+    rho = np.full((ny, nx), pp.rho_v)
+    z = np.zeros_like(rho)
+    T = np.full_like(rho, pp.T0)
+    T[16, 16] += 0.002 * pp.Tc
+    off = [pp.rho_v, 0.0, 0.0, pp.T0]
+    scale = [pp.rho_l - pp.rho_v, 0.01 * pp.c, 0.01 * pp.c, 0.05 * pp.Tc]
+    p = S.init_params(channels=64, blocks=2, seed=0)
+    zero = lambda a: np.zeros_like(a)
+    wl = zero(p["lift"][0])
+    wl[4, 0, 3], wl[4, 1, 3] = 1.0, -1.0        # h0 = x_T, h1 = -x_T (relu keeps each sign)
+    p["lift"] = (wl, zero(p["lift"][1]))
+    p["blocks"] = [((zero(w1), zero(b1)), (zero(w2), zero(b2))) for (w1, b1), (w2, b2) in p["blocks"]]
+    A = 10.0
+    wp = zero(p["proj"][0])
+    for tap in range(9):
+        a = 8 * A if tap == 4 else -A
+        wp[tap, 3, 0], wp[tap, 3, 1] = a, -a
+    p["proj"] = (wp, zero(p["proj"][1]))
+    s = lbm.Surrogate(off, scale, K=10, blocks=2)
+    s.set_params(lbm.surrogate_params_from_oracle_layout(p))
+    lat = lbm.Lattice.create(nx, ny, precision="f32")
+    lat.set_fields(rho, z, z, T)
+    st = s.rollout(lat, 1, drift_tol=1e-3, iface_tol=0.5, verify_steps=2, field_tol=0.02)
+    assert st["fallbacks"] == 1 and st["accepted"] == 0 and st["unphysical"] == 0
+    assert st["max_mass_drift_all"] < 1e-6 and st["max_energy_drift_all"] < 1e-3
+    assert st["max_local_change_T_all"] > 0.02
+    lat.set_fields(rho, z, z, T)
+    st = s.rollout(lat, 1, drift_tol=1e-3, iface_tol=0.5, verify_steps=2, field_tol=1.0)
     assert st["accepted"] == 1
