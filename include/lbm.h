@@ -107,6 +107,27 @@ typedef struct lbm_config {
                               runs stay deterministic; other values:
                               LBM_ERR_ARG. The batched sweep (lbm_batch_*)
                               rounds to nearest whatever the value. */
+    int32_t open_sides;    /* open, heated sides at constant pressure, for the
+                              Stefan problem and the evaporating droplet
+                              (paragraph after Eq. 19, where the outflow and
+                              constant-pressure condition drives the phase
+                              change; its scheme is in another paper, so
+                              this one is the library's): a ghost node beyond
+                              an open side carries the post-collision
+                              populations of its nearest fluid node with
+                              their equilibrium part moved to (rho_open,
+                              T_open) at that node's velocity (non-
+                              equilibrium extrapolation); populations that
+                              leave through it are lost, and the pair force
+                              sees rho_open beyond it. Bits: 1 bottom, 2 top
+                              (both need walls = 1; they replace that wall),
+                              4 left, 8 right (only as 15: all four sides).
+                              0: none. Other combinations: LBM_ERR_ARG */
+    double Tr_open;        /* reduced temperature of the open sides (> 0 when
+                              open_sides != 0) */
+    double rho_open;       /* density of the open sides; <= 0: the vapour
+                              branch of Eq. 17 at Tr_open and the saturation
+                              pressure at Tr0 */
 } lbm_config;
 
 /* Quantities derived in lbm_init (Eq. 16-19, SM Eq. S3-S5 constants). */
@@ -120,6 +141,7 @@ typedef struct lbm_params {
     double cv, Cref;
     double beta, kS, hS, bS; /* SM: beta, k, h, b */
     double se, sq;          /* from the relaxation constraint */
+    double rho_open, T_open; /* state of the open sides (0 without them) */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;

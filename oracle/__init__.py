@@ -13,8 +13,9 @@ scalar source (rows 0, 1 and 3-8; row eps, gamma2 q, is a literal reading).
 The coefficient k s_eps omega_e of S
 (row e, column eps; SM Eq. S5a) is pinned only through the linear stability
 of the moving vapour, the walls (not in the paper) only through textbook
-flows (Poiseuille, steady conduction), and the open heated bottom (not in the
-paper) only through the Stefan problem (Eq. 20, 21).
+flows (Poiseuille, steady conduction), and the open heated sides (not in the
+paper) through the Stefan problem (Eq. 20, 21) and the quasi-steady
+evaporation of a droplet.
 """
 from __future__ import annotations
 
@@ -71,7 +72,7 @@ class OrcParams(ctypes.Structure):
         ("ax", ctypes.c_double), ("ay", ctypes.c_double),
         ("T_bottom", ctypes.c_double), ("T_top", ctypes.c_double), ("T_hot", ctypes.c_double),
         ("hot_x0", ctypes.c_int), ("hot_len", ctypes.c_int),
-        ("bottom_outflow", ctypes.c_int), ("rho_out", ctypes.c_double),
+        ("open_sides", ctypes.c_int), ("rho_out", ctypes.c_double), ("T_open", ctypes.c_double),
     ]
 
 

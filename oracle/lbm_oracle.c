@@ -39,9 +39,12 @@
  *   a wall equals the density of the adjacent fluid node (neutral wetting);
  *   heat-conduction rate sigma_j interpolated linearly in rho between
  *   tau_j,v at rho_v and tau_j,l at rho_l (clamped), and sigma_q = sigma_j;
- *   an optional open, heated bottom for the one-dimensional Stefan problem
- *   (non-equilibrium extrapolation to the vapour at T_bottom and the
- *   liquid's saturation pressure).
+ *   open, heated sides for the one-dimensional Stefan problem (the bottom)
+ *   and the evaporating droplet (all four sides): a ghost node beyond an
+ *   open side carries the post-collision populations of its nearest fluid
+ *   node with their equilibrium part moved to the open state (rho_out,
+ *   T_open) at that node's velocity (non-equilibrium extrapolation);
+ *   rho_out is the vapour at T_open and the liquid's saturation pressure.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -58,8 +61,10 @@ typedef struct {
     double ax, ay;
     double T_bottom, T_top, T_hot;
     int hot_x0, hot_len;
-    int bottom_outflow;  /* with walls: the bottom is an open, heated outflow */
-    double rho_out;      /* its density (vapour at T_bottom and the liquid's p_s) */
+    int open_sides;      /* open, heated sides: 1 bottom, 2 top (both need
+                            walls), 4 left, 8 right (only with all four) */
+    double rho_out;      /* their density (vapour at T_open and the liquid's p_s) */
+    double T_open;       /* their temperature */
 } orc_params;
 
 /* SM Eq. S1: e_i / c for i = 0..8 */
@@ -144,11 +149,19 @@ static double rho_at(const orc_params* P, const double* rho, int x, int y)
     return rho[(size_t)y * P->nx + x];
 }
 
-/* The density the pair force sees at (x, y): beyond an open bottom it is
+/* Is the lattice point (x, y) beyond an open side? (x is periodic unless
+ * the left and right sides are open.) */
+static int beyond_open(const orc_params* P, int x, int y)
+{
+    return ((P->open_sides & 1) && y < 0) || ((P->open_sides & 2) && y >= P->ny) ||
+           ((P->open_sides & 4) && x < 0) || ((P->open_sides & 8) && x >= P->nx);
+}
+
+/* The density the pair force sees at (x, y): beyond an open side it is
  * the fixed density rho_out, elsewhere rho_at's. */
 static double rho_seen(const orc_params* P, const double* rho, int x, int y)
 {
-    if (y < 0 && P->walls && P->bottom_outflow) return P->rho_out;
+    if (beyond_open(P, x, y)) return P->rho_out;
     return rho_at(P, rho, x, y);
 }
 
@@ -401,30 +414,40 @@ int orc_step(const orc_params* P, double* f, double* g, int nsteps)
                 node_state s;
                 node_macro(P, fl, gl, rho, x, y, &s);
                 node_collide(P, fl, gl, &s, fb, gb);
-                const int open_bottom = P->walls && P->bottom_outflow && y == 0;
-                if (open_bottom) {
-                    /* Open, heated bottom (not in the paper, whose Stefan
-                     * problem takes its outflow scheme from another paper):
-                     * the ghost node below this one carries this node's
-                     * post-collision populations with their equilibrium
-                     * part moved to (rho_out, T_bottom) at this node's
-                     * velocity (non-equilibrium extrapolation), and streams
-                     * into the bottom row what enters from below. What
-                     * leaves through the bottom is lost. */
+                int on_open = 0;
+                for (int i = 1; i < 9; ++i) on_open |= beyond_open(P, x + EX[i], y + EY[i]);
+                if (on_open) {
+                    /* Open, heated sides (not in the paper, whose boundary
+                     * scheme is taken from another paper): every ghost node
+                     * beyond an open side whose nearest fluid node is this
+                     * one carries this node's post-collision populations
+                     * with their equilibrium part moved to (rho_out,
+                     * T_open) at this node's velocity (non-equilibrium
+                     * extrapolation), and streams into the lattice the
+                     * populations that point back across the open sides.
+                     * What leaves through an open side is lost. */
                     double fe[9], ge[9], fo[9], go[9];
                     eq_populations(P, s.rho, s.ux, s.uy, s.T, fe, ge);
-                    eq_populations(P, P->rho_out, s.ux, s.uy, P->T_bottom, fo, go);
-                    for (int i = 0; i < 9; ++i) {
-                        if (EY[i] != 1) continue;
-                        size_t pd = (size_t)wrap(x + EX[i], nx);
-                        fn[i * N + pd] = fb[i] + fo[i] - fe[i];
-                        gn[i * N + pd] = gb[i] + go[i] - ge[i];
-                    }
+                    eq_populations(P, P->rho_out, s.ux, s.uy, P->T_open, fo, go);
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int gx = x + dx, gy = y + dy;
+                            const int ox = beyond_open(P, gx, y), oy = beyond_open(P, x, gy);
+                            if (!(ox || oy) || (dx != 0 && !ox) || (dy != 0 && !oy)) continue;
+                            for (int i = 1; i < 9; ++i) {
+                                if ((dx != 0 && EX[i] != -dx) || (dy != 0 && EY[i] != -dy)) continue;
+                                const int xd = gx + EX[i], yd = gy + EY[i];
+                                if (beyond_open(P, xd, yd)) continue;
+                                size_t pd = (size_t)yd * nx + wrap(xd, nx);
+                                fn[i * N + pd] = fb[i] + fo[i] - fe[i];
+                                gn[i * N + pd] = gb[i] + go[i] - ge[i];
+                            }
+                        }
                 }
                 /* Eq. 12a, push form */
                 for (int i = 0; i < 9; ++i) {
                     int xd = x + EX[i], yd = y + EY[i];
-                    if (open_bottom && yd < 0) continue;
+                    if (beyond_open(P, xd, yd)) continue;
                     if (P->walls && (yd < 0 || yd >= ny)) {
                         int o = OPP[i];
                         fn[o * N + p] = fb[i];

@@ -275,7 +275,8 @@ class Config:
     Tr_hot: float = 0.0            # hot-spot reduced T on the bottom wall
     hot_x0: int = 0
     hot_len: int = 0
-    bottom_outflow: int = 0        # with walls: open bottom at Tr_bottom (Stefan problem)
+    open_sides: int = 0            # open, heated sides: 1 bottom, 2 top (with walls), 15 all four
+    Tr_open: float = 0.0           # reduced T of the open sides
 
 
 @dataclass
@@ -327,19 +328,24 @@ class Params:
     T_hot: float
     hot_x0: int
     hot_len: int
-    bottom_outflow: int
+    open_sides: int
     rho_out: float
+    T_open: float
 
 
 def _outflow_density(cfg: Config, T0, rv):
-    """Density of the open bottom: the vapour at T_bottom and at the
-    saturation pressure of the liquid at T0 (the vapour branch of Eq. 17)."""
-    if not cfg.bottom_outflow:
+    """Density of the open sides: the vapour at T_open and at the saturation
+    pressure of the liquid at T0 (the vapour branch of Eq. 17)."""
+    if not cfg.open_sides:
         return 0.0
+    if cfg.open_sides & 3 and not cfg.walls:
+        raise ValueError("an open bottom or top needs walls = 1")
+    if cfg.open_sides & 12 and cfg.open_sides != 15:
+        raise ValueError("open left and right sides come only with all four sides open")
     Tc, _ = critical_point(cfg.a_t, cfg.b_t, cfg.R)
-    Tb = cfg.Tr_bottom * Tc
+    Tb = cfg.Tr_open * Tc
     if not Tb > 0:
-        raise ValueError("an open bottom needs Tr_bottom > 0")
+        raise ValueError("open sides need Tr_open > 0")
     ps = maxwell(T0, cfg.a_t, cfg.b_t, cfg.R)[2]
     return brentq(lambda r: p_eos(r, Tb, cfg.a_t, cfg.b_t, cfg.R) - ps, 1e-6 * rv, rv * T0 / Tb * 1.5)
 
@@ -379,7 +385,7 @@ def derive_params(cfg: Config) -> Params:
         tauj_v=cfg.tau_j_v, tauj_l=cfg.tau_j_l, ax=cfg.accel_x, ay=cfg.accel_y,
         T_bottom=cfg.Tr_bottom * Tc, T_top=cfg.Tr_top * Tc, T_hot=cfg.Tr_hot * Tc,
         hot_x0=cfg.hot_x0, hot_len=cfg.hot_len,
-        bottom_outflow=cfg.bottom_outflow, rho_out=_outflow_density(cfg, T0, rv))
+        open_sides=cfg.open_sides, rho_out=_outflow_density(cfg, T0, rv), T_open=cfg.Tr_open * Tc)
 
 
 def params_dict(p: Params) -> dict:

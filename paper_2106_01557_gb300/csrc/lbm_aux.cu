@@ -54,16 +54,21 @@ __device__ __forceinline__ int ey_of(int i) {
 }
 
 // Write post-streaming population l_i(x, y) so that the next pull finds it:
-// at x - e_i (wrapped in x; wrapped in y when periodic, ghost row at a wall).
+// at x - e_i (wrapped in x unless the left and right sides are open; wrapped
+// in y when periodic; a ghost row or column at a wall or an open side).
 template <class S>
 __device__ __forceinline__ void scatter(S* buf, const Geometry& G, int p, int i, int x, int y, S v) {
     int xs = x - ex_of(i), ys = y - ey_of(i);
-    xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
+    if (!(G.open & 12)) xs = xs < 0 ? xs + G.nx : (xs >= G.nx ? xs - G.nx : xs);
     if (!G.walls) ys = ys < 0 ? ys + G.ny : (ys >= G.ny ? ys - G.ny : ys);
     put<S>(buf, G, p, xs, ys, v);
 }
 
-__device__ __forceinline__ double rho_nb(const double* rho, const Geometry& G, int x, int y) {
+// density at (x, y) as the pair force sees it: the open sides' fixed
+// density beyond them, the adjacent fluid node's beyond a wall, periodic
+// images elsewhere
+__device__ __forceinline__ double rho_nb(const double* rho, const Geometry& G, double rho_open, int x, int y) {
+    if (G.open && beyond_open(G, x, y)) return rho_open;
     x = x < 0 ? x + G.nx : (x >= G.nx ? x - G.nx : x);
     if (G.walls) y = y < 0 ? 0 : (y >= G.ny ? G.ny - 1 : y);
     else y = y < 0 ? y + G.ny : (y >= G.ny ? y - G.ny : y);
@@ -82,7 +87,7 @@ __global__ void k_init(const Launch L, const double* __restrict__ rho, const dou
         NodeMacro<C> s;
         C rn[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) rn[i] = (C)rho_nb(rho, G, x + ex_of(i), y + ey_of(i));
+        for (int i = 0; i < 9; ++i) rn[i] = (C)rho_nb(rho, G, (double)L.kd.rho_open, x + ex_of(i), y + ey_of(i));
         const C r = (C)rho[idx], vx = (C)ux[idx], vy = (C)uy[idx];
         s.rho = r;
         s.inv_rho = C(1) / r;
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(AUX_NT) k_moments(const Launch L, const S* __r
         for (int i = 0; i < 9; ++i) {
             f[i] = load_c<S, C>(buf, G, i, x - ex_of(i), y - ey_of(i), (C)L.kf.rest[i]);
             g[i] = load_c<S, C>(buf, G, 9 + i, x - ex_of(i), y - ey_of(i), (C)L.kf.rest[9 + i]);
-            rn[i] = (C)rho_nb(rho_f, G, x + ex_of(i), y + ey_of(i));
+            rn[i] = (C)rho_nb(rho_f, G, (double)L.kd.rho_open, x + ex_of(i), y + ey_of(i));
         }
         NodeMacro<C> s;
         node_macro(k, f, g, rn, s);

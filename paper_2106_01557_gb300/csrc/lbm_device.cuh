@@ -130,9 +130,14 @@ __device__ __forceinline__ void moments9(const C l[9], C m[9]) {
 // one product is a gain of 9 e per step in mass (f) and energy (g). In FP32,
 // m0 * fl(1/9) has e = 9 fl(1/9) - 1 = +7.45e-9 at every node, a drift the
 // bulk phases cannot average out; the constant split into a rounded part
-// and its remainder (hi + lo = 1/9 to 48 bits) gives a correctly rounded
-// quotient in all but rare ties. FP64's e = -5.6e-17 needs no split.
-__device__ __forceinline__ double ninth(double m) { return m * (1.0 / 9.0); }
+// and its remainder (hi + lo = 1/9 to 48 bits in FP32, to 110 bits in FP64)
+// gives a correctly rounded quotient in all but rare ties. In FP64 the same
+// split removes e = -5.6e-17 per step (3e-12 of the mass over 60,000 steps).
+__device__ __forceinline__ double ninth(double m) {
+    constexpr double hi = 1.0 / 9.0;
+    constexpr double lo = 6.1679056923619804e-18;  // 1/9 - hi, rounded
+    return __fma_rn(m, hi, m * lo);
+}
 __device__ __forceinline__ float ninth(float m) {
     constexpr float hi = (float)(1.0 / 9.0);
     constexpr float lo = (float)(1.0 / 9.0 - (double)(float)(1.0 / 9.0));
@@ -375,7 +380,8 @@ __device__ __forceinline__ void g_rest_wall(const KC<C>& k, C rho_w, C T_w, C& g
 }
 
 // Store one post-collision value at physical (x, y) of plane p, with the
-// copies the periodic ghost cells need. y may be -1 or ny for a wall ghost.
+// copies the periodic ghost cells need. y may be -1 or ny for a wall ghost,
+// and, with open left and right sides, x may be -1 or nx.
 template <class S>
 __device__ __forceinline__ void put(S* __restrict__ out, const Geometry& G, int p, int x, int y, S v) {
     S* base = out + (long long)p * G.plane;
@@ -392,9 +398,81 @@ __device__ __forceinline__ void put(S* __restrict__ out, const Geometry& G, int 
         if (r >= nr) break;
         S* row = base + (long long)(rows[r] + 2) * G.pitch + G.PX;
         row[x] = v;
-        if (x < HX) row[x + G.nx] = v;
-        if (x >= G.nx - HX) row[x - G.nx] = v;
+        if (!(G.open & 12)) {
+            if (x < HX) row[x + G.nx] = v;
+            if (x >= G.nx - HX) row[x - G.nx] = v;
+        }
     }
+}
+
+// Equilibrium populations M^-1 m^eq and M^-1 n^eq (SM Eq. S3a, S4a) of the
+// force-free state (rho, u^ = u / c, T), with rho e_k = rho c_v T +
+// rho |u|^2 / 2.
+template <class C>
+__device__ __forceinline__ void eq_pops(const KC<C>& k, C rho, C ux, C uy, C T, C fe[9], C ge[9]) {
+    const C u2 = ux * ux + uy * uy;
+    const C pbe = p_BE(k, rho, T);
+    const C eta = pbe * k.cs2_inv - rho;
+    const C E = rho * k.cv * T + C(0.5) * k.c2 * rho * u2;
+    const C rhk = E + pbe;
+    const C CT = k.Cref * T;
+    C m[9], n[9];
+    m[0] = rho;
+    m[1] = C(-2) * rho + C(2) * eta + C(3) * rho * u2;
+    m[2] = rho + k.beta * eta - C(3) * rho * u2;
+    m[3] = rho * ux;
+    m[4] = -rho * ux;
+    m[5] = rho * uy;
+    m[6] = -rho * uy;
+    m[7] = rho * (ux * ux - uy * uy);
+    m[8] = rho * ux * uy;
+    n[0] = E;
+    n[1] = C(-4) * E + (C(4) + k.g1) * CT;
+    n[2] = C(4) * E - (C(4) - k.g2) * CT;
+    n[3] = rhk * ux;
+    n[4] = -rhk * ux;
+    n[5] = rhk * uy;
+    n[6] = -rhk * uy;
+    n[7] = C(0);
+    n[8] = C(0);
+    populations9(m, fe);
+    populations9(n, ge);
+}
+
+// Ghost populations beyond the open sides next to node (x, y): every ghost
+// node whose nearest fluid node is (x, y) -- the one across each open side
+// the node touches, and the corner between two -- carries the node's
+// post-collision populations f, g (for shifted formats, their deviations
+// from the rest populations) with the equilibrium part moved from the
+// node's state (rho, u^, T) to the open state (rho_open, u^, T_open)
+// (non-equilibrium extrapolation), and streams into the lattice the
+// directions that point back across the open sides.
+// (f and g come as the nine values each so that the caller's arrays stay in
+// registers on the path that does not call this.)
+template <class C>
+struct Pops9 {
+    C v[9];
+};
+template <class S, class C>
+__device__ __noinline__ void open_store(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
+                                        const Pops9<C> f, const Pops9<C> g, C rho, C ux, C uy, C T) {
+    C fe[9], ge[9], fo[9], go[9];
+    eq_pops(k, rho, ux, uy, T, fe, ge);
+    eq_pops(k, k.rho_open, ux, uy, k.T_open, fo, go);
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int gx = x + dx, gy = y + dy;
+            const bool ox = beyond_open(G, gx, y), oy = beyond_open(G, x, gy);
+            if (!(ox || oy) || (dx != 0 && !ox) || (dy != 0 && !oy)) continue;
+            for (int i = 1; i < 9; ++i) {
+                if ((dx != 0 && ex[i] != -dx) || (dy != 0 && ey[i] != -dy)) continue;
+                if (beyond_open(G, gx + ex[i], gy + ey[i])) continue;
+                put<S>(out, G, i, gx, gy, Store<S, C>::cvt(f.v[i] + fo[i] - fe[i]));
+                put<S>(out, G, 9 + i, gx, gy, Store<S, C>::cvt(g.v[i] + go[i] - ge[i]));
+            }
+        }
 }
 
 }  // namespace lbm

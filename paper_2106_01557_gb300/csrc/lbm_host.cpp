@@ -231,6 +231,11 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     if (!(c.c_v > 0)) return fail(LBM_ERR_ARG, "c_v must be positive");
     if (c.hot_len < 0 || c.hot_len > c.nx) return fail(LBM_ERR_ARG, "hot_len out of range");
     if (!std::isfinite(c.accel_x) || !std::isfinite(c.accel_y)) return fail(LBM_ERR_ARG, "non-finite acceleration");
+    if (c.open_sides < 0 || c.open_sides > 15) return fail(LBM_ERR_ARG, "open_sides must lie in 0..15");
+    if ((c.open_sides & 3) && c.walls != 1) return fail(LBM_ERR_ARG, "an open bottom or top needs walls = 1");
+    if ((c.open_sides & 12) && c.open_sides != 15)
+        return fail(LBM_ERR_ARG, "open left and right sides come only with all four sides open");
+    if (c.open_sides && !(c.Tr_open > 0)) return fail(LBM_ERR_ARG, "open sides need Tr_open > 0");
 
     // Eq. 17: a~ = A R^2 Tc^2 / pc, b~ = B R Tc / pc
     const double A = 0.4963880577294099, B = 0.1872945669467330;
@@ -241,6 +246,25 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     double ps;
     if (!maxwell(e, &p.rho_v, &p.rho_l, &ps)) return fail(LBM_ERR_ARG, "no liquid-vapour coexistence at Tr0");
     p.p_s = c.K_EOS * ps;
+    // the open sides' density: the vapour branch of Eq. 17 at their own
+    // temperature and the saturation pressure at Tr0
+    double rho_open = c.rho_open;
+    if (c.open_sides && !(rho_open > 0)) {
+        Eos eo{c.a_t, c.b_t, c.R, c.Tr_open * p.Tc};
+        const double rmax = 4.0 / c.b_t;
+        // the vapour branch ends at the first maximum of p (or, above the
+        // critical temperature, p is monotonic): scan for where dp turns negative
+        double hi = rmax * 0.9999;
+        for (int k = 1; k < 4000; ++k) {
+            const double r = rmax * k / 4000.0;
+            if (eo.dp(r) < 0.0) { hi = r; break; }
+        }
+        hi = bisect([&](double r) { return eo.dp(r); }, 1e-12 * rmax, hi);
+        if (!(eo.p(hi) > ps)) return fail(LBM_ERR_ARG, "no vapour at Tr_open with the saturation pressure at Tr0");
+        rho_open = bisect([&](double r) { return eo.p(r) - ps; }, 1e-14 * rmax, hi);
+    }
+    p.rho_open = c.open_sides ? rho_open : 0.0;
+    p.T_open = c.open_sides ? c.Tr_open * p.Tc : 0.0;
     // Eq. 18, 19 (dx = 1): c_s^2 = K_INT^2 (dp_EOS/drho + 2 K_EOS a~ rho) at rho_l
     p.G2 = c.K_INT * c.K_INT * 2.0 * c.K_EOS * c.a_t;
     const double cs2 = c.K_INT * c.K_INT * (c.K_EOS * e.dp(p.rho_l) + 2.0 * c.K_EOS * c.a_t * p.rho_l);
@@ -281,6 +305,7 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     G.plane = (long long)G.pitch * G.nyp;
     G.hot_x0 = ((c.hot_x0 % c.nx) + c.nx) % c.nx;
     G.hot_len = c.hot_len;
+    G.open = c.open_sides;
 
     auto fill = [&](auto& k, auto cast) {
         k.c = cast(p.c);
@@ -331,6 +356,8 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
         k.T_bottom = cast(c.Tr_bottom > 0 ? c.Tr_bottom * p.Tc : 0.0);
         k.T_top = cast(c.Tr_top > 0 ? c.Tr_top * p.Tc : 0.0);
         k.T_hot = cast(c.Tr_hot > 0 ? c.Tr_hot * p.Tc : 0.0);
+        k.rho_open = cast(c.open_sides ? rho_open : 0.0);
+        k.T_open = cast(c.open_sides ? c.Tr_open * p.Tc : 0.0);
     };
     fill(L.kd, [](double v) { return v; });
     fill(L.kf, [](double v) { return (float)v; });
@@ -689,10 +716,11 @@ static uint64_t config_hash(const lbm_config& c) {
             h *= 1099511628211ull;
         }
     };
-    const int32_t ints[] = {c.nx, c.ny, c.precision, c.walls, c.hot_x0, c.hot_len, c.rounding};
+    const int32_t ints[] = {c.nx, c.ny, c.precision, c.walls, c.hot_x0, c.hot_len, c.rounding, c.open_sides};
     const double dbl[] = {c.a_t, c.b_t, c.R, c.K_EOS, c.K_INT, c.Tr0, c.varpi, c.gamma1, c.gamma2,
                           c.s_p, c.s_eps, c.sig_e, c.sig_eps, c.sig_p, c.tau_j_v, c.tau_j_l, c.c_v,
-                          c.C_ref, c.accel_x, c.accel_y, c.Tr_bottom, c.Tr_top, c.Tr_hot, c.rho_ref};
+                          c.C_ref, c.accel_x, c.accel_y, c.Tr_bottom, c.Tr_top, c.Tr_hot, c.rho_ref,
+                          c.Tr_open, c.rho_open};
     mix(ints, sizeof ints);
     mix(dbl, sizeof dbl);
     return h;

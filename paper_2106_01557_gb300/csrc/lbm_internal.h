@@ -38,6 +38,7 @@ struct KC {
     C c4g1_Cref, c4g2_Cref;          // (4 + gamma_1) C_ref, (4 - gamma_2) C_ref
     C c2_third;      // c^2 / 3
     C T_bottom, T_top, T_hot;
+    C rho_open, T_open;  // state of the open sides
     C rest[18];      // shifted-storage rest populations (f 0..8, g 9..17)
     C mrest[3], nrest[3];  // moments 0-2 of the f and g rest populations (the others vanish)
 };
@@ -51,7 +52,15 @@ struct Geometry {
     long long plane; // elements per plane
     int hot_x0, hot_len;
     int sms;         // persistent grid size (one CTA per SM)
+    int open;        // open sides: 1 bottom, 2 top, 4 left, 8 right (left and right only together with all)
 };
+
+// Is lattice point (x, y) beyond an open side? (x is periodic unless the
+// left and right sides are open.)
+__host__ __device__ __forceinline__ bool beyond_open(const Geometry& G, int x, int y) {
+    return ((G.open & 1) && y < 0) || ((G.open & 2) && y >= G.ny) || ((G.open & 4) && x < 0) ||
+           ((G.open & 8) && x >= G.nx);
+}
 
 struct Launch {
     Geometry geo;

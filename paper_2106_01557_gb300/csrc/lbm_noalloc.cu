@@ -82,7 +82,10 @@ __global__ void __launch_bounds__(NA_NT) k_na_record(const Launch L, const doubl
         for (int i = 0; i < 9; ++i) {
             fl[i] = f[i * n + idx];
             gl[i] = g[i * n + idx];
-            rn[i] = rho_f[na_wrap(G, x + na_ex(i), y + na_ey(i))];
+            // beyond an open side the pair force sees the open sides' density
+            rn[i] = (G.open && beyond_open(G, x + na_ex(i), y + na_ey(i)))
+                        ? k.rho_open
+                        : rho_f[na_wrap(G, x + na_ex(i), y + na_ey(i))];
         }
         NodeMacro<double> s;
         node_macro(k, fl, gl, rn, s);

@@ -115,11 +115,13 @@ struct Acc {
 
 // Post-collision populations of node (x, y) into its own slot of the output
 // state (pull scheme), with the periodic ghost copies near the edges and the
-// wall reflections in the rows next to a wall. For shifted formats f and g
-// already hold the deviations from the rest populations.
-template <class S, class C>
+// wall reflections in the rows next to a wall, or, with OPEN, the ghosts
+// beyond the open sides. For shifted formats f and g already hold the
+// deviations from the rest populations.
+template <class S, class C, bool OPEN>
 __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
-                                           const C f[9], const C g[9], C rho, uint32_t dither) {
+                                           const C f[9], const C g[9], const NodeMacro<C>& s, uint32_t dither) {
+    const C rho = s.rho;
     const C* rest = k.rest;
     constexpr bool SH = Store<S, C>::SHIFTED;
     const int HX = G.HX;
@@ -158,14 +160,29 @@ __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& 
     if (G.walls && (y == 0 || y == G.ny - 1)) {
         // the reflections work on the populations themselves
         auto a = [&](const C* v, int i, int off) { return SH ? v[i] + rest[off + i] : v[i]; };
-        if (y == 0)
+        // (a side that is open has its own ghosts, below)
+        if (y == 0 && !(OPEN && (G.open & 1)))
             wall_store<S, C>(out, G, k, x, y, a(f, 4, 0), a(f, 7, 0), a(f, 8, 0), a(g, 4, 9), a(g, 7, 9), a(g, 8, 9), rho);
-        else
+        if (y == G.ny - 1 && !(OPEN && (G.open & 2)))
             wall_store<S, C>(out, G, k, x, y, a(f, 2, 0), a(f, 5, 0), a(f, 6, 0), a(g, 2, 9), a(g, 5, 9), a(g, 6, 9), rho);
+    }
+    if constexpr (OPEN) {
+        if (((G.open & 1) && y == 0) || ((G.open & 2) && y == G.ny - 1) || ((G.open & 4) && x == 0) ||
+            ((G.open & 8) && x == G.nx - 1)) {
+            Pops9<C> pf, pg;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                pf.v[i] = f[i];
+                pg.v[i] = g[i];
+            }
+            open_store<S, C>(out, G, k, x, y, pf, pg, s.rho, s.uhx, s.uhy, s.T);
+        }
     }
 }
 
-template <class S, class C>
+// OPEN: the case has open sides (a separate instantiation, so that the
+// common path carries none of their code)
+template <class S, class C, bool OPEN>
 __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     k_step(const __grid_constant__ CUtensorMap tmf, const __grid_constant__ CUtensorMap tmg,
            S* __restrict__ out, const __grid_constant__ Launch L, double* __restrict__ partials,
@@ -246,6 +263,10 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
         for (int idx = tid; idx < RX * RY; idx += NT) {
             const int rx = idx % RX, ry = idx / RX;
             const int gy = ty0 + ry - 1;
+            if (OPEN && beyond_open(G, tx0 + rx - 1, gy)) {  // the open sides' fixed density
+                srho[idx] = k.rho_open;
+                continue;
+            }
             int sy = ry + 1;  // staged row of this node: y - (ty0 - 2)
             if (G.walls) {    // density beyond a wall = adjacent fluid node's
                 if (gy < 0) sy -= gy;
@@ -297,7 +318,7 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
                 if (!(rho > C(0) && rho < C(1e30) && u2 < C(1e30))) acc.bad += C(1);  // also catches NaN
             }
             collide<Store<S, C>::SHIFTED>(k, f, g, s);
-            store_node<S, C>(out, G, k, x, y, f, g, s.rho,
+            store_node<S, C, OPEN>(out, G, k, x, y, f, g, s,
                              step_key ? fmix32((uint32_t)(y * G.nx + x) ^ step_key) | 1u : 0u);
         }
         if (NS == 1) {
@@ -386,7 +407,12 @@ cudaError_t launch_t(const Launch& L, const CUtensorMap* tmf, const CUtensorMap*
     const int ntiles = ((L.geo.nx + SM::BX - 1) / SM::BX) * ((L.geo.ny + SM::BY - 1) / SM::BY);
     const int slots = Tile<S>::CPS * L.geo.sms;
     const int grid = ntiles < slots ? ntiles : slots;
-    k_step<S, C><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats, counter, status);
+    if (L.geo.open)
+        k_step<S, C, true><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats,
+                                                                counter, status);
+    else
+        k_step<S, C, false><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats,
+                                                                 counter, status);
     return cudaGetLastError();
 }
 
@@ -417,14 +443,20 @@ size_t step_smem_bytes(int storage) {
     }
 }
 
+template <class S, class C>
+cudaError_t attr_t(int smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_step<S, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_step<S, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t prepare_step(int storage) {
     const int smem = (int)step_smem_bytes(storage);
     switch (storage) {
-        case S_F64: return cudaFuncSetAttribute(k_step<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case S_F32: return cudaFuncSetAttribute(k_step<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case S_F16: return cudaFuncSetAttribute(k_step<__half, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case S_BF16:
-            return cudaFuncSetAttribute(k_step<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case S_F64: return attr_t<double, double>(smem);
+        case S_F32: return attr_t<float, float>(smem);
+        case S_F16: return attr_t<__half, float>(smem);
+        case S_BF16: return attr_t<__nv_bfloat16, float>(smem);
     }
     return cudaErrorInvalidValue;
 }

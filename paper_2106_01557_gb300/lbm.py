@@ -44,13 +44,14 @@ class LbmConfig(ctypes.Structure):
         ("rho_ref", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("device", ctypes.c_int32), ("rounding", ctypes.c_int32),
+        ("open_sides", ctypes.c_int32), ("Tr_open", ctypes.c_double), ("rho_open", ctypes.c_double),
     ]
 
 
 class LbmParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "Tc", "pc", "T0", "rho_v", "rho_l", "p_s", "cs", "c", "dt", "G2", "a", "kappa",
-        "cv", "Cref", "beta", "kS", "hS", "bS", "se", "sq")]
+        "cv", "Cref", "beta", "kS", "hS", "bS", "se", "sq", "rho_open", "T_open")]
 
 
 _lib = None

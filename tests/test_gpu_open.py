@@ -1,0 +1,136 @@
+"""The open, heated sides (the outflow and constant-pressure condition of the
+paper's phase-change runs, paragraph after Eq. 19) on the GPU path: parity
+with the oracle for an open bottom (the Stefan problem's boundary) and for a
+box open on all four sides (the evaporating droplet's), and the Stefan front
+of Eq. 20 on the GPU. Tolerances as in the other parity tests: FP64 storage
+1e-12 and FP32 storage 1e-5 of max |gpu - oracle| / max |oracle|."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_common import gpu_case, oracle_case, rel_err
+from paper_2106_01557_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def _vapour_below_liquid(o, seed):
+    """Vapour in the lower quarter of the box, liquid above (tanh edge of
+    width 4), with seeded perturbations of rho, u and T."""
+    p = o.p
+    nx, ny = o.nx, o.ny
+    rho = p.rho_l + p.rho_v - inputs.layer(nx, ny, p.rho_v, p.rho_l, 0.25 * ny, 4.0)
+    rho = inputs.perturbed(rho, 0.02, seed)
+    ux, uy = inputs.random_velocity((ny, nx), 0.01 * p.c, seed + 1)
+    T = inputs.perturbed(np.full((ny, nx), p.T0), 0.02, seed + 2)
+    return rho, ux, uy, T
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_open_bottom_matches_oracle(gpu_lib, prec):
+    # 40 x 36: ragged tiles in both directions; the open bottom at T_r 0.85
+    # below the vapour, a bounce-back top wall above the liquid
+    kw = dict(walls=1, open_sides=1, Tr_open=0.85)
+    o = oracle_case(40, 36, **kw)
+    g = gpu_case(40, 36, prec, **kw)
+    assert g.params()["rho_open"] == pytest.approx(o.p.rho_out, rel=1e-12)
+    assert g.params()["T_open"] == pytest.approx(o.p.T_open, rel=1e-14)
+    fields = _vapour_below_liquid(o, seed=31)
+    o.init_fields(*fields)
+    g.set_fields(*fields)
+    f0, g0 = g.get_populations()
+    assert rel_err(f0, o.f) < TOL[prec] and rel_err(g0, o.g) < TOL[prec]
+    for n in (1, 49):
+        o.step(n)
+        g.step(n)
+        f, gg = g.get_populations()
+        assert rel_err(f, o.f) < TOL[prec], (n, rel_err(f, o.f))
+        assert rel_err(gg, o.g) < TOL[prec], (n, rel_err(gg, o.g))
+    m, mo = g.moments(), o.moments()
+    assert rel_err(m["rho"], mo["rho"]) < TOL[prec] and rel_err(m["T"], mo["T"]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_box_open_on_all_four_sides_matches_oracle(gpu_lib, prec):
+    # a perturbed droplet off the centre of a 40 x 36 box whose four sides
+    # (corners included) are open at T_r 0.85
+    kw = dict(walls=1, open_sides=15, Tr_open=0.85)
+    o = oracle_case(40, 36, **kw)
+    g = gpu_case(40, 36, prec, **kw)
+    p = o.p
+    rho = inputs.droplets(40, 36, p.rho_v, p.rho_l, [(17.0, 19.5)], [9.0], 4.0)
+    rho = inputs.perturbed(rho, 0.02, 41)
+    ux, uy = inputs.random_velocity((36, 40), 0.01 * p.c, 42)
+    T = inputs.perturbed(np.full((36, 40), p.T0), 0.02, 43)
+    o.init_fields(rho, ux, uy, T)
+    g.set_fields(rho, ux, uy, T)
+    for n in (1, 49):
+        o.step(n)
+        g.step(n)
+        f, gg = g.get_populations()
+        assert rel_err(f, o.f) < TOL[prec], (n, rel_err(f, o.f))
+        assert rel_err(gg, o.g) < TOL[prec], (n, rel_err(gg, o.g))
+
+
+def test_open_sides_keep_their_own_state_on_gpu(gpu_lib):
+    # the open state itself, at rest, is a fixed point of the GPU step
+    for sides, shape in ((1, (8, 32)), (15, (16, 16))):
+        g = gpu_case(*shape, "f64", walls=1, open_sides=sides, Tr_open=0.85)
+        p = g.params()
+        one = np.ones(shape[::-1])
+        g.set_fields(p["rho_open"] * one, 0 * one, 0 * one, p["T_open"] * one)
+        f0, g0 = g.get_populations()
+        g.step(300)
+        f1, g1 = g.get_populations()
+        assert rel_err(f1, f0) < 1e-13 and rel_err(g1, g0) < 1e-13
+
+
+def test_open_side_configurations_are_checked(gpu_lib):
+    from paper_2106_01557_gb300 import lbm
+    for kw in (dict(walls=0, open_sides=1, Tr_open=0.85), dict(walls=1, open_sides=4, Tr_open=0.85),
+               dict(walls=1, open_sides=1, Tr_open=0.0), dict(walls=1, open_sides=16, Tr_open=0.85)):
+        with pytest.raises(lbm.LbmError) as e:
+            gpu_case(16, 16, "f32", **kw)
+        assert e.value.code == -1
+
+
+def test_stefan_front_on_gpu(gpu_lib):
+    # The one-dimensional Stefan problem of Eq. 20, 21 on the GPU path, as the
+    # oracle's pin sets it up (open bottom at T_r 0.85 below vapour, liquid
+    # at T_r 0.8 above, c_v = 11.2 R so that Ste = 0.005 with the model's
+    # latent heat) on 8 x 256 nodes, FP32 storage, 2.5 million steps: X^2
+    # grows at 4 k^2 alpha_v (the oracle measured 1.03 of it over 2.5
+    # million steps on 4 x 256).
+    from oracle import thermo
+    paper = GOLD["stefan_problem"]
+    nx, ny = 8, 256
+    kw = dict(walls=1, open_sides=1, Tr_open=paper["Tr1"], c_v=11.2)
+    o = oracle_case(nx, ny, **kw)
+    p = o.p
+    g = gpu_case(nx, ny, "f32", **kw)
+    T0, T1 = p.T0, paper["Tr1"] * p.Tc
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    rho = thermo.planar_profile(T0, 1.0, 4.0, 1.0, o.cfg.K_EOS, o.cfg.K_INT, y - 20.0)
+    T = np.where(y < 20.0, T1 + (T0 - T1) * (y + 0.5) / 20.5, T0)
+    g.set_fields(rho, 0 * rho, 0 * rho, T)
+
+    def front():
+        r = g.moments()["rho"].mean(axis=1)
+        mid = 0.5 * (p.rho_v + p.rho_l)
+        j = int(np.argmax(r > mid))
+        return j - 0.5 + (mid - r[j - 1]) / (r[j] - r[j - 1])
+
+    g.step(1_000_000)
+    X1 = front()
+    g.step(1_500_000)
+    X2 = front()
+    k = thermo.stefan_root(paper["Ste"])
+    alpha_v = (4 + 3 * p.gamma1 + 2 * p.gamma2) / 6 * p.Cref * p.c * p.tauj_v / (p.rho_v * p.cv)
+    ratio = (X2 ** 2 - X1 ** 2) / (1_500_000 * p.dt) / (4 * k * k * alpha_v)
+    print("Stefan front", X1, X2, "growth of X^2 over 4 k^2 alpha_v:", ratio)
+    assert 0.9 < ratio < 1.15, ratio

@@ -57,8 +57,8 @@ MUTATIONS = [
      "t->L[3][4] = sigq * wj;", "t->L[3][4] = 2.0 * sigq * wj;"),
     ("force term dt F_m halved in m_bar (Eq. 12b)",
      "mb[k] = m[k] + P->dt * t.Fm[k] - Sx[k] + SQ[k];", "mb[k] = m[k] + 0.5 * P->dt * t.Fm[k] - Sx[k] + SQ[k];"),
-    ("open heated bottom: the bottom row's temperature instead of T_bottom",
-     "eq_populations(P, P->rho_out, s.ux, s.uy, P->T_bottom, fo, go);",
+    ("open heated side: the boundary node's temperature instead of T_open",
+     "eq_populations(P, P->rho_out, s.ux, s.uy, P->T_open, fo, go);",
      "eq_populations(P, P->rho_out, s.ux, s.uy, s.T, fo, go);"),
     ("q_m: gamma1 and gamma2 swapped between rows e and eps (SM Eq. S4b)",
      "{q, P->gamma1 * q, P->gamma2 * q,", "{q, P->gamma2 * q, P->gamma1 * q,"),

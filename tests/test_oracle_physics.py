@@ -246,22 +246,53 @@ def test_closed_box_heating_carries_the_models_latent_heat():
 
 
 def test_open_heated_bottom_keeps_its_own_state_at_rest():
-    # a uniform vapour at the open bottom's own state (rho_out, T_bottom),
+    # a uniform vapour at the open bottom's own state (rho_out, T_open),
     # at rest under an adiabatic top wall, is a fixed point: the ghost row
     # then carries exactly the bottom row's populations
-    o = Oracle(thermo.Config(nx=4, ny=32, walls=1, Tr_bottom=0.85, bottom_outflow=1))
+    o = Oracle(thermo.Config(nx=4, ny=32, walls=1, Tr_open=0.85, open_sides=1))
     p = o.p
     one = np.ones((32, 4))
-    o.init_fields(p.rho_out * one, 0 * one, 0 * one, p.T_bottom * one)
+    o.init_fields(p.rho_out * one, 0 * one, 0 * one, p.T_open * one)
     f0, g0 = o.f.copy(), o.g.copy()
     o.step(500)
     assert np.abs(o.f - f0).max() < 1e-14 * np.abs(f0).max()
     assert np.abs(o.g - g0).max() < 1e-14 * np.abs(g0).max()
-    # the open bottom's density: the vapour branch of Eq. 17 at T_bottom
+    # the open bottom's density: the vapour branch of Eq. 17 at T_open
     # and the liquid's saturation pressure
     ps = thermo.maxwell(p.T0, p.a_t, p.b_t, p.R)[2]
-    assert thermo.p_eos(p.rho_out, p.T_bottom, p.a_t, p.b_t, p.R) == pytest.approx(ps, rel=1e-12)
+    assert thermo.p_eos(p.rho_out, p.T_open, p.a_t, p.b_t, p.R) == pytest.approx(ps, rel=1e-12)
     assert p.rho_out < p.rho_v
+
+
+def test_box_open_on_all_four_sides_keeps_its_own_state_and_symmetry():
+    # With all four sides open (the evaporating droplet's box): a uniform
+    # vapour at the open state (rho_out, T_open) at rest is a fixed point --
+    # every ghost, corners included, then carries its nearest node's own
+    # populations -- and a centred droplet stays symmetric under the quarter
+    # turn and the mirror of the box, which a corner ghost taken from the
+    # wrong node, or a side missed, would break.
+    n = 16
+    o = Oracle(thermo.Config(nx=n, ny=n, walls=1, Tr_open=0.85, open_sides=15))
+    p = o.p
+    one = np.ones((n, n))
+    o.init_fields(p.rho_out * one, 0 * one, 0 * one, p.T_open * one)
+    f0, g0 = o.f.copy(), o.g.copy()
+    o.step(300)
+    assert np.abs(o.f - f0).max() < 1e-13 * np.abs(f0).max()
+    assert np.abs(o.g - g0).max() < 1e-13 * np.abs(g0).max()
+    from paper_2106_01557_gb300 import inputs
+    n = 24
+    o = Oracle(thermo.Config(nx=n, ny=n, walls=1, Tr_open=0.85, open_sides=15))
+    p = o.p
+    rho = inputs.droplets(n, n, p.rho_v, p.rho_l, [(n / 2 - 0.5, n / 2 - 0.5)], [6.0], 4.0)
+    o.init_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
+    o.step(200)
+    m = o.moments()
+    for f in ("rho", "T"):
+        a = m[f]
+        assert np.abs(a - np.rot90(a)).max() < 1e-12 * np.abs(a).max(), f
+        assert np.abs(a - a[:, ::-1]).max() < 1e-12 * np.abs(a).max(), f
+    assert np.abs(m["ux"] + m["ux"][:, ::-1]).max() < 1e-12 * p.c
 
 
 def test_stefan_front_with_an_open_heated_bottom():
@@ -274,7 +305,7 @@ def test_stefan_front_with_an_open_heated_bottom():
     # With the EOS's latent heat the front would run about 4.5 times faster.
     ny, nx = 128, 4
     paper = GOLD["stefan_problem"]
-    cfg = thermo.Config(nx=nx, ny=ny, walls=1, Tr_bottom=paper["Tr1"], bottom_outflow=1, c_v=11.2)
+    cfg = thermo.Config(nx=nx, ny=ny, walls=1, Tr_open=paper["Tr1"], open_sides=1, c_v=11.2)
     o = Oracle(cfg)
     p = o.p
     T0, T1 = p.T0, paper["Tr1"] * p.Tc
