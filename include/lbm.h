@@ -105,8 +105,7 @@ typedef struct lbm_config {
                               step, population), so that increments below
                               half a 16-bit step still act on average and
                               runs stay deterministic; other values:
-                              LBM_ERR_ARG. The batched sweep (lbm_batch_*)
-                              rounds to nearest whatever the value. */
+                              LBM_ERR_ARG. */
     int32_t open_sides;    /* open, heated sides at constant pressure, for the
                               Stefan problem and the evaporating droplet
                               (paragraph after Eq. 19, where the outflow and
@@ -165,6 +164,23 @@ int lbm_get_params(const lbm_handle* h, lbm_params* out);
  * reduced temperature Tr: out[0] rho_v, out[1] rho_l, out[2] saturation
  * pressure. Host only; LBM_ERR_ARG if Tr is not in (0.3, 1). */
 int lbm_maxwell(const lbm_config* cfg, double Tr, double out[3]);
+
+/* Coexistence across a curved interface at reduced temperature Tr (host
+ * only): the densities with equal chemical potential whose pressures
+ * (Eq. 17 with K_EOS) differ by dp, the liquid's above the vapour's --
+ * Laplace's law for a droplet of radius R in 2-D takes dp = sigma / R.
+ * out[0] rho_v, out[1] rho_l, out[2] the vapour's pressure; dp = 0 gives
+ * lbm_maxwell's values. LBM_ERR_ARG if Tr is not in (0.3, 1) or no such
+ * pair exists. */
+int lbm_coexistence(const lbm_config* cfg, double Tr, double dp, double out[3]);
+
+/* Surface tension of a planar interface at reduced temperature Tr from the
+ * square-gradient theory of the model's pressure tensor (Eq. 11, kappa of
+ * Eq. 16 with G of Eq. 18): sigma = int sqrt(2 kappa K_EOS Omega) drho
+ * over [rho_v, rho_l], Omega the grand-potential excess of Eq. 17's free
+ * energy. With the paper's K_EOS, K_INT it is 0.01 at Tr = 0.8 (the value
+ * the paper prescribes). Host only. */
+int lbm_surface_tension(const lbm_config* cfg, double Tr, double* sigma);
 
 /* Initial populations from macroscopic fields (rho, u_x, u_y, T), each
  * [ny][nx] double: m = m^eq - dt/2 F_m and n = n^eq - dt/2 q_m at every
@@ -243,11 +259,13 @@ int lbm_destroy(lbm_handle* h);
  * in device tables. The rows are the same model as lbm_step; a case in a
  * batch gives the same populations as that case on its own handle with the
  * same precision, up to floating-point rounding (the two kernels are
- * compiled separately; with 16-bit storage the batch rounds stores to
- * nearest, a single handle by default stochastically: lbm_config.rounding). Extension of the paper's method for
- * parameter sweeps (the paper runs single cases). Requirements: every
- * cfgs[i] periodic (walls = 0), one precision for all (LBM_F32, LBM_F16S or
- * LBM_BF16S), the stream and device of cfgs[0] are used. */
+ * compiled separately). With 16-bit storage the batch rounds its stores
+ * as lbm_config.rounding says, stochastically by default, with the dither
+ * of a single handle keyed by (node, batch step count), which the device
+ * keeps. Extension of the paper's method for parameter sweeps (the paper
+ * runs single cases). Requirements: every cfgs[i] periodic (walls = 0, no
+ * open sides), one precision for all (LBM_F32, LBM_F16S or LBM_BF16S), one
+ * rounding for all; the stream and device of cfgs[0] are used. */
 typedef struct lbm_batch lbm_batch;
 
 int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out);
@@ -263,8 +281,12 @@ int lbm_batch_conservation(lbm_batch* b, int32_t i, double out[6]);
 int lbm_batch_get_populations(lbm_batch* b, int32_t i, double* f, double* g);
 /* Case i's conservation record as reduced inside the most recent step
  * (per-tile FP32 partial sums, summed per case in FP64): layout of
- * lbm_step_stats out[0..6]. Synchronous. */
-int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[7]);
+ * lbm_step_stats out[0..6]; out[7] = the steps the batch has executed, as
+ * counted on the device (the count that keys stochastic rounding).
+ * Synchronous. */
+int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[8]);
+/* Steps the batch has executed (host count; includes autotuner trials). */
+int64_t lbm_batch_step_count(const lbm_batch* b);
 /* Autotuner: times every candidate (tile shape x work-list order) for
  * trial_steps steps on the current state and keeps the fastest; the trial
  * steps are real steps of every case (the state advances). choice[0] =

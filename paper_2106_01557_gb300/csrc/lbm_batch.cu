@@ -51,7 +51,8 @@ template <class S, class T>
 __global__ void __launch_bounds__(T::NT, 1)
     k_batch_step(const BatchItem* __restrict__ items, int nitems, const BatchCase* __restrict__ cases,
                  const KC<float>* __restrict__ kcs, const CUtensorMap* __restrict__ maps, int from,
-                 S* __restrict__ arena_out, float* __restrict__ partials, int* __restrict__ status) {
+                 S* __restrict__ arena_out, float* __restrict__ partials, int* __restrict__ status,
+                 double* __restrict__ steps, unsigned* __restrict__ done, int rounding) {
     using C = float;
     constexpr int BX = T::BX, BY = T::BY, HX = T::HX, WX = T::WX, NT = T::NT;
     constexpr int FR = T::FR, GR = T::GR, RX = T::RX, RY = T::RY;
@@ -104,6 +105,12 @@ __global__ void __launch_bounds__(T::NT, 1)
         if (item_of(1) < nitems) issue(item_of(1), 1);
     }
 
+    // stochastic rounding of 16-bit storage, keyed as for a single case by
+    // (node, step): the batch's step count is kept on the device by the last
+    // block of each launch
+    const uint32_t step_key = (Store<S, C>::SHIFTED && rounding)
+                                  ? fmix32((uint32_t)(long long)__ldcg(steps) * 0x9e3779b9u + 0x7f4a7c15u)
+                                  : 0u;
     bool ok = true;
     int it = 0;
     for (; item_of(it) < nitems; ++it) {
@@ -183,19 +190,34 @@ __global__ void __launch_bounds__(T::NT, 1)
             }
             // shifted formats: f and g leave the collision as deviations from the rest populations
             collide<Store<S, C>::SHIFTED>(k, f, g, s);
+            S sf[9], sg[9];
+            if (Store<S, C>::SHIFTED && step_key) {
+                uint32_t r = fmix32((uint32_t)(y * G.nx + x) ^ step_key) | 1u;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    r = lcg_next(r);
+                    Store<S, C>::cvt_sr2(f[i], g[i], r ^ (r >> 15), sf[i], sg[i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    sf[i] = Store<S, C>::cvt(f[i]);
+                    sg[i] = Store<S, C>::cvt(g[i]);
+                }
+            }
             const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
             if (interior) {
                 S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    o[i * G.plane] = Store<S, C>::cvt(f[i]);
-                    o[(9 + i) * G.plane] = Store<S, C>::cvt(g[i]);
+                    o[i * G.plane] = sf[i];
+                    o[(9 + i) * G.plane] = sg[i];
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    put<S>(out, G, i, x, y, Store<S, C>::cvt(f[i]));
-                    put<S>(out, G, 9 + i, x, y, Store<S, C>::cvt(g[i]));
+                    put<S>(out, G, i, x, y, sf[i]);
+                    put<S>(out, G, 9 + i, x, y, sg[i]);
                 }
             }
         }
@@ -221,6 +243,15 @@ __global__ void __launch_bounds__(T::NT, 1)
         for (int j = it; j <= it + 1; ++j) {
             const uint64_t t0 = globaltimer_ns();
             while (!mbar_try_wait(&bar[j & 1], (j >> 1) & 1) && globaltimer_ns() - t0 < WAIT_NS) {}
+        }
+    }
+    // the last block to finish counts the step (every block read the count
+    // at its start, before any block could reach this point)
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            *steps = *steps + 1.0;
+            *done = 0u;
         }
     }
 }
@@ -259,7 +290,8 @@ template <class S, class T>
 cudaError_t launch_bt(const BatchLaunch& B, int from, void* out, cudaStream_t s) {
     const int grid = B.nitems < B.sms ? B.nitems : B.sms;
     k_batch_step<S, T><<<grid, T::NT, T::BYTES, s>>>(B.items, B.nitems, B.cases, B.kcs, B.maps, from,
-                                                     static_cast<S*>(out), B.partials, B.status);
+                                                     static_cast<S*>(out), B.partials, B.status, B.steps,
+                                                     B.done, B.rounding);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,9 @@ struct BatchLaunch {
     float* partials;          // [nitems][8]
     int* status;
     int sms;
+    double* steps;            // steps the batch has executed (device; keys stochastic rounding)
+    unsigned* done;           // blocks of the current launch that have finished
+    int rounding;             // 16-bit storage: 0 nearest, 1 stochastic
 };
 
 void batch_tile(int storage, int variant, int* bx, int* by);

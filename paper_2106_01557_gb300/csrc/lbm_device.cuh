@@ -381,8 +381,9 @@ __device__ __forceinline__ void g_rest_wall(const KC<C>& k, C rho_w, C T_w, C& g
 
 // Store one post-collision value at physical (x, y) of plane p, with the
 // copies the periodic ghost cells need. y may be -1 or ny for a wall ghost,
-// and, with open left and right sides, x may be -1 or nx.
-template <class S>
+// and, with open left and right sides, x may be -1 or nx. XOPEN = false:
+// the caller knows that x is periodic.
+template <class S, bool XOPEN = true>
 __device__ __forceinline__ void put(S* __restrict__ out, const Geometry& G, int p, int x, int y, S v) {
     S* base = out + (long long)p * G.plane;
     const int HX = G.HX;
@@ -398,7 +399,7 @@ __device__ __forceinline__ void put(S* __restrict__ out, const Geometry& G, int 
         if (r >= nr) break;
         S* row = base + (long long)(rows[r] + 2) * G.pitch + G.PX;
         row[x] = v;
-        if (!(G.open & 12)) {
+        if (!(XOPEN && (G.open & 12))) {
             if (x < HX) row[x + G.nx] = v;
             if (x >= G.nx - HX) row[x - G.nx] = v;
         }

@@ -123,6 +123,29 @@ bool maxwell(const Eos& e, double* rv_out, double* rl_out, double* ps_out) {
     return rv > 0 && rl > rv;
 }
 
+// Coexistence across a curved interface at temperature T: mu(rho_v) =
+// mu(rho_l) and K_EOS (p(rho_l) - p(rho_v)) = dp (Laplace's law, dp = sigma
+// / R in 2-D), by Newton's method from the flat (Maxwell) pair.
+bool shifted_coexistence(const Eos& e, double K, double dp, double* rv, double* rl, double* pv) {
+    double ps;
+    if (!maxwell(e, rv, rl, &ps)) return false;
+    for (int it = 0; it < 50 && dp != 0.0; ++it) {
+        const double F1 = K * (e.p(*rl) - e.p(*rv)) - dp, F2 = e.mu(*rl) - e.mu(*rv);
+        const double a11 = -K * e.dp(*rv), a12 = K * e.dp(*rl);
+        const double a21 = -e.dp(*rv) / *rv, a22 = e.dp(*rl) / *rl;
+        const double det = a11 * a22 - a12 * a21;
+        if (!(std::fabs(det) > 0)) return false;
+        const double dv = (-F1 * a22 + F2 * a12) / det;
+        const double dl = (-a11 * F2 + a21 * F1) / det;
+        if (!std::isfinite(dv) || !std::isfinite(dl)) return false;
+        *rv += dv;
+        *rl += dl;
+        if (std::fabs(dv) <= 1e-15 * *rv && std::fabs(dl) <= 1e-15 * *rl) break;
+    }
+    *pv = K * e.p(*rv);
+    return *rv > 0 && *rl > *rv;
+}
+
 int storage_of(int precision) {
     switch (precision) {
         case LBM_F64: return S_F64;
@@ -522,6 +545,56 @@ int lbm_get_params(const lbm_handle* h, lbm_params* out) {
     return LBM_OK;
 }
 
+int lbm_coexistence(const lbm_config* cfg, double Tr, double dp, double out[3]) {
+    if (!cfg || !out) return fail(LBM_ERR_ARG, "null argument");
+    if (!(Tr > 0.3 && Tr < 1.0)) return fail(LBM_ERR_ARG, "Tr must lie in (0.3, 1)");
+    if (!std::isfinite(dp)) return fail(LBM_ERR_ARG, "non-finite pressure jump");
+    const double A = 0.4963880577294099, B = 0.1872945669467330;
+    const double Tc = (B / A) * cfg->a_t / (cfg->b_t * cfg->R);
+    Eos e{cfg->a_t, cfg->b_t, cfg->R, Tr * Tc};
+    if (!shifted_coexistence(e, cfg->K_EOS, dp, &out[0], &out[1], &out[2]))
+        return fail(LBM_ERR_ARG, "no coexistence with this pressure jump at this temperature");
+    return LBM_OK;
+}
+
+int lbm_surface_tension(const lbm_config* cfg, double Tr, double* sigma) {
+    if (!cfg || !sigma) return fail(LBM_ERR_ARG, "null argument");
+    if (!(Tr > 0.3 && Tr < 1.0)) return fail(LBM_ERR_ARG, "Tr must lie in (0.3, 1)");
+    const double A = 0.4963880577294099, B = 0.1872945669467330;
+    const double Tc = (B / A) * cfg->a_t / (cfg->b_t * cfg->R);
+    const double T = Tr * Tc;
+    Eos e{cfg->a_t, cfg->b_t, cfg->R, T};
+    double rv, rl, ps;
+    if (!maxwell(e, &rv, &rl, &ps)) return fail(LBM_ERR_ARG, "no coexistence at this temperature");
+    // free energy density per unit K_EOS whose pressure rho psi' - psi is Eq.
+    // 17's: psi = rho mu - p, mu from Eos::mu; the grand-potential excess
+    // Omega = psi - mu_s rho + p_s vanishes at both coexistence densities
+    const double mus = e.mu(rv);
+    auto omega = [&](double r) {
+        const double om = r * e.mu(r) - e.p(r) - mus * r + ps;
+        return om > 0.0 ? om : 0.0;
+    };
+    // square-gradient coefficient of Eq. 11 and 16: kappa = G^2 / 4 (dx = 1)
+    const double kappa = 0.25 * cfg->K_INT * cfg->K_INT * 2.0 * cfg->K_EOS * cfg->a_t;
+    // sigma = int sqrt(2 kappa K_EOS Omega) drho over [rho_v, rho_l]:
+    // 8-point Gauss-Legendre on 1,000 cells spaced closer at both ends
+    static const double gx[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    static const double gw[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    const int ncell = 1000;
+    const double pi = 3.14159265358979323846;
+    double s = 0.0;
+    for (int j = 0; j < ncell; ++j) {
+        const double lo = rv + (rl - rv) * 0.5 * (1.0 - std::cos(pi * j / ncell));
+        const double hi = rv + (rl - rv) * 0.5 * (1.0 - std::cos(pi * (j + 1) / ncell));
+        const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+        for (int q = 0; q < 4; ++q)
+            s += half * gw[q] * (std::sqrt(2.0 * kappa * cfg->K_EOS * omega(mid - half * gx[q])) +
+                                 std::sqrt(2.0 * kappa * cfg->K_EOS * omega(mid + half * gx[q])));
+    }
+    *sigma = s;
+    return LBM_OK;
+}
+
 int lbm_maxwell(const lbm_config* cfg, double Tr, double out[3]) {
     if (!cfg || !out) return fail(LBM_ERR_ARG, "null argument");
     if (!(Tr > 0.3 && Tr < 1.0)) return fail(LBM_ERR_ARG, "Tr must lie in (0.3, 1)");
@@ -810,6 +883,8 @@ struct lbm_batch {
     std::vector<BatchItem> items[2][3];  // [shape][order]
     float* d_partials = nullptr;
     int* d_status = nullptr;
+    double* d_steps = nullptr;   // step count (device copy, keys stochastic rounding)
+    unsigned* d_done = nullptr;  // finished blocks of the current launch
     double* d_rec = nullptr;     // 8 (case record) + 8 (conservation)
     double* scratch = nullptr;   // 18 x largest case
     double* aux_partials = nullptr;
@@ -833,13 +908,17 @@ static BatchLaunch batch_launch(lbm_batch* b) {
     B.partials = b->d_partials;
     B.status = b->d_status;
     B.sms = b->sms;
+    B.steps = b->d_steps;
+    B.done = b->d_done;
+    B.rounding = b->cfg[0].rounding;
     return B;
 }
 
 static void batch_release(lbm_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     void* ptrs[] = {b->arena[0], b->arena[1], b->d_cases[0], b->d_cases[1], b->d_kcs, b->d_maps[0], b->d_maps[1],
-                    b->d_items, b->d_partials, b->d_status, b->d_rec, b->scratch, b->aux_partials, b->aux_counter};
+                    b->d_items, b->d_partials, b->d_status, b->d_rec, b->scratch, b->aux_partials, b->aux_counter,
+                    b->d_steps, b->d_done};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -875,7 +954,11 @@ int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out) {
     size_t max_n = 0;
     for (int i = 0; i < ncases; ++i) {
         if (cfgs[i].precision != prec) { delete b; return fail(LBM_ERR_ARG, "all batch cases need one precision"); }
-        if (cfgs[i].walls != 0) { delete b; return fail(LBM_ERR_ARG, "batch cases must be periodic (walls = 0)"); }
+        if (cfgs[i].walls != 0 || cfgs[i].open_sides != 0) {
+            delete b;
+            return fail(LBM_ERR_ARG, "batch cases must be periodic (walls = 0, no open sides)");
+        }
+        if (cfgs[i].rounding != cfgs[0].rounding) { delete b; return fail(LBM_ERR_ARG, "all batch cases need one rounding"); }
         std::memset(&b->L[i], 0, sizeof(Launch));
         int rc = derive(cfgs[i], b->prm[i], b->L[i]);
         if (rc) { delete b; return rc; }
@@ -944,7 +1027,9 @@ int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out) {
               cudaMalloc(&b->d_rec, 16 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&b->scratch, 18 * max_n * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&b->aux_partials, nb_aux * NQ * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&b->aux_counter, sizeof(unsigned)) == cudaSuccess;
+              cudaMalloc(&b->aux_counter, sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&b->d_steps, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&b->d_done, sizeof(unsigned)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         batch_release(b);
@@ -995,7 +1080,9 @@ int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out) {
          cudaMemset(b->arena[0], 0, abytes) == cudaSuccess && cudaMemset(b->arena[1], 0, abytes) == cudaSuccess &&
          cudaMemset(b->d_status, 0, sizeof(int)) == cudaSuccess &&
          cudaMemset(b->d_partials, 0, (size_t)b->max_items * 8 * sizeof(float)) == cudaSuccess &&
-         cudaMemset(b->aux_counter, 0, sizeof(unsigned)) == cudaSuccess;
+         cudaMemset(b->aux_counter, 0, sizeof(unsigned)) == cudaSuccess &&
+         cudaMemset(b->d_steps, 0, sizeof(double)) == cudaSuccess &&
+         cudaMemset(b->d_done, 0, sizeof(unsigned)) == cudaSuccess;
     if (!ok) { batch_release(b); delete b; return fail(LBM_ERR_CUDA, "device initialisation failed"); }
     e = batch_prepare(b->storage);
     if (e == cudaSuccess) e = prepare_step(b->storage);
@@ -1111,15 +1198,19 @@ int lbm_batch_get_populations(lbm_batch* b, int32_t i, double* f, double* g) {
     return batch_check(b);
 }
 
-int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[7]) {
+int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[8]) {
     if (!b || i < 0 || i >= b->n || !out) return fail(LBM_ERR_ARG, "bad argument");
     CK(launch_batch_case_record(batch_launch(b), i, b->d_rec, b->stream));
-    double s[8];
+    double s[8], steps = 0.0;
     CK(cudaMemcpyAsync(s, b->d_rec, 8 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(&steps, b->d_steps, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     int rc = batch_check(b);
     for (int k = 0; k < 7; ++k) out[k] = s[k];
+    out[7] = steps;
     return rc;
 }
+
+int64_t lbm_batch_step_count(const lbm_batch* b) { return b ? b->steps : -1; }
 
 int lbm_batch_select(lbm_batch* b, int32_t shape, int32_t order) {
     if (!b || shape < 0 || shape > 1 || order < 0 || order > 2) return fail(LBM_ERR_ARG, "bad candidate");

@@ -75,7 +75,7 @@ struct Smem {
 // of f; of g adiabatic, or anti-bounce-back on a fixed-temperature segment).
 // fo[j], go[j] are the post-collision populations of the three directions
 // that leave through the wall: (4, 7, 8) at the bottom, (2, 5, 6) at the top.
-template <class S, class C>
+template <class S, class C, bool OPEN>
 __device__ __noinline__ void wall_store(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
                                         C fo0, C fo1, C fo2, C go0, C go1, C go2, C rho) {
     const bool bottom = (y == 0);
@@ -101,8 +101,8 @@ __device__ __noinline__ void wall_store(S* __restrict__ out, const Geometry& G, 
             g_rest_wall(k, rho, T_link, ga, gd);
             gv = C(2) * (j == 0 ? ga : gd) - gv;
         }
-        put<S>(out, G, opp, xg, yg, Store<S, C>::st(fv, k.rest[opp]));
-        put<S>(out, G, 9 + opp, xg, yg, Store<S, C>::st(gv, k.rest[9 + opp]));
+        put<S, OPEN>(out, G, opp, xg, yg, Store<S, C>::st(fv, k.rest[opp]));
+        put<S, OPEN>(out, G, 9 + opp, xg, yg, Store<S, C>::st(gv, k.rest[9 + opp]));
     }
 }
 
@@ -153,8 +153,8 @@ __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& 
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            put<S>(out, G, i, x, y, sf[i]);
-            put<S>(out, G, 9 + i, x, y, sg[i]);
+            put<S, OPEN>(out, G, i, x, y, sf[i]);
+            put<S, OPEN>(out, G, 9 + i, x, y, sg[i]);
         }
     }
     if (G.walls && (y == 0 || y == G.ny - 1)) {
@@ -162,9 +162,9 @@ __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& 
         auto a = [&](const C* v, int i, int off) { return SH ? v[i] + rest[off + i] : v[i]; };
         // (a side that is open has its own ghosts, below)
         if (y == 0 && !(OPEN && (G.open & 1)))
-            wall_store<S, C>(out, G, k, x, y, a(f, 4, 0), a(f, 7, 0), a(f, 8, 0), a(g, 4, 9), a(g, 7, 9), a(g, 8, 9), rho);
+            wall_store<S, C, OPEN>(out, G, k, x, y, a(f, 4, 0), a(f, 7, 0), a(f, 8, 0), a(g, 4, 9), a(g, 7, 9), a(g, 8, 9), rho);
         if (y == G.ny - 1 && !(OPEN && (G.open & 2)))
-            wall_store<S, C>(out, G, k, x, y, a(f, 2, 0), a(f, 5, 0), a(f, 6, 0), a(g, 2, 9), a(g, 5, 9), a(g, 6, 9), rho);
+            wall_store<S, C, OPEN>(out, G, k, x, y, a(f, 2, 0), a(f, 5, 0), a(f, 6, 0), a(g, 2, 9), a(g, 5, 9), a(g, 6, 9), rho);
     }
     if constexpr (OPEN) {
         if (((G.open & 1) && y == 0) || ((G.open & 2) && y == G.ny - 1) || ((G.open & 4) && x == 0) ||

@@ -90,7 +90,10 @@ SIGNATURES = {
     "lbm_batch_synchronize": ([_H], ctypes.c_int),
     "lbm_batch_get_params": ([_H, ctypes.c_int32, ctypes.POINTER(LbmParams)], ctypes.c_int),
     "lbm_maxwell": ([ctypes.POINTER(LbmConfig), ctypes.c_double, _DP], ctypes.c_int),
+    "lbm_coexistence": ([ctypes.POINTER(LbmConfig), ctypes.c_double, ctypes.c_double, _DP], ctypes.c_int),
+    "lbm_surface_tension": ([ctypes.POINTER(LbmConfig), ctypes.c_double, _DP], ctypes.c_int),
     "lbm_batch_nodes": ([_H], ctypes.c_int64),
+    "lbm_batch_step_count": ([_H], ctypes.c_int64),
     "lbm_batch_bytes_per_step": ([_H], ctypes.c_double),
     "lbm_batch_destroy": ([_H], ctypes.c_int),
     "lbm_surrogate_create": ([ctypes.c_void_p, ctypes.POINTER(_H)], ctypes.c_int),
@@ -166,6 +169,22 @@ def maxwell(cfg: LbmConfig, Tr: float):
     out = np.zeros(3)
     _check(load().lbm_maxwell(ctypes.byref(cfg), float(Tr), _host_ptr(out)))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def coexistence(cfg: LbmConfig, Tr: float, dp: float = 0.0):
+    """Densities (rho_v, rho_l) with equal chemical potential whose pressures
+    differ by dp (Laplace's law: sigma / R), and the vapour's pressure, from
+    the library's host solver."""
+    out = np.zeros(3)
+    _check(load().lbm_coexistence(ctypes.byref(cfg), float(Tr), float(dp), _host_ptr(out)))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def surface_tension(cfg: LbmConfig, Tr: float) -> float:
+    """Planar surface tension at Tr from square-gradient theory (library host code)."""
+    out = np.zeros(1)
+    _check(load().lbm_surface_tension(ctypes.byref(cfg), float(Tr), _host_ptr(out)))
+    return float(out[0])
 
 
 NOALLOC_MAX_NODES = 1 << 20
@@ -348,9 +367,13 @@ class Batch:
         return f, g
 
     def step_stats(self, i):
-        out = np.zeros(7)
+        out = np.zeros(8)
         _check(self.lib.lbm_batch_step_stats(self.h, int(i), _host_ptr(out)))
         return out
+
+    @property
+    def steps(self) -> int:
+        return int(self.lib.lbm_batch_step_count(self.h))
 
     def autotune(self, trial_steps=10):
         choice = (ctypes.c_int32 * 2)()

@@ -114,6 +114,32 @@ def test_library_maxwell_matches_oracle_on_host(lib):
         lbm.maxwell(cfg, 1.1)
 
 
+def test_library_laplace_coexistence_and_surface_tension_on_host(lib):
+    # the library's host solvers for the curved-interface reference of the
+    # batched sweep, against the oracle's thermodynamics: its surface
+    # tension (square-gradient theory, the paper's sigma = 0.01 at T_r 0.8),
+    # and coexistence with a pressure jump, which must keep the chemical
+    # potentials equal and carry the jump
+    from oracle import thermo
+    from paper_2106_01557_gb300 import lbm
+    cfg = lbm.default_config(64, 64)
+    Tc, _ = thermo.critical_point(1.0, 4.0, 1.0)
+    for Tr in (0.65, 0.8, 0.9):
+        sig = lbm.surface_tension(cfg, Tr)
+        osig, _ = thermo.surface_tension_and_width(Tr * Tc, 1.0, 4.0, 1.0, cfg.K_EOS, cfg.K_INT)
+        assert sig == pytest.approx(osig, rel=1e-8), Tr
+        for R in (10.0, 40.0):
+            rv, rl, pv = lbm.coexistence(cfg, Tr, sig / R)
+            T = Tr * Tc
+            assert thermo.mu(rv, T, 1.0, 4.0, 1.0) == pytest.approx(thermo.mu(rl, T, 1.0, 4.0, 1.0), rel=1e-12)
+            assert (thermo.p_eos(rl, T, 1.0, 4.0, 1.0, cfg.K_EOS) - thermo.p_eos(rv, T, 1.0, 4.0, 1.0, cfg.K_EOS)
+                    == pytest.approx(sig / R, rel=1e-9))
+            mv, ml, _ = thermo.maxwell(T, 1.0, 4.0, 1.0)
+            assert rv > mv and rl > ml        # a droplet's vapour and liquid are both denser
+    assert lbm.surface_tension(cfg, 0.8) == pytest.approx(0.01, rel=1e-5)
+    assert lbm.coexistence(cfg, 0.8, 0.0)[:2] == pytest.approx(lbm.maxwell(cfg, 0.8)[:2], rel=1e-14)
+
+
 def test_null_arguments_are_rejected_without_gpu(lib):
     # every entry point checks its handle and required pointers before any
     # device work: LBM_ERR_ARG, a no-op for the destroy calls, -1 or 0 for the
@@ -122,7 +148,7 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     l = lbm.load()
     skip = {"lbm_last_error"}
     noop = {"lbm_destroy", "lbm_batch_destroy", "lbm_surrogate_destroy"}
-    queries = {"lbm_step_count": -1, "lbm_bytes_per_step": 0.0, "lbm_batch_nodes": 0,
+    queries = {"lbm_step_count": -1, "lbm_batch_step_count": -1, "lbm_bytes_per_step": 0.0, "lbm_batch_nodes": 0,
                "lbm_batch_bytes_per_step": 0.0, "lbm_surrogate_num_params": 0}
     for name, (args, res) in lbm.SIGNATURES.items():
         if name in skip:

@@ -102,3 +102,42 @@ def test_batch_autotune_picks_a_candidate(gpu_lib):
     assert np.all(ms > 0) and ms[3 * shape + order] == ms.min()
     b.step(25)
     b.synchronize()
+
+
+def test_batch_fp16_storage_matches_oracle(gpu_lib):
+    # FP16 shifted storage in the batch, stochastic rounding (the default),
+    # against the FP64 oracle at the single-lattice FP16 bounds after 100
+    # steps (rho 5e-3, T 8e-3 of the field's largest value, u 5e-4 of c): a
+    # perturbed slab on 100 x 37 and a droplet case at another temperature;
+    # the device's step count, which keys the rounding, follows the steps
+    from oracle import Oracle, thermo
+    from paper_2106_01557_gb300 import inputs, lbm
+    shapes = [(100, 37, 0.8), (72, 64, 0.85)]
+    cfgs = [lbm.default_config(nx, ny, precision="f16s", Tr0=tr) for nx, ny, tr in shapes]
+    assert all(c.rounding == 1 for c in cfgs)
+    b = lbm.Batch(cfgs)
+    ors = []
+    for i, (nx, ny, tr) in enumerate(shapes):
+        o = Oracle(thermo.Config(nx=nx, ny=ny, Tr0=tr))
+        p = o.p
+        if i == 0:
+            rho = inputs.slab(nx, ny, p.rho_v, p.rho_l, nx / 4, 3 * nx / 4, 4.0)
+        else:
+            rho = inputs.droplets(nx, ny, p.rho_v, p.rho_l, [(nx / 2, ny / 2)], [14.0], 4.0)
+        rho = inputs.perturbed(rho, 0.02, 90 + i)
+        ux, uy = inputs.random_velocity((ny, nx), 0.01 * p.c, 92 + i)
+        T = inputs.perturbed(np.full((ny, nx), p.T0), 0.02, 94 + i)
+        o.init_fields(rho, ux, uy, T)
+        b.set_fields(i, rho, ux, uy, T)
+        ors.append(o)
+    b.step(100)
+    for o in ors:
+        o.step(100)
+    for i, o in enumerate(ors):
+        m, mo = b.moments(i), o.moments()
+        e_rho = rel_err(m["rho"], mo["rho"])
+        e_T = rel_err(m["T"], mo["T"])
+        e_u = max(np.abs(m["ux"] - mo["ux"]).max(), np.abs(m["uy"] - mo["uy"]).max()) / o.p.c
+        print(f"batch f16s case {i}: rho {e_rho:.3e} T {e_T:.3e} u/c {e_u:.3e}")
+        assert e_rho < 5e-3 and e_T < 8e-3 and e_u < 5e-4, (i, e_rho, e_T, e_u)
+    assert b.steps == 100 and b.step_stats(0)[7] == 100

@@ -203,10 +203,12 @@ def test_rollout_falls_back_and_accepts(gpu_lib):
     st = s.rollout(lat, 3, drift_tol=1e-3, verify_steps=2)
     assert st["fallbacks"] == 3 and st["accepted"] == 0
     assert lat.steps == 36  # every jump advances K + verify_steps
-    # a network whose projection is zero is the identity: every jump is accepted
+    # a network whose projection is zero is the identity: every jump is
+    # accepted (the young tanh-4 droplet still relaxes fast, so the local
+    # check is loosened here; it has a test of its own)
     p["proj"] = (0 * p["proj"][0], 0 * p["proj"][1])
     s.set_params(lbm.surrogate_params_from_oracle_layout(p))
-    st = s.rollout(lat, 3, drift_tol=1e-3, verify_steps=2)
+    st = s.rollout(lat, 3, drift_tol=1e-3, verify_steps=2, field_tol=0.5)
     # an accepted jump counts its K predicted steps and its verification steps
     assert st["accepted"] == 3 and st["fallbacks"] == 0 and lat.steps == 36 + 3 * (10 + 2)
     assert st["max_mass_drift"] < 1e-6
@@ -296,20 +298,31 @@ def test_rollout_rejects_a_local_temperature_spike(gpu_lib):
     wl[4, 0, 3], wl[4, 1, 3] = 1.0, -1.0        # h0 = x_T, h1 = -x_T (relu keeps each sign)
     p["lift"] = (wl, zero(p["lift"][1]))
     p["blocks"] = [((zero(w1), zero(b1)), (zero(w2), zero(b2))) for (w1, b1), (w2, b2) in p["blocks"]]
-    A = 10.0
+    s = lbm.Surrogate(off, scale, K=10, blocks=2)
+    lat = lbm.Lattice.create(nx, ny, precision="f32")
+    tol = 0.05
+    # the identity (zero projection) on the same state: the LB's own local
+    # change after the re-initialisation stays well inside the tolerance
+    p["proj"] = (zero(p["proj"][0]), zero(p["proj"][1]))
+    s.set_params(lbm.surrogate_params_from_oracle_layout(p))
+    lat.set_fields(rho, z, z, T)
+    st = s.rollout(lat, 1, drift_tol=1e-3, iface_tol=0.5, verify_steps=2, field_tol=tol)
+    own = st["max_local_change_T_all"]
+    assert st["accepted"] == 1 and own < 0.1 * tol, own
+    A = 30.0
     wp = zero(p["proj"][0])
     for tap in range(9):
         a = 8 * A if tap == 4 else -A
         wp[tap, 3, 0], wp[tap, 3, 1] = a, -a
     p["proj"] = (wp, zero(p["proj"][1]))
-    s = lbm.Surrogate(off, scale, K=10, blocks=2)
     s.set_params(lbm.surrogate_params_from_oracle_layout(p))
-    lat = lbm.Lattice.create(nx, ny, precision="f32")
     lat.set_fields(rho, z, z, T)
-    st = s.rollout(lat, 1, drift_tol=1e-3, iface_tol=0.5, verify_steps=2, field_tol=0.02)
+    st = s.rollout(lat, 1, drift_tol=1e-3, iface_tol=0.5, verify_steps=2, field_tol=tol)
+    print("local T change: identity", own, "spike", st["max_local_change_T_all"],
+          "energy drift", st["max_energy_drift_all"])
     assert st["fallbacks"] == 1 and st["accepted"] == 0 and st["unphysical"] == 0
     assert st["max_mass_drift_all"] < 1e-6 and st["max_energy_drift_all"] < 1e-3
-    assert st["max_local_change_T_all"] > 0.02
+    assert st["max_local_change_T_all"] > tol
     lat.set_fields(rho, z, z, T)
-    st = s.rollout(lat, 1, drift_tol=1e-3, iface_tol=0.5, verify_steps=2, field_tol=1.0)
+    st = s.rollout(lat, 1, drift_tol=1e-3, iface_tol=0.5, verify_steps=2, field_tol=10.0)
     assert st["accepted"] == 1
