@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -286,17 +287,25 @@ def precision_variants(lbm, torch, nsteps):
     return out
 
 
+# The sweep's relaxation rates of g: the paper leaves sigma_eps and sigma_p
+# free; 1.4 and 1.8 keep both bulk phases linearly stable at rest down to
+# T/Tc = 0.65 (the default rates only to 0.75) and pass every oracle pin.
+SWEEP_RATES = dict(sig_eps=1.4, sig_p=1.8)
+SWEEP_TR_LO = 0.65
+
+
 def batch_cases_fields(lbm, ncases, seed, precision, stream_ptr):
     """The heterogeneous sweep: ncases periodic boxes, sides log-uniform in
     [64, 512] (multiples of 8), one droplet of radius U[8, 0.3 min(nx, ny)]
-    at the centre, T/Tc uniform in [0.75, 0.95] (the model's bulk liquid is
-    linearly unstable below T/Tc = 0.75 with these rates), tanh edge of
-    width 4."""
+    at the centre, T/Tc uniform in [0.65, 0.95], tanh edge of width 4, with
+    the g rates sigma_eps = 1.4, sigma_p = 1.8 (below T/Tc = 0.65 the bulk
+    liquid of the model is linearly unstable even with these; the benchmark
+    list's range starts at 0.6)."""
     from paper_2106_01557_gb300 import inputs
-    cases = inputs.batch_cases(ncases, seed, tr_lo=0.75)
+    cases = inputs.batch_cases(ncases, seed, tr_lo=SWEEP_TR_LO)
     cfgs = []
     for c in cases:
-        cfg = lbm.default_config(c["nx"], c["ny"], precision=precision, Tr0=c["Tr"])
+        cfg = lbm.default_config(c["nx"], c["ny"], precision=precision, Tr0=c["Tr"], **SWEEP_RATES)
         if stream_ptr is not None:
             cfg.stream = stream_ptr
         cfgs.append(cfg)
@@ -360,10 +369,15 @@ def batch_variant(lbm, torch, steps, ncases=256, seed=4):
 def batch_study(steps, ncases=256, seed=4, precision="f16s"):
     """The heterogeneous sweep run for `steps` steps (FP16 storage, FP32
     math): per case, the droplet-centre (liquid) and corner (vapour) densities
-    against the Maxwell densities at each bulk's measured temperature, from
-    the library's own coexistence solver. A case whose droplet has
-    evaporated (centre density below the mean of the two Maxwell densities)
-    is reported and left out of the 1% statistic."""
+    against the coexistence densities across a curved interface (Laplace's
+    law): equal chemical potentials with the pressure jump sigma(T) / R, R the
+    droplet's equimolar radius sqrt(A / pi), A = sum (rho - rho_vb) /
+    (rho_lb - rho_vb) from the measured bulk densities, sigma from
+    square-gradient theory, each bulk at its own measured temperature (all
+    from the library's host solvers). The flat (Maxwell) reference is
+    reported beside it. A case whose droplet has evaporated (centre density
+    below the mean of the two Maxwell densities) is reported and left out of
+    the 1% statistic."""
     import torch
     from paper_2106_01557_gb300 import inputs, lbm
     stream = torch.cuda.Stream()
@@ -377,10 +391,21 @@ def batch_study(steps, ncases=256, seed=4, precision="f16s"):
     b.autotune(5)
     t0 = time.perf_counter()
     b.step(steps)
-    b.synchronize()
+    diverged = set()
+    try:
+        b.synchronize()
+    except lbm.LbmError:
+        # a case whose density went non-finite or non-positive: the cases are
+        # independent, so the others are still valid; the record of the last
+        # step names the diverged ones
+        diverged = {i for i in range(ncases) if b.step_stats(i)[6] > 0}
     wall = time.perf_counter() - t0
-    rows, ok, evap = [], 0, 0
+    rows, ok, ok_flat, evap = [], 0, 0, 0
     for i, c in enumerate(cases):
+        if i in diverged:
+            rows.append({"nx": c["nx"], "ny": c["ny"], "R0": round(c["R"], 2), "Tr": round(c["Tr"], 4),
+                         "diverged": True, "evaporated": False})
+            continue
         m = b.moments(i)
         p = b.params(i)
         cy, cx = c["ny"] // 2, c["nx"] // 2
@@ -389,22 +414,139 @@ def batch_study(steps, ncases=256, seed=4, precision="f16s"):
         Mv = lbm.maxwell(cfgs[i], Tv / p["Tc"])[0]
         Ml = lbm.maxwell(cfgs[i], Tl / p["Tc"])[1]
         gone = rl < 0.5 * (Mv + Ml)
-        ev, el = rv / Mv - 1, rl / Ml - 1
+        row = {"nx": c["nx"], "ny": c["ny"], "R0": round(c["R"], 2), "Tr": round(c["Tr"], 4),
+               "Tr_vapour": round(float(Tv / p["Tc"]), 5), "Tr_liquid": round(float(Tl / p["Tc"]), 5),
+               "err_rho_v_flat": rv / Mv - 1, "err_rho_l_flat": rl / Ml - 1, "evaporated": bool(gone)}
         if gone:
             evap += 1
-        elif abs(ev) < 0.01 and abs(el) < 0.01:
-            ok += 1
-        rows.append({"nx": c["nx"], "ny": c["ny"], "R0": round(c["R"], 2), "Tr": round(c["Tr"], 4),
-                     "Tr_vapour": round(float(Tv / p["Tc"]), 5), "Tr_liquid": round(float(Tl / p["Tc"]), 5),
-                     "err_rho_v": ev, "err_rho_l": el, "evaporated": bool(gone)})
+        else:
+            area = float(((m["rho"] - rv) / (rl - rv)).sum())
+            R = math.sqrt(max(area, 1e-12) / math.pi)
+            Lv = lbm.coexistence(cfgs[i], Tv / p["Tc"], lbm.surface_tension(cfgs[i], Tv / p["Tc"]) / R)[0]
+            Ll = lbm.coexistence(cfgs[i], Tl / p["Tc"], lbm.surface_tension(cfgs[i], Tl / p["Tc"]) / R)[1]
+            ev, el = rv / Lv - 1, rl / Ll - 1
+            row.update({"R_equimolar": round(R, 3), "err_rho_v": ev, "err_rho_l": el})
+            ok += abs(ev) < 0.01 and abs(el) < 0.01
+            ok_flat += abs(row["err_rho_v_flat"]) < 0.01 and abs(row["err_rho_l_flat"]) < 0.01
+        rows.append(row)
     b.close()
-    kept = ncases - evap
-    return {"metric": "batched sweep coexistence vs Maxwell", "steps": steps, "cases": ncases,
-            "storage": precision, "wall_s": wall, "evaporated": evap,
-            "within_1pct": ok, "of_kept": kept,
-            "max_abs_err_kept": max((max(abs(r["err_rho_v"]), abs(r["err_rho_l"])) for r in rows if not r["evaporated"]),
-                                    default=None),
+    kept = [r for r in rows if not r["evaporated"] and not r.get("diverged")]
+    med = lambda k: float(np.median([r[k] for r in kept])) if kept else None
+    return {"metric": "batched sweep coexistence vs the Laplace-shifted equilibrium", "steps": steps,
+            "cases": ncases, "storage": precision, "rates": SWEEP_RATES, "tr_range": [SWEEP_TR_LO, 0.95],
+            "wall_s": wall, "evaporated": evap, "diverged": len(diverged),
+            "diverged_cases": [rows[i] for i in sorted(diverged)],
+            "within_1pct": int(ok), "within_1pct_of_flat_maxwell": int(ok_flat), "of_kept": len(kept),
+            "median_err": {"rho_v": med("err_rho_v"), "rho_l": med("err_rho_l"),
+                           "rho_v_flat": med("err_rho_v_flat"), "rho_l_flat": med("err_rho_l_flat")},
+            "max_abs_err_kept": max((max(abs(r["err_rho_v"]), abs(r["err_rho_l"])) for r in kept), default=None),
             "per_case": rows}
+
+
+def droplet_study(n=1024, D0=256.0, Tr1=0.85, cv=11.2, precision="f32", samples=24, max_steps=40_000_000,
+                  every=None):
+    """A droplet of diameter D0 evaporating in an n x n box heated from all
+    four sides (open sides at T_r 0.85 and the liquid's saturation
+    pressure; the droplet at T_r 0.8; c_v = 11.2 R gives Ste = 0.005 with the
+    model's latent heat), as in the paper's D^2-law run (1024^2, D0 = 256).
+    Reports (D / D0)^2 against t* = alpha_v t / D0^2 (D from the liquid area,
+    D = 2 sqrt(A / pi), A = sum (rho - rho_v) / (rho_l - rho_v)), the slope of
+    a straight-line fit over 0.8 > (D/D0)^2 > 0.2 with its coefficient of
+    determination, and the quasi-steady conduction rate of a cylinder in a
+    square box, d(D^2)/dt = -8 alpha_v Ste / ln(1.08 (n / 2) / R), at the
+    fit's mid-point."""
+    from paper_2106_01557_gb300 import inputs, lbm
+    cfg = lbm.default_config(n, n, precision=precision, walls=1, open_sides=15, Tr_open=Tr1, c_v=cv)
+    lat = lbm.Lattice(cfg)
+    p = lat.params()
+    rho = inputs.droplets(n, n, p["rho_v"], p["rho_l"], [(n / 2 - 0.5, n / 2 - 0.5)], [D0 / 2], 4.0)
+    lat.set_fields(rho, 0 * rho, 0 * rho, 0 * rho + p["T0"])
+    h_lv = p["a"] * (p["rho_l"] - p["rho_v"]) + p["p_s"] * (1 / p["rho_v"] - 1 / p["rho_l"])
+    T1 = Tr1 * p["Tc"]
+    ste = p["rho_v"] * p["cv"] * (T1 - p["T0"]) / (p["rho_l"] * h_lv)
+    alpha_v = (4 + 3 * cfg.gamma1 + 2 * cfg.gamma2) / 6 * p["Cref"] * p["c"] * cfg.tau_j_v / (p["rho_v"] * p["cv"])
+    # quasi-steady lifetime estimate sets the sampling interval
+    life = D0 * D0 * math.log(1.08 * n / D0) / (8 * alpha_v * ste) / p["dt"]
+    every = every or max(1000, int(life / samples))
+    rows, done, t_start = [], 0, time.perf_counter()
+    while done < max_steps:
+        m = lat.moments()
+        r = m["rho"]
+        area = float(((r - p["rho_v"]) / (p["rho_l"] - p["rho_v"])).clip(0, None).sum())
+        D = 2 * math.sqrt(area / math.pi)
+        t = done * p["dt"]
+        rows.append({"steps": done, "t_star": alpha_v * t / D0 ** 2, "D2": (D / D0) ** 2,
+                     "T_centre_over_Tc": float(m["T"][n // 2, n // 2] / p["Tc"])})
+        if (D / D0) ** 2 < 0.05 or r.max() < 0.5 * (p["rho_v"] + p["rho_l"]):
+            break
+        lat.step(every)
+        done += every
+    lat.close()
+    pts = [(q["t_star"], q["D2"]) for q in rows if 0.2 < q["D2"] < 0.8]
+    fit = None
+    if len(pts) >= 3:
+        x = np.array([a for a, _ in pts])
+        y = np.array([b for _, b in pts])
+        A = np.vstack([x, np.ones_like(x)]).T
+        (k, c), res, *_ = np.linalg.lstsq(A, y, rcond=None)
+        ss = float(((y - (k * x + c)) ** 2).sum())
+        r2 = 1 - ss / float(((y - y.mean()) ** 2).sum())
+        Rm = 0.5 * D0 * math.sqrt(0.5)
+        qs = 8 * ste / math.log(1.08 * (n / 2) / Rm)      # -d(D/D0)^2 / dt* at (D/D0)^2 = 0.5
+        fit = {"slope": float(k), "intercept": float(c), "r2": r2, "quasi_steady_slope_at_half": -qs,
+               "slope_over_quasi_steady": float(-k / qs)}
+    return {"metric": "droplet evaporation (D^2 law) on the GPU path", "lattice": [n, n], "D0": D0,
+            "storage": precision, "Ste": ste, "alpha_v": alpha_v, "steps_per_sample": every,
+            "wall_s": time.perf_counter() - t_start, "fit": fit, "samples": rows}
+
+
+def stefan_study(times=None, nx=8, ny=1024, precision="f64"):
+    """The one-dimensional Stefan problem of Eq. 20, 21 at the paper's size
+    (1024 nodes along the heating, 8 across), run to the four times of its
+    Fig. 1: the open bottom at T_r 0.85 (outflow at the liquid's saturation
+    pressure) below vapour, liquid at T_r 0.8, c_v = 11.2 R so that Ste =
+    0.005 with the model's latent heat. The front X (where rho crosses the
+    mean of the coexistence densities, from the boundary at y = -1/2)
+    against X = 2 k sqrt(alpha_v (t + t0)), k the root of Eq. 21 and t0 set
+    by the initial front at X0 = 20.5."""
+    from paper_2106_01557_gb300 import lbm
+    Tr1, Ste, cv = 0.85, 0.005, 11.2
+    times = times or [4.01e6, 8.03e6, 12.04e6, 16.06e6]
+    cfg = lbm.default_config(nx, ny, precision=precision, walls=1, open_sides=1, Tr_open=Tr1, c_v=cv)
+    lat = lbm.Lattice(cfg)
+    p = lat.params()
+    T0, T1 = p["T0"], Tr1 * p["Tc"]
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    X0 = 20.0
+    rho = p["rho_v"] + (p["rho_l"] - p["rho_v"]) * 0.5 * (1 + np.tanh(2 * (y - X0) / 10.0))
+    T = np.where(y < X0, T1 + (T0 - T1) * (y + 0.5) / (X0 + 0.5), T0)
+    lat.set_fields(rho, 0 * rho, 0 * rho, T)
+    # the Stefan number with the model's latent heat a (rho_l - rho_v) + p_s (1/rho_v - 1/rho_l)
+    h_lv = p["a"] * (p["rho_l"] - p["rho_v"]) + p["p_s"] * (1 / p["rho_v"] - 1 / p["rho_l"])
+    ste = p["rho_v"] * p["cv"] * (T1 - T0) / (p["rho_l"] * h_lv)
+    f = lambda k: k * math.sqrt(math.pi) * math.exp(k * k) * math.erf(k) - Ste
+    lo, hi = 1e-12, 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if f(mid) < 0 else (lo, mid)
+    k = 0.5 * (lo + hi)
+    alpha_v = (4 + 3 * cfg.gamma1 + 2 * cfg.gamma2) / 6 * p["Cref"] * p["c"] * cfg.tau_j_v / (p["rho_v"] * p["cv"])
+    t0 = (X0 + 0.5) ** 2 / (4 * k * k * alpha_v)
+    mid_rho = 0.5 * (p["rho_v"] + p["rho_l"])
+    rows, done, t_start = [], 0, time.perf_counter()
+    for t in times:
+        n = int(round(t / p["dt"]))
+        lat.step(n - done)
+        done = n
+        r = lat.moments()["rho"].mean(axis=1)
+        j = int(np.argmax(r > mid_rho))
+        X = j - 0.5 + (mid_rho - r[j - 1]) / (r[j] - r[j - 1])
+        Xa = 2 * k * math.sqrt(alpha_v * (t + t0))
+        rows.append({"t": t, "steps": n, "X": X, "X_eq20": Xa, "rel_err": X / Xa - 1})
+    lat.close()
+    return {"metric": "Stefan front (Eq. 20) on the GPU path", "lattice": [nx, ny], "storage": precision,
+            "Ste": ste, "k": k, "alpha_v": alpha_v, "t0": t0, "wall_s": time.perf_counter() - t_start,
+            "fronts": rows}
 
 
 def precision_study(checkpoints=(1000, 10000, 100000)):
@@ -502,6 +644,11 @@ def main():
     ap.add_argument("--batch-precision", default="f16s", choices=["f32", "f16s", "bf16s"])
     ap.add_argument("--precision-study", type=int, default=0,
                     help="run FP64/FP32/FP16S/BF16S side by side to 1,000, 10,000 and this many steps; print the errors")
+    ap.add_argument("--droplet-study", type=int, default=0,
+                    help="box size n: a droplet of diameter n/4 evaporating in an n x n box heated on all sides")
+    ap.add_argument("--stefan-study", action="store_true",
+                    help="run the 1-D Stefan problem to the paper's Fig. 1 times and report the front against Eq. 20")
+    ap.add_argument("--stefan-precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--surrogate-ks", default="100,200",
                     help="jump lengths K of the extra surrogate studies (comma list; empty: none)")
     ap.add_argument("--surrogate-iters", type=int, default=3000,
@@ -518,6 +665,15 @@ def main():
     if args.batch_study:
         if rank == 0:
             print(json.dumps(batch_study(args.batch_study, precision=args.batch_precision)))
+        return
+    if args.stefan_study:
+        if rank == 0:
+            print(json.dumps(stefan_study(precision=args.stefan_precision)))
+        return
+    if args.droplet_study:
+        if rank == 0:
+            n = args.droplet_study
+            print(json.dumps(droplet_study(n=n, D0=n / 4)))
         return
     if args.precision_study:
         if rank == 0:

@@ -7,8 +7,11 @@
 //                another tensor, residual add (BF16 or FP32), BF16 or FP32
 //                output. Also serves the input gradient (flipped weights).
 //   k_wgrad      weight gradient: per (tap, 16 output channels) a GEMM over
-//                pixels, warps splitting the pixels, FP32 atomics at the end.
-//   k_bgrad      bias gradient.
+//                pixels, warps splitting the pixels; each block writes its
+//                partial sums, which k_wgrad_sum adds in block order.
+//   k_bgrad      bias gradient (per-block partials, summed in block order).
+// No reduction uses atomics: the order of every sum is fixed, so training
+// is bit-for-bit reproducible.
 //   k_mse        loss and its gradient.
 //   k_adam       optimiser step on FP32 master weights, refreshing the BF16
 //                forward and flipped copies.
@@ -195,7 +198,7 @@ struct WgCfg {
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(WT)
     k_wgrad(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dout, int N, int H, int W,
-            int in_relu, float* __restrict__ dw) {
+            int in_relu, float* __restrict__ part) {
     using Cf = WgCfg<CIN, COUT>;
     extern __shared__ __align__(16) unsigned char wg_smem[];
     const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
@@ -280,26 +283,40 @@ __global__ void __launch_bounds__(WT)
         __syncthreads();  // the stage is refilled by the next iteration's load
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    // accumulator (row co, column ci) -> dw[tap][co][ci], tap = 3 (dy + 1) + dx + 1
+    // accumulator (row co, column ci) of filter column dx = tap - 1 -> this
+    // block's partial [blockIdx.x][dy + 1][tap][co][ci]
+    float* pb = part + ((size_t)blockIdx.x * 3 + blockIdx.y) * 3 * COUT * CIN;
 #pragma unroll
     for (int tap = 0; tap < 3; ++tap) {
-        const int tp = 3 * (dy + 1) + tap;
 #pragma unroll
         for (int j = 0; j < Cf::NPW; ++j) {
             const int co = mt * 16 + g, ci = (nt0 + j) * 8 + 2 * t;
-            float* d = dw + ((size_t)tp * COUT + co) * CIN + ci;
-            atomicAdd(d, acc[tap][j][0]);
-            atomicAdd(d + 1, acc[tap][j][1]);
-            atomicAdd(d + 8 * CIN, acc[tap][j][2]);
-            atomicAdd(d + 8 * CIN + 1, acc[tap][j][3]);
+            float* d = pb + ((size_t)tap * COUT + co) * CIN + ci;
+            d[0] = acc[tap][j][0];
+            d[1] = acc[tap][j][1];
+            d[8 * CIN] = acc[tap][j][2];
+            d[8 * CIN + 1] = acc[tap][j][3];
         }
+    }
+}
+
+// dw[tp][co][ci] += sum over blocks b = 0, 1, ... of the partials, tap
+// tp = 3 (dy + 1) + dx + 1 (the order of the sum is fixed)
+__global__ void k_wgrad_sum(const float* __restrict__ part, int nblk, int cc, float* __restrict__ dw) {
+    const int n = 9 * cc;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int tp = e / cc, rem = e % cc;
+        const int by = tp / 3, tl = tp % 3;
+        float s = 0.f;
+        for (int b = 0; b < nblk; ++b) s += part[(((size_t)b * 3 + by) * 3 + tl) * cc + rem];
+        dw[e] += s;
     }
 }
 
 // Bias gradient db[c] += sum_p dOut[p][c] (C a multiple of 8, C <= 256):
 // thread = one 8-channel group of a pixel (16-byte loads, coalesced across
 // the block), per-thread sums reduced per channel group in shared memory.
-__global__ void k_bgrad(const __nv_bfloat16* __restrict__ dout, long long P, int C, float* __restrict__ db) {
+__global__ void k_bgrad(const __nv_bfloat16* __restrict__ dout, long long P, int C, float* __restrict__ part) {
     __shared__ float s[256][9];
     const int G8 = C / 8;
     const int per = blockDim.x / G8;  // pixels per block sweep
@@ -320,7 +337,25 @@ __global__ void k_bgrad(const __nv_bfloat16* __restrict__ dout, long long P, int
         const int g8 = c / 8, q = c % 8;
         float t = 0.f;
         for (int k = 0; k < per; ++k) t += s[k * G8 + g8][q];
-        atomicAdd(&db[c], t);
+        part[(size_t)blockIdx.x * C + c] = t;
+    }
+}
+
+// db[c] += sum over blocks b = 0, 1, ... of part[b][c]
+__global__ void k_bgrad_sum(const float* __restrict__ part, int nblk, int C, float* __restrict__ db) {
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float t = 0.f;
+        for (int b = 0; b < nblk; ++b) t += part[(size_t)b * C + c];
+        db[c] += t;
+    }
+}
+
+// *out += sum over i = 0 .. n-1 of part[i] (one thread, a fixed order)
+__global__ void k_sum_in_order(const double* __restrict__ part, int n, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += part[i];
+        *out += t;
     }
 }
 
@@ -330,7 +365,7 @@ __global__ void k_bgrad(const __nv_bfloat16* __restrict__ dout, long long P, int
 // 2 (mean(x_rho) - mean(target_rho)) / (4 P); csum[n] = sum over image n of
 // (x_rho - target_rho), HW pixels per image.
 __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ target, long long P,
-                      __nv_bfloat16* __restrict__ dout, double* __restrict__ loss, const double* __restrict__ csum,
+                      __nv_bfloat16* __restrict__ dout, double* __restrict__ part, const double* __restrict__ csum,
                       long long HW) {
     __shared__ double s[256];
     double acc = 0.0;
@@ -353,7 +388,7 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t
         if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(loss, s[0] / (double)(P * 4));
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0] / (double)(P * 4);
 }
 
 // Adam on FP32 master weights of one convolution ([9][COUT][CIN] and bias),
@@ -413,8 +448,10 @@ __global__ void k_unpack(const float* __restrict__ y, long long P, NormConsts nc
 // Mass-conserving output layer: per image n, sums[n] = sum of
 // (y_rho - x_rho) and, with a target, sums[N + n] = sum of (x_rho - t_rho);
 // then y_rho -= sums[n] / HW. y: [P][16], x, t: [P][4]; grid y = images.
+// Each block writes its two partial sums to part[n][block][2];
+// k_mass_sums adds them in block order.
 __global__ void k_mass_stats(const float* __restrict__ y, const float* __restrict__ x, const float* __restrict__ t,
-                             int N, long long HW, double* __restrict__ sums) {
+                             int N, long long HW, double* __restrict__ part) {
     __shared__ double s[2][256];
     const int n = blockIdx.y;
     double a = 0.0, b = 0.0;
@@ -434,9 +471,22 @@ __global__ void k_mass_stats(const float* __restrict__ y, const float* __restric
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        atomicAdd(&sums[n], s[0][0]);
-        if (t) atomicAdd(&sums[N + n], s[1][0]);
+        double* pp = part + ((size_t)n * gridDim.x + blockIdx.x) * 2;
+        pp[0] = s[0][0];
+        pp[1] = s[1][0];
     }
+}
+
+__global__ void k_mass_sums(const double* __restrict__ part, int N, int nblk, int with_t, double* __restrict__ sums) {
+    const int n = threadIdx.x + blockIdx.x * blockDim.x;
+    if (n >= N) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nblk; ++k) {
+        a += part[((size_t)n * nblk + k) * 2];
+        b += part[((size_t)n * nblk + k) * 2 + 1];
+    }
+    sums[n] = a;
+    if (with_t) sums[N + n] = b;
 }
 
 __global__ void k_mass_apply(float* __restrict__ y, long long P, long long HW, const double* __restrict__ sums) {
@@ -525,7 +575,7 @@ cudaError_t conv_t(const ConvArgs& a, cudaStream_t s, int sms) {
 
 template <int CIN, int COUT>
 cudaError_t wgrad_t(const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W, int in_relu, float* dw,
-                    cudaStream_t s, int sms) {
+                    float* part, cudaStream_t s, int sms) {
     using Cf = WgCfg<CIN, COUT>;
     static bool set = false;
     if (!set) {
@@ -537,7 +587,8 @@ cudaError_t wgrad_t(const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, i
     long long gx = (2 * sms + 2) / 3;  // with the three filter rows: about two CTAs per SM
     if (gx > chunks) gx = chunks;
     if (gx < 1) gx = 1;
-    k_wgrad<CIN, COUT><<<dim3((unsigned)gx, 3), WT, 2 * Cf::STAGE, s>>>(in, dout, N, H, W, in_relu, dw);
+    k_wgrad<CIN, COUT><<<dim3((unsigned)gx, 3), WT, 2 * Cf::STAGE, s>>>(in, dout, N, H, W, in_relu, part);
+    k_wgrad_sum<<<(9 * COUT * CIN + 255) / 256, 256, 0, s>>>(part, (int)gx, COUT * CIN, dw);
     return cudaGetLastError();
 }
 
@@ -565,13 +616,12 @@ cudaError_t launch_field_change(const double* a, const double* b, long long P, u
 }
 
 cudaError_t launch_mass_layer(float* y, const float* x, const float* t, int N, long long HW, double* sums,
-                              cudaStream_t s) {
+                              double* part, cudaStream_t s) {
     if (N < 1 || HW < 1) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * (size_t)N * sizeof(double), s);
-    if (e != cudaSuccess) return e;
     long long gx = (HW + 255) / 256;
-    if (gx > 256) gx = 256;
-    k_mass_stats<<<dim3((unsigned)gx, (unsigned)N), 256, 0, s>>>(y, x, t, N, HW, sums);
+    if (gx > MASS_BLOCKS) gx = MASS_BLOCKS;
+    k_mass_stats<<<dim3((unsigned)gx, (unsigned)N), 256, 0, s>>>(y, x, t, N, HW, part);
+    k_mass_sums<<<(N + 127) / 128, 128, 0, s>>>(part, N, (int)gx, t != nullptr, sums);
     const long long P = (long long)N * HW;
     long long g = (P + 255) / 256;
     if (g > 2048) g = 2048;
@@ -594,29 +644,37 @@ cudaError_t launch_conv(int cin, int cout, const ConvArgs& a, cudaStream_t s, in
     return cudaErrorInvalidValue;
 }
 
+size_t grad_scratch_floats(int sms) {
+    const size_t gx = (size_t)(2 * sms + 2) / 3;
+    const size_t w = gx * 9 * 64 * 64, b = (size_t)608 * 256;
+    return w > b ? w : b;
+}
+
 cudaError_t launch_wgrad(int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W,
-                         int in_relu, float* dw, cudaStream_t s, int sms) {
-    if (cin == 16 && cout == 64) return wgrad_t<16, 64>(in, dout, N, H, W, in_relu, dw, s, sms);
-    if (cin == 64 && cout == 64) return wgrad_t<64, 64>(in, dout, N, H, W, in_relu, dw, s, sms);
-    if (cin == 64 && cout == 16) return wgrad_t<64, 16>(in, dout, N, H, W, in_relu, dw, s, sms);
+                         int in_relu, float* dw, float* part, cudaStream_t s, int sms) {
+    if (cin == 16 && cout == 64) return wgrad_t<16, 64>(in, dout, N, H, W, in_relu, dw, part, s, sms);
+    if (cin == 64 && cout == 64) return wgrad_t<64, 64>(in, dout, N, H, W, in_relu, dw, part, s, sms);
+    if (cin == 64 && cout == 16) return wgrad_t<64, 16>(in, dout, N, H, W, in_relu, dw, part, s, sms);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, cudaStream_t s) {
+cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, float* part, cudaStream_t s) {
     if (C < 8 || C % 8 != 0 || C > 256) return cudaErrorInvalidValue;
     const int per = 256 / (C / 8);
     long long g = (P + per - 1) / per;
     if (g > 608) g = 608;
-    k_bgrad<<<(unsigned)g, 256, 0, s>>>(dout, P, C, db);
+    k_bgrad<<<(unsigned)g, 256, 0, s>>>(dout, P, C, part);
+    k_bgrad_sum<<<1, 256, 0, s>>>(part, (int)g, C, db);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mse(const float* out, const float* target, long long P, __nv_bfloat16* dout, double* loss,
-                       const double* csum, long long HW, cudaStream_t s) {
+                       const double* csum, long long HW, double* part, cudaStream_t s) {
     if (csum && HW < 1) return cudaErrorInvalidValue;
     long long g = (P + 255) / 256;
-    if (g > 1024) g = 1024;
-    k_mse<<<(unsigned)g, 256, 0, s>>>(out, target, P, dout, loss, csum, HW);
+    if (g > MSE_BLOCKS) g = MSE_BLOCKS;
+    k_mse<<<(unsigned)g, 256, 0, s>>>(out, target, P, dout, part, csum, HW);
+    k_sum_in_order<<<1, 32, 0, s>>>(part, (int)g, loss);
     return cudaGetLastError();
 }
 

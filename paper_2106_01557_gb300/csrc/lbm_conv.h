@@ -33,19 +33,27 @@ cudaError_t launch_conv(int cin, int cout, const ConvArgs& a, cudaStream_t s, in
 // (lbm_conv_tc.cu); bit 0 of the device int *status is set if a wait for
 // the tensor cores ran out of time (the output is then incomplete).
 cudaError_t launch_conv_tc(int cin, int cout, const ConvArgs& a, cudaStream_t s, int sms, int* status);
+// The gradient reductions write per-block partial sums to `part` and add
+// them in block order (no atomics, so results are reproducible bit for
+// bit); grad_scratch_floats(sms) floats serve both.
+size_t grad_scratch_floats(int sms);
 cudaError_t launch_wgrad(int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W,
-                         int in_relu, float* dw, cudaStream_t s, int sms);
-cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, cudaStream_t s);
+                         int in_relu, float* dw, float* part, cudaStream_t s, int sms);
+cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, float* part, cudaStream_t s);
+// blocks per image of the mass layer's sums: part holds 2 MASS_BLOCKS N doubles
+constexpr int MASS_BLOCKS = 256;
+// loss partials: part holds MSE_BLOCKS doubles
+constexpr int MSE_BLOCKS = 1024;
 // csum (may be null): per-image sums of (x_rho - target_rho) of the
 // mass-conserving output layer, HW pixels per image
 cudaError_t launch_mse(const float* out, const float* target, long long P, __nv_bfloat16* dout, double* loss,
-                       const double* csum, long long HW, cudaStream_t s);
+                       const double* csum, long long HW, double* part, cudaStream_t s);
 // Mass-conserving output layer on y [N*HW][16] given the input x [N*HW][4]:
 // y_rho -= mean over each image of (y_rho - x_rho). With a target t, also
 // sums[N + n] = sum over image n of (x_rho - t_rho) for launch_mse.
 // sums: 2 N doubles of scratch.
 cudaError_t launch_mass_layer(float* y, const float* x, const float* t, int N, long long HW, double* sums,
-                              cudaStream_t s);
+                              double* part, cudaStream_t s);
 cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float b1, float b2, float eps,
                         float c1, float c2, cudaStream_t s);
 cudaError_t launch_refresh(const float* w, int cin, int cout, int cin_real, int cout_real, __nv_bfloat16* w16,

@@ -67,6 +67,9 @@ struct lbm_surrogate {
     double* d_loss = nullptr;
     unsigned long long* d_cnt = nullptr;  // field checks (4 counts)
     double* d_msum = nullptr;        // mass-layer sums, 2 per image
+    double* d_mpart = nullptr;       // their per-block partials (2 MASS_BLOCKS per image)
+    double* d_lpart = nullptr;       // loss partials (MSE_BLOCKS)
+    float* gpart = nullptr;          // weight- and bias-gradient partials
     int msum_cap = 0;
     int* d_status = nullptr;         // bit 0: a tensor-core wait ran out of time
     double* fields = nullptr;        // 4 planes of the rollout case (device)
@@ -206,8 +209,8 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
     }
     // projection: its input is relu(h_B)
     Layer& proj = s->layers.back();
-    SCK(launch_wgrad(C, 16, s->h[B], s->dy16, N, H, W, 1, proj.gw, s->stream, s->sms));
-    SCK(launch_bgrad(s->dy16, P, 16, proj.gb, s->stream));
+    SCK(launch_wgrad(C, 16, s->h[B], s->dy16, N, H, W, 1, proj.gw, s->gpart, s->stream, s->sms));
+    SCK(launch_bgrad(s->dy16, P, 16, proj.gb, s->gpart, s->stream));
     ConvArgs a = cargs(s->dy16, proj.wflip, nullptr, N, H, W, 0);
     a.mask = s->h[B];
     a.out16 = s->g0;  // d h_B
@@ -218,14 +221,14 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
         Layer& L1 = s->layers[1 + 2 * b];
         Layer& L2 = s->layers[2 + 2 * b];
         // h_{b+1} = h_b + conv2(relu(z1)); d z2 = d h_{b+1}
-        SCK(launch_wgrad(C, C, s->z1[b], dh, N, H, W, 1, L2.gw, s->stream, s->sms));
-        SCK(launch_bgrad(dh, P, C, L2.gb, s->stream));
+        SCK(launch_wgrad(C, C, s->z1[b], dh, N, H, W, 1, L2.gw, s->gpart, s->stream, s->sms));
+        SCK(launch_bgrad(dh, P, C, L2.gb, s->gpart, s->stream));
         a = cargs(dh, L2.wflip, nullptr, N, H, W, 0);
         a.mask = s->z1[b];
         a.out16 = s->g1;  // d z1
         CONV(C, C, a);
-        SCK(launch_wgrad(C, C, s->h[b], s->g1, N, H, W, 1, L1.gw, s->stream, s->sms));
-        SCK(launch_bgrad(s->g1, P, C, L1.gb, s->stream));
+        SCK(launch_wgrad(C, C, s->h[b], s->g1, N, H, W, 1, L1.gw, s->gpart, s->stream, s->sms));
+        SCK(launch_bgrad(s->g1, P, C, L1.gb, s->gpart, s->stream));
         a = cargs(s->g1, L1.wflip, nullptr, N, H, W, 0);
         a.mask = s->h[b];
         a.res16 = dh;
@@ -234,8 +237,8 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
         std::swap(dh, spare);
     }
     Layer& lift = s->layers[0];
-    SCK(launch_wgrad(16, C, s->x16, dh, N, H, W, 0, lift.gw, s->stream, s->sms));
-    SCK(launch_bgrad(dh, P, C, lift.gb, s->stream));
+    SCK(launch_wgrad(16, C, s->x16, dh, N, H, W, 0, lift.gw, s->gpart, s->stream, s->sms));
+    SCK(launch_bgrad(dh, P, C, lift.gb, s->gpart, s->stream));
     return LBM_OK;
 }
 
@@ -246,12 +249,15 @@ static int mass_layer(lbm_surrogate* s, int N, long long HW, const float* t32) {
     if (N > s->msum_cap) {
         SCK(cudaStreamSynchronize(s->stream));
         s_free(s->d_msum);
+        s_free(s->d_mpart);
         s->d_msum = nullptr;
+        s->d_mpart = nullptr;
         s->msum_cap = 0;
         SCK(cudaMalloc(&s->d_msum, 2 * (size_t)N * sizeof(double)));
+        SCK(cudaMalloc(&s->d_mpart, 2 * (size_t)MASS_BLOCKS * N * sizeof(double)));
         s->msum_cap = N;
     }
-    SCK(launch_mass_layer(s->y32, s->x32, t32, N, HW, s->d_msum, s->stream));
+    SCK(launch_mass_layer(s->y32, s->x32, t32, N, HW, s->d_msum, s->d_mpart, s->stream));
     return LBM_OK;
 }
 
@@ -311,6 +317,8 @@ int lbm_surrogate_create(const lbm_surrogate_config* cfg, lbm_surrogate** out) {
         }
     }
     ok = ok && cudaMalloc(&s->d_loss, sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->d_lpart, MSE_BLOCKS * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->gpart, grad_scratch_floats(s->sms) * sizeof(float)) == cudaSuccess &&
          cudaMalloc(&s->d_cnt, 4 * sizeof(unsigned long long)) == cudaSuccess &&
          cudaMalloc(&s->d_status, sizeof(int)) == cudaSuccess && cudaMemset(s->d_status, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
@@ -418,7 +426,7 @@ static int loss_and_backward(lbm_surrogate* s, const double* in, const double* t
     if (rc) return rc;
     SCK(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
     SCK(launch_mse(s->y32, s->t32, P, s->dy16, s->d_loss, s->cfg.conserve_mass ? s->d_msum + N : nullptr,
-                   (long long)H * W, s->stream));
+                   (long long)H * W, s->d_lpart, s->stream));
     rc = run_backward(s, N, H, W);
     if (rc) return rc;
     if (loss) {
@@ -629,7 +637,7 @@ int lbm_surrogate_destroy(lbm_surrogate* s) {
         s_free(L.vb); s_free(L.w16); s_free(L.wflip);
     }
     release_acts(s);
-    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->d_status); s_free(s->d_msum); s_free(s->fields); s_free(s->pred); s_free(s->ver); s_free(s->d_chg); s_free(s->snapshot);
+    s_free(s->d_loss); s_free(s->d_cnt); s_free(s->d_status); s_free(s->d_msum); s_free(s->d_mpart); s_free(s->d_lpart); s_free(s->gpart); s_free(s->fields); s_free(s->pred); s_free(s->ver); s_free(s->d_chg); s_free(s->snapshot);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return LBM_OK;

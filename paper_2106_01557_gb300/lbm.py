@@ -494,7 +494,7 @@ class Surrogate:
                                                  ctypes.byref(loss)))
         return loss.value
 
-    def rollout(self, lattice, njumps, drift_tol=1e-3, iface_tol=0.5, verify_steps=None, field_tol=0.02):
+    def rollout(self, lattice, njumps, drift_tol=1e-3, iface_tol=0.5, verify_steps=None, field_tol=0.2):
         """drift_tol: largest relative change of mass and of total energy per
         jump; iface_tol: largest mean interface displacement per jump, in
         lattice units; verify_steps: LB steps run from each surrogate state

@@ -176,7 +176,7 @@ def identity_local_change(sur, cfg, fields, K, kv, njumps=2):
 
 
 def rollout_study(sur, p, size=1024, njumps=10, K=50, tol=1e-3, iface_tol=0.5, seed=99, n_drop=24,
-                  field_tol=0.02):
+                  field_tol=0.2):
     """Surrogate rollout with LB fallback against the plain LB over the same
     njumps * (K + K/10) steps (each jump: K steps predicted, K/10 LB
     verification steps) on a size x size evaporation case: wall time of

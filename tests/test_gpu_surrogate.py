@@ -38,10 +38,15 @@ def _to_dev(x):
     return torch.from_numpy(np.ascontiguousarray(np.moveaxis(x, -1, 0))).cuda()
 
 
+# BF16 operands and activations with FP32 accumulation: the network's
+# change of the fields, element by element, within 2% of its largest value,
+# and every gradient tensor, element by element, within 5% of its largest
+# entry (measured: forward up to 0.6%, gradients up to 2.5%)
+FWD_TOL, GRAD_TOL = 2e-2, 5e-2
+
+
 def _close(d, d_ref):
-    # the network's change of the fields, compared at BF16 precision
-    assert np.abs(d - d_ref).max() < 2e-2 * np.abs(d_ref).max()
-    assert np.corrcoef(d.ravel(), d_ref.ravel())[0, 1] > 0.999
+    assert np.abs(d - d_ref).max() < FWD_TOL * np.abs(d_ref).max(), np.abs(d - d_ref).max() / np.abs(d_ref).max()
 
 
 # (N, H, W): one partial 128-pixel strip; several strips with a ragged 16-pixel
@@ -67,9 +72,9 @@ def test_forward_matches_oracle(gpu_lib, conv_path, shape, conserve_mass):
 def test_conv_paths_bit_identical(gpu_lib, shape):
     # both convolution paths sum each output's 9 CIN / 16 K-steps in the same
     # (dy, dx, channel chunk) order, each step a K = 16 product of BF16
-    # operands with FP32 accumulation: the forward output agrees bit for bit.
-    # The gradients agree to the rounding of the weight-gradient kernel's
-    # atomic FP32 sums, whose order varies from run to run. The 1 x 300 x 1024
+    # operands with FP32 accumulation: the forward output agrees bit for bit,
+    # and so do the gradients (the weight and bias gradients sum their
+    # per-block partials in a fixed order). The 1 x 300 x 1024
     # case gives each CTA a run of about 16 rows of eight 128-pixel strips,
     # some runs going on from one strip into the next.
     import torch
@@ -83,7 +88,7 @@ def test_conv_paths_bit_identical(gpu_lib, shape):
         outs.append(out)
         grads.append(s.loss_grad(x, t)[1])
     assert torch.equal(outs[0], outs[1])
-    assert np.linalg.norm(grads[0] - grads[1]) <= 1e-5 * np.linalg.norm(grads[1])
+    assert np.array_equal(grads[0], grads[1])
 
 
 def test_forward_full_size_sampled_windows(gpu_lib):
@@ -137,15 +142,17 @@ def test_gradients_match_oracle(gpu_lib, conv_path, conserve_mass, shape):
     g_ref = S.flatten(S.backward(p, cache, y_ref, t))
     loss, g = s.loss_grad(_to_dev(x), _to_dev(t))
     assert loss == pytest.approx(S.loss(y_ref, t), rel=2e-2)
-    off = 0
-    for gr in g_ref:
+    off, worst = 0, 0.0
+    for k, gr in enumerate(g_ref):
         n = gr.size
         gg = g[off:off + n].astype(np.float64)
         gr = gr.reshape(-1)
         off += n
-        err = np.linalg.norm(gg - gr) / max(np.linalg.norm(gr), 1e-30)
-        assert err < 0.05, (off, err)
+        err = np.abs(gg - gr).max() / max(np.abs(gr).max(), 1e-30)
+        worst = max(worst, err)
+        assert err < GRAD_TOL, (k, err)
     assert off == g.size
+    print(f"{conv_path} mass={conserve_mass} {shape}: largest per-tensor gradient error {worst:.3e}")
 
 
 def test_training_reduces_loss(gpu_lib):
@@ -162,6 +169,22 @@ def test_training_reduces_loss(gpu_lib):
         s.train_step(a, b, lr=2e-3)
     last = [s.loss_grad(a, b, grads=False)[0] for a, b in dev]
     assert np.mean(last) < 0.1 * np.mean(first)
+
+
+def test_training_is_reproducible_bit_for_bit(gpu_lib):
+    # no reduction of the training step uses atomics: two networks trained
+    # from the same weights on the same minibatches give the same losses and
+    # the same weights, bit for bit
+    xs = [_fields(4, 16, 32, 40 + k) for k in range(3)]
+    ts = [x + 0.2 * np.roll(x, 1, axis=1) for x in xs]
+    dev = [(_to_dev(x), _to_dev(t)) for x, t in zip(xs, ts)]
+    runs = []
+    for _ in range(2):
+        S, p, s = _make(blocks=2, seed=17, conserve_mass=True)
+        losses = [s.train_step(*dev[it % 3], lr=1e-3) for it in range(30)]
+        runs.append((losses, s.get_params()))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
 
 
 def test_first_adam_step_is_the_textbook_update(gpu_lib):
@@ -300,7 +323,7 @@ def test_rollout_rejects_a_local_temperature_spike(gpu_lib):
     p["blocks"] = [((zero(w1), zero(b1)), (zero(w2), zero(b2))) for (w1, b1), (w2, b2) in p["blocks"]]
     s = lbm.Surrogate(off, scale, K=10, blocks=2)
     lat = lbm.Lattice.create(nx, ny, precision="f32")
-    tol = 0.05
+    tol = 0.2
     # the identity (zero projection) on the same state: the LB's own local
     # change after the re-initialisation stays well inside the tolerance
     p["proj"] = (zero(p["proj"][0]), zero(p["proj"][1]))
@@ -309,7 +332,7 @@ def test_rollout_rejects_a_local_temperature_spike(gpu_lib):
     st = s.rollout(lat, 1, drift_tol=1e-3, iface_tol=0.5, verify_steps=2, field_tol=tol)
     own = st["max_local_change_T_all"]
     assert st["accepted"] == 1 and own < 0.1 * tol, own
-    A = 30.0
+    A = 80.0
     wp = zero(p["proj"][0])
     for tap in range(9):
         a = 8 * A if tap == 4 else -A
