@@ -211,16 +211,17 @@ def run_ours(args, rank, world):
     mlups = whole_job_mlups(nodes, world, ms_step)
 
     # end to end through the public API with host buffers: set fields from
-    # pinned host memory, run K steps, read the moments back to the host
+    # pinned host memory, run K steps, read the moments back into pinned
+    # host memory (the caller's buffers, filled in place)
     rho, ux, uy, T = (torch.from_numpy(a).pin_memory() for a in fields)
-    outs = {k: torch.empty((NY, NX), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy", "T")}
+    outs = {k: torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy() for k in ("rho", "ux", "uy", "T")}
+    lat.set_fields(rho.numpy(), ux.numpy(), uy.numpy(), T.numpy())   # untimed: first-touch of the pages
+    lat.moments(out=outs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     lat.set_fields(rho.numpy(), ux.numpy(), uy.numpy(), T.numpy())
     lat.step(args.steps)
-    m = lat.moments()
-    for k in outs:
-        outs[k].numpy()[...] = m[k]
+    lat.moments(out=outs)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": nodes * world * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 4 * 8 * nodes / args.steps, "d2h_bytes_per_step": 4 * 8 * nodes / args.steps,

@@ -184,8 +184,9 @@ int lbm_surface_tension(const lbm_config* cfg, double Tr, double* sigma);
 
 /* Initial populations from macroscopic fields (rho, u_x, u_y, T), each
  * [ny][nx] double: m = m^eq - dt/2 F_m and n = n^eq - dt/2 q_m at every
- * node (SM Eq. S3, S4), so that Eq. 14 returns the given fields exactly.
- * Synchronous. */
+ * node (SM Eq. S3, S4), so that Eq. 14 returns the given fields to the
+ * storage's precision (per-node arithmetic in FP64 for LBM_F64 storage, in
+ * FP32 for the others). Synchronous. */
 int lbm_set_fields(lbm_handle* h, const double* rho, const double* ux,
                    const double* uy, const double* T, int on_device);
 
@@ -193,7 +194,8 @@ int lbm_set_fields(lbm_handle* h, const double* rho, const double* ux,
 int lbm_step(lbm_handle* h, int n);
 
 /* Macroscopic fields of the current state (Eq. 13, 14), [ny][nx] double
- * each; any pointer may be NULL. Synchronous. */
+ * each; any pointer may be NULL. Per-node arithmetic in FP64 for LBM_F64
+ * storage, in FP32 for the others. Synchronous. */
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy,
                 double* T, int on_device);
 

@@ -108,9 +108,8 @@ __global__ void __launch_bounds__(T::NT, 1)
     // stochastic rounding of 16-bit storage, keyed as for a single case by
     // (node, step): the batch's step count is kept on the device by the last
     // block of each launch
-    const uint32_t step_key = (Store<S, C>::SHIFTED && rounding)
-                                  ? fmix32((uint32_t)(long long)__ldcg(steps) * 0x9e3779b9u + 0x7f4a7c15u)
-                                  : 0u;
+    const bool sr = Store<S, C>::SHIFTED && rounding;
+    const uint32_t step_key = sr ? fmix32((uint32_t)(long long)__ldcg(steps) * 0x9e3779b9u + 0x7f4a7c15u) : 0u;
     bool ok = true;
     int it = 0;
     for (; item_of(it) < nitems; ++it) {
@@ -191,13 +190,8 @@ __global__ void __launch_bounds__(T::NT, 1)
             // shifted formats: f and g leave the collision as deviations from the rest populations
             collide<Store<S, C>::SHIFTED>(k, f, g, s);
             S sf[9], sg[9];
-            if (Store<S, C>::SHIFTED && step_key) {
-                uint32_t r = fmix32((uint32_t)(y * G.nx + x) ^ step_key) | 1u;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    r = lcg_next(r);
-                    Store<S, C>::cvt_sr2(f[i], g[i], r ^ (r >> 15), sf[i], sg[i]);
-                }
+            if (sr) {
+                cvt_sr_node<S, C>(f, g, fmix32((uint32_t)(y * G.nx + x) ^ step_key), sf, sg);
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {

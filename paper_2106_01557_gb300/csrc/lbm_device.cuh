@@ -76,10 +76,10 @@ struct Store<__nv_bfloat16, float> {
 };
 
 // Dither of the stochastic rounding: the 32-bit finaliser of MurmurHash3
-// (A. Appleby) mixes (node, step) into a seed per node, and the linear
-// congruential step of Numerical Recipes (x -> 1664525 x + 1013904223)
-// gives one 32-bit value per pair of stored populations (its weak low half
-// is mixed with its high half before use).
+// (A. Appleby) mixes (node, step) into a seed h per node, uniform on 32 bits;
+// pair i of stored populations takes h K_i mod 2^32 with a fixed odd K_i
+// (multiplicative hashing, Knuth): a bijection of h, so each pair's 32 bits
+// are uniform too, at one multiply per pair.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -88,7 +88,17 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;
     return h;
 }
-__device__ __forceinline__ uint32_t lcg_next(uint32_t r) { return r * 1664525u + 1013904223u; }
+
+// The nine (f_i, g_i) pairs of a node converted with stochastic rounding
+// from the node's seed h (cvt_sr2: the upper 16 bits round f_i, the lower
+// 16 bits g_i).
+template <class S, class C>
+__device__ __forceinline__ void cvt_sr_node(const C f[9], const C g[9], uint32_t h, S sf[9], S sg[9]) {
+    constexpr uint32_t K[9] = {0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du, 0x27d4eb2fu, 0x165667b1u,
+                               0xd3a2646du, 0xfd7046c5u, 0xb55a4f09u, 0x61c88647u};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<S, C>::cvt_sr2(f[i], g[i], h * K[i], sf[i], sg[i]);
+}
 
 // Reciprocal: IEEE in FP64; in FP32 the hardware approximation (relative
 // error ~1e-7, far below the FP32 path's 1e-5 parity bound).

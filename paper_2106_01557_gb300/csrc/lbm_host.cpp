@@ -649,7 +649,9 @@ int lbm_set_fields(lbm_handle* h, const double* rho, const double* ux, const dou
     // ghost copies); clear first so the unread corners are defined too.
     const size_t bytes = (size_t)18 * h->L.geo.plane * h->esize;
     CK(cudaMemsetAsync(h->buf[0], 0, bytes, h->stream));
-    CK(launch_init(h->storage, h->L, d[0], d[1], d[2], d[3], h->buf[0], h->stream));
+    // per-node arithmetic in the storage's compute type: FP64 for FP64
+    // storage, FP32 otherwise (the stored values are FP32 or narrower)
+    CK(launch_init(h->storage, h->L, d[0], d[1], d[2], d[3], h->buf[0], h->stream, h->storage != S_F64));
     h->cur = 0;
     return check_status(h);
 }
@@ -723,7 +725,7 @@ int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, double* T, i
     double* d[4];
     for (int k = 0; k < 4; ++k) d[k] = outs[k] ? (on_device ? outs[k] : h->scratch + (1 + k) * n) : nullptr;
     CK(launch_moments(h->storage, h->L, h->buf[h->cur], h->scratch, d[0], d[1], d[2], d[3], nullptr, nullptr,
-                      nullptr, h->stream));
+                      nullptr, h->stream, h->storage != S_F64));
     if (!on_device)
         for (int k = 0; k < 4; ++k)
             if (outs[k]) CK(cudaMemcpyAsync(outs[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

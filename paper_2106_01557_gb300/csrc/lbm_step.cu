@@ -120,22 +120,17 @@ struct Acc {
 // deviations from the rest populations.
 template <class S, class C, bool OPEN>
 __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& G, const KC<C>& k, int x, int y,
-                                           const C f[9], const C g[9], const NodeMacro<C>& s, uint32_t dither) {
+                                           const C f[9], const C g[9], const NodeMacro<C>& s, bool sr, uint32_t seed) {
     const C rho = s.rho;
     const C* rest = k.rest;
     constexpr bool SH = Store<S, C>::SHIFTED;
     const int HX = G.HX;
     const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
-    // the values as stored: 16-bit storage rounds stochastically where a
-    // dither seed is given (non-zero), else to nearest
+    // the values as stored: 16-bit storage rounds stochastically (sr, from
+    // the node's seed), else to nearest
     S sf[9], sg[9];
-    if (SH && dither) {
-        uint32_t r = dither;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            r = lcg_next(r);
-            Store<S, C>::cvt_sr2(f[i], g[i], r ^ (r >> 15), sf[i], sg[i]);
-        }
+    if (SH && sr) {
+        cvt_sr_node<S, C>(f, g, seed, sf, sg);
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -230,9 +225,8 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     int it = 0;
     // stochastic rounding of 16-bit storage: the step count (kept in the
     // record by the last block of the previous launch) keys the dither
-    const uint32_t step_key = (Store<S, C>::SHIFTED && L.rounding)
-                                  ? fmix32((uint32_t)(long long)__ldcg(&stats[7]) * 0x9e3779b9u + 0x7f4a7c15u)
-                                  : 0u;
+    const bool sr = Store<S, C>::SHIFTED && L.rounding;
+    const uint32_t step_key = sr ? fmix32((uint32_t)(long long)__ldcg(&stats[7]) * 0x9e3779b9u + 0x7f4a7c15u) : 0u;
     // NS >= 2: one block barrier per tile. At the barrier after the density
     // pass of tile `it`, every thread has finished tile it-1, so its stage is
     // refilled with tile it+NS-1 and the other density buffer is free.
@@ -318,8 +312,7 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
                 if (!(rho > C(0) && rho < C(1e30) && u2 < C(1e30))) acc.bad += C(1);  // also catches NaN
             }
             collide<Store<S, C>::SHIFTED>(k, f, g, s);
-            store_node<S, C, OPEN>(out, G, k, x, y, f, g, s,
-                             step_key ? fmix32((uint32_t)(y * G.nx + x) ^ step_key) | 1u : 0u);
+            store_node<S, C, OPEN>(out, G, k, x, y, f, g, s, sr, fmix32((uint32_t)(y * G.nx + x) ^ step_key));
         }
         if (NS == 1) {
             __syncthreads();  // every thread is done with the stage: refill it

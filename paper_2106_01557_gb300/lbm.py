@@ -258,12 +258,18 @@ class Lattice:
         _check(self.lib.lbm_synchronize(self.h))
 
     def moments(self, out=None):
-        """dict rho, ux, uy, T as (ny, nx) float64 host arrays; or, with
-        out = dict of CUDA float64 tensors, filled on the device."""
+        """dict rho, ux, uy, T as (ny, nx) float64 host arrays; with out = a
+        dict of CUDA float64 tensors, filled on the device; with out = a dict
+        of C-contiguous float64 numpy arrays (e.g. pinned host memory),
+        filled in place."""
         if out is not None:
+            keys = ("rho", "ux", "uy", "T")
+            if isinstance(out["rho"], np.ndarray):
+                _check(self.lib.lbm_moments(self.h, *(_host_ptr(out[k]) for k in keys), 0))
+                return out
             import torch
             torch.cuda.current_stream().synchronize()
-            _check(self.lib.lbm_moments(self.h, *(_dev_ptr(out[k]) for k in ("rho", "ux", "uy", "T")), 1))
+            _check(self.lib.lbm_moments(self.h, *(_dev_ptr(out[k]) for k in keys), 1))
             return out
         res = {k: np.empty((self.ny, self.nx)) for k in ("rho", "ux", "uy", "T")}
         _check(self.lib.lbm_moments(self.h, *(_host_ptr(res[k]) for k in ("rho", "ux", "uy", "T")), 0))

@@ -134,3 +134,52 @@ def test_stefan_front_on_gpu(gpu_lib):
     ratio = (X2 ** 2 - X1 ** 2) / (1_500_000 * p.dt) / (4 * k * k * alpha_v)
     print("Stefan front", X1, X2, "growth of X^2 over 4 k^2 alpha_v:", ratio)
     assert 0.9 < ratio < 1.15, ratio
+
+
+def test_droplet_heated_from_all_sides_follows_the_d2_law(gpu_lib):
+    # N2, the evaporating droplet of the text after Eq. 21, scaled down: a
+    # droplet of diameter D0 = 32 in a 128 x 128 box open and heated on all
+    # four sides (T_r 0.85 at the liquid's saturation pressure), droplet at
+    # T_r 0.8, c_v = 11.2 R (Ste = 0.005 with the model's latent heat), FP32
+    # storage. (D / D0)^2, D from the liquid area, falls on a straight line
+    # in time (the D^2 law) over 0.8 > (D/D0)^2 > 0.2, and its slope is of
+    # the size the quasi-steady conduction through the vapour gives,
+    # d(D^2)/dt = -8 alpha_v Ste / ln(R_inf / R) with R_inf = 1.08 x the
+    # half-width of the square (a 1-D estimate that ignores the outward
+    # Stefan flow; the 256^2 run measured 0.65 of it). The droplet keeps its
+    # temperature near T_r 0.8 (evaporative cooling of 1-2%).
+    import math
+    n, D0 = 128, 32.0
+    kw = dict(walls=1, open_sides=15, Tr_open=0.85, c_v=11.2)
+    g = gpu_case(n, n, "f32", **kw)
+    p = g.params()
+    rho = inputs.droplets(n, n, p["rho_v"], p["rho_l"], [(n / 2 - 0.5, n / 2 - 0.5)], [D0 / 2], 4.0)
+    g.set_fields(rho, 0 * rho, 0 * rho, 0 * rho + p["T0"])
+    cv, Tc = p["cv"], p["Tc"]
+    h_lv = p["a"] * (p["rho_l"] - p["rho_v"]) + p["p_s"] * (1 / p["rho_v"] - 1 / p["rho_l"])
+    ste = p["rho_v"] * cv * (0.85 * Tc - p["T0"]) / (p["rho_l"] * h_lv)
+    assert ste == pytest.approx(0.005, rel=0.01)
+    alpha_v = (4 + 3 * -2.0 + 2 * 2.0) / 6 * p["Cref"] * p["c"] * 0.25 / (p["rho_v"] * cv)
+    ts, d2, Tcen = [], [], []
+    steps, every = 0, 25000
+    while True:
+        m = g.moments()
+        area = float(((m["rho"] - p["rho_v"]) / (p["rho_l"] - p["rho_v"])).clip(0, None).sum())
+        ts.append(alpha_v * steps * p["dt"] / D0 ** 2)
+        d2.append(4 * area / math.pi / D0 ** 2)
+        Tcen.append(m["T"][n // 2, n // 2] / Tc)
+        if d2[-1] < 0.15 or steps > 3_000_000:
+            break
+        g.step(every)
+        steps += every
+    ts, d2 = np.array(ts), np.array(d2)
+    sel = (d2 < 0.8) & (d2 > 0.2)
+    assert sel.sum() >= 8
+    k, c = np.polyfit(ts[sel], d2[sel], 1)
+    r2 = 1 - ((d2[sel] - (k * ts[sel] + c)) ** 2).sum() / ((d2[sel] - d2[sel].mean()) ** 2).sum()
+    qs = 8 * ste / math.log(1.08 * (n / 2) / (0.5 * D0 * math.sqrt(0.5)))
+    print(f"D^2 law: slope {k:.4e} per t*, r2 {r2:.6f}, quasi-steady {-qs:.4e}, ratio {-k / qs:.3f}, "
+          f"droplet T/Tc {min(Tcen):.4f}..{max(Tcen):.4f}")
+    assert r2 > 0.995
+    assert 0.4 < -k / qs < 1.0
+    assert all(0.77 < t < 0.801 for t in Tcen)

@@ -35,7 +35,10 @@ def test_derived_parameters_match_oracle(gpu_lib, prec):
 def test_init_populations_match_oracle(gpu_lib, prec):
     o, g = _pair(100, 37, prec)
     f, gg = g.get_populations()
-    tol = 1e-14 if prec == "f64" else 1e-7
+    # FP32 storage: the set-up computes in FP32 (a few ulps of the largest
+    # population); FP64 storage in FP64
+    tol = 1e-14 if prec == "f64" else 5e-7
+    print(prec, "init error", rel_err(f, o.f), rel_err(gg, o.g))
     assert rel_err(f, o.f) < tol
     assert rel_err(gg, o.g) < tol
 
