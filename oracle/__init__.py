@@ -73,6 +73,7 @@ class OrcParams(ctypes.Structure):
         ("T_bottom", ctypes.c_double), ("T_top", ctypes.c_double), ("T_hot", ctypes.c_double),
         ("hot_x0", ctypes.c_int), ("hot_len", ctypes.c_int),
         ("open_sides", ctypes.c_int), ("rho_out", ctypes.c_double), ("T_open", ctypes.c_double),
+        ("cubic", ctypes.c_int),
     ]
 
 
@@ -91,6 +92,8 @@ def _load():
             lib.orc_moments.restype = ctypes.c_int
             lib.orc_collide_node.argtypes = [pp, dp, dp, dp, dp, dp, dp]
             lib.orc_collide_node.restype = None
+            lib.orc_collide_node_r.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp]
+            lib.orc_collide_node_r.restype = None
             lib.orc_get_M.argtypes = [dp, dp]
             lib.orc_get_M.restype = None
             _lib = lib
@@ -170,13 +173,21 @@ class Oracle:
                          m["rek"].sum(), e_tot.sum(),
                          np.sqrt(m["ux"] ** 2 + m["uy"] ** 2).max()])
 
-    def collide_node(self, fl, gl, rho_nb):
+    def collide_node(self, fl, gl, rho_nb, dphi=None):
+        """One node's collision; dphi = the central differences (d_x(rho
+        u_x^3), d_y(rho u_y^3)) at the node, u over c, from which the
+        cubic-term source is formed (None: no source)."""
         fl, gl, rho_nb = (np.ascontiguousarray(a, dtype=np.float64) for a in (fl, gl, rho_nb))
         fb = np.zeros(9)
         gb = np.zeros(9)
         macro = np.zeros(8)
-        self.lib.orc_collide_node(ctypes.byref(self.cp), _ptr(fl), _ptr(gl), _ptr(rho_nb),
-                                  _ptr(fb), _ptr(gb), _ptr(macro))
+        if dphi is None:
+            self.lib.orc_collide_node(ctypes.byref(self.cp), _ptr(fl), _ptr(gl), _ptr(rho_nb),
+                                      _ptr(fb), _ptr(gb), _ptr(macro))
+        else:
+            r = np.ascontiguousarray(dphi, dtype=np.float64)
+            self.lib.orc_collide_node_r(ctypes.byref(self.cp), _ptr(fl), _ptr(gl), _ptr(rho_nb), _ptr(r),
+                                        _ptr(fb), _ptr(gb), _ptr(macro))
         return fb, gb, macro
 
 

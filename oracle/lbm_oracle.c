@@ -44,7 +44,18 @@
  *   open side carries the post-collision populations of its nearest fluid
  *   node with their equilibrium part moved to the open state (rho_out,
  *   T_open) at that node's velocity (non-equilibrium extrapolation);
- *   rho_out is the vapour at T_open and the liquid's saturation pressure.
+ *   rho_out is the vapour at T_open and the liquid's saturation pressure;
+ *   an optional elimination of the cubic velocity terms of the viscous
+ *   stress (paragraph after Eq. 16, whose "trivial modifications" are in
+ *   another paper): the equilibria of the third-order moments q_x, q_y
+ *   gain 3 rho u_x u_y^2 and 3 rho u_y u_x^2 (u over c), so that the
+ *   lattice's third moments Q_xyy, Q_xxy carry their rho u u u parts, and
+ *   the two that D2Q9 cannot carry (Q_xxx = j_x, Q_yyy = j_y) are made up
+ *   in the deviatoric normal stress: a source R_xx - R_yy in the p_xx row,
+ *   R_xx = -c d_x(rho u_x^3), R_yy = -c d_y(rho u_y^3) (central differences
+ *   of the neighbours' values), entering the f collision as dt (I - S/2) R
+ *   like a force term. The trace (row e) is left to the model's own
+ *   velocity coupling of that row in S.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -65,6 +76,7 @@ typedef struct {
                             walls), 4 left, 8 right (only with all four) */
     double rho_out;      /* their density (vapour at T_open and the liquid's p_s) */
     double T_open;       /* their temperature */
+    int cubic;           /* eliminate the cubic velocity terms (periodic boxes) */
 } orc_params;
 
 /* SM Eq. S1: e_i / c for i = 0..8 */
@@ -247,6 +259,11 @@ static void node_terms_build(const orc_params* P, const node_state* s, node_term
     double meq[9] = {rho, -2.0 * rho + 2.0 * eta + 3.0 * rho * u2, rho + P->beta * eta - 3.0 * rho * u2,
                      rho * uxh, -rho * uxh, rho * uyh, -rho * uyh,
                      rho * (uxh * uxh - uyh * uyh), rho * uxh * uyh};
+    if (P->cubic) {
+        /* q_x = 3 Q_xyy - 2 j_x: Q_xyy = rho u_x / 3 + rho u_x u_y^2 */
+        meq[4] += 3.0 * rho * uxh * uyh * uyh;
+        meq[6] += 3.0 * rho * uyh * uxh * uxh;
+    }
     double FU = Fxh * uxh + Fyh * uyh;
     double Fm[9] = {0.0, 6.0 * FU, -6.0 * FU, Fxh, -Fxh, Fyh, -Fyh,
                     2.0 * Fxh * uxh - 2.0 * Fyh * uyh, Fxh * uyh + Fyh * uxh};
@@ -312,9 +329,20 @@ static void node_terms_build(const orc_params* P, const node_state* s, node_term
     t->Y[6][1] = -uyh / 3.0; t->Y[6][7] = uyh;  t->Y[6][8] = -2.0 * uxh;
 }
 
-/* Collision at one node: Eq. 12b and 12c, back-transform with M^-1. */
+/* The cubic-term source in moment space from the central differences
+ * dphix = d_x(rho u_x^3), dphiy = d_y(rho u_y^3) (u over c) at the node:
+ * R_xx = -c dphix, R_yy = -c dphiy, in the p_xx row as R_xx - R_yy. */
+static void cubic_source(const orc_params* P, double dphix, double dphiy, double* Rm)
+{
+    for (int k = 0; k < 9; ++k) Rm[k] = 0.0;
+    double Rxx = -P->c * dphix, Ryy = -P->c * dphiy;
+    Rm[7] = Rxx - Ryy;
+}
+
+/* Collision at one node: Eq. 12b and 12c, back-transform with M^-1.
+ * Rm: the cubic-term source in moment space (row p_xx), or NULL. */
 static void node_collide(const orc_params* P, const double* fl, const double* gl,
-                         const node_state* s, double* fb, double* gb)
+                         const node_state* s, const double* Rm, double* fb, double* gb)
 {
     node_terms t;
     node_terms_build(P, s, &t);
@@ -324,6 +352,12 @@ static void node_collide(const orc_params* P, const double* fl, const double* gl
     matvec(t.S, tmp, Sx);
     matvec(t.S, t.Qm, SQ);
     for (int k = 0; k < 9; ++k) mb[k] = m[k] + P->dt * t.Fm[k] - Sx[k] + SQ[k];
+    if (Rm) {
+        /* dt (I - S/2) R, R a source like F_m */
+        double SR[9];
+        matvec(t.S, Rm, SR);
+        for (int k = 0; k < 9; ++k) mb[k] += P->dt * (Rm[k] - 0.5 * SR[k]);
+    }
 
     matvec(MM, gl, n);
     for (int k = 0; k < 9; ++k) tmp[k] = n[k] - t.neq[k] + 0.5 * P->dt * t.qm[k];
@@ -402,8 +436,24 @@ int orc_step(const orc_params* P, double* f, double* g, int nsteps)
     double* gn = (double*)malloc(9 * N * sizeof(double));
     if (!rho || !fn || !gn) { free(rho); free(fn); free(gn); return -1; }
 
+    double* phi = P->cubic ? (double*)malloc(2 * N * sizeof(double)) : NULL;
+    if (P->cubic && !phi) { free(rho); free(fn); free(gn); return -1; }
     for (int step = 0; step < nsteps; ++step) {
         rho_field(P, f, rho);
+        if (P->cubic) {
+            /* rho u_x^3 and rho u_y^3 (u over c) of every node, for the
+             * cubic-term source */
+            #pragma omp parallel for schedule(static)
+            for (long p = 0; p < (long)N; ++p) {
+                double fl[9], gl[9];
+                for (int i = 0; i < 9; ++i) { fl[i] = f[i * N + p]; gl[i] = g[i * N + p]; }
+                node_state s;
+                node_macro(P, fl, gl, rho, (int)(p % nx), (int)(p / nx), &s);
+                double ux = s.ux / P->c, uy = s.uy / P->c;
+                phi[p] = s.rho * ux * ux * ux;
+                phi[N + p] = s.rho * uy * uy * uy;
+            }
+        }
         /* nodes are independent and every push target is written once */
         #pragma omp parallel for schedule(static)
         for (int y = 0; y < ny; ++y)
@@ -413,7 +463,15 @@ int orc_step(const orc_params* P, double* f, double* g, int nsteps)
                 for (int i = 0; i < 9; ++i) { fl[i] = f[i * N + p]; gl[i] = g[i * N + p]; }
                 node_state s;
                 node_macro(P, fl, gl, rho, x, y, &s);
-                node_collide(P, fl, gl, &s, fb, gb);
+                double Rm[9];
+                if (P->cubic) {
+                    /* periodic central differences of rho u_x^3 along x and
+                     * rho u_y^3 along y */
+                    double dx = 0.5 * (phi[(size_t)y * nx + wrap(x + 1, nx)] - phi[(size_t)y * nx + wrap(x - 1, nx)]);
+                    double dy = 0.5 * (phi[N + (size_t)wrap(y + 1, ny) * nx + x] - phi[N + (size_t)wrap(y - 1, ny) * nx + x]);
+                    cubic_source(P, dx, dy, Rm);
+                }
+                node_collide(P, fl, gl, &s, P->cubic ? Rm : NULL, fb, gb);
                 int on_open = 0;
                 for (int i = 1; i < 9; ++i) on_open |= beyond_open(P, x + EX[i], y + EY[i]);
                 if (on_open) {
@@ -469,7 +527,7 @@ int orc_step(const orc_params* P, double* f, double* g, int nsteps)
         memcpy(f, fn, 9 * N * sizeof(double));
         memcpy(g, gn, 9 * N * sizeof(double));
     }
-    free(rho); free(fn); free(gn);
+    free(rho); free(fn); free(gn); free(phi);
     return 0;
 }
 
@@ -548,9 +606,19 @@ int orc_init(const orc_params* P, const double* rho_in, const double* ux_in,
 }
 
 /* One node's collision in isolation, for unit tests of Eq. 12b/12c:
- * inputs fl, gl (9 each), rho_nb[9] = rho at x + e_i (rho_nb[0] unused). */
+ * inputs fl, gl (9 each), rho_nb[9] = rho at x + e_i (rho_nb[0] unused),
+ * dphi (may be NULL) = the central differences d_x(rho u_x^3), d_y(rho
+ * u_y^3) at the node, from which the cubic-term source is formed. */
+void orc_collide_node_r(const orc_params* P, const double* fl, const double* gl,
+                        const double* rho_nb, const double* dphi, double* fb, double* gb, double* macro);
 void orc_collide_node(const orc_params* P, const double* fl, const double* gl,
                       const double* rho_nb, double* fb, double* gb, double* macro)
+{
+    orc_collide_node_r(P, fl, gl, rho_nb, NULL, fb, gb, macro);
+}
+
+void orc_collide_node_r(const orc_params* P, const double* fl, const double* gl,
+                        const double* rho_nb, const double* dphi, double* fb, double* gb, double* macro)
 {
     if (!MI_ready) invert_M();
     node_state s;
@@ -568,7 +636,9 @@ void orc_collide_node(const orc_params* P, const double* fl, const double* gl,
     s.q = s.Fx * s.ux + s.Fy * s.uy;
     s.rek = eg + 0.5 * P->dt * s.q;
     s.T = (s.rek - 0.5 * rho * (s.ux * s.ux + s.uy * s.uy)) / (rho * P->cv);
-    node_collide(P, fl, gl, &s, fb, gb);
+    double Rm[9];
+    if (dphi) cubic_source(P, dphi[0], dphi[1], Rm);
+    node_collide(P, fl, gl, &s, dphi ? Rm : NULL, fb, gb);
     if (macro) {
         macro[0] = s.rho; macro[1] = s.ux; macro[2] = s.uy; macro[3] = s.T;
         macro[4] = s.Fx; macro[5] = s.Fy; macro[6] = s.q; macro[7] = s.rek;

@@ -277,6 +277,7 @@ class Config:
     hot_len: int = 0
     open_sides: int = 0            # open, heated sides: 1 bottom, 2 top (with walls), 15 all four
     Tr_open: float = 0.0           # reduced T of the open sides
+    cubic: int = 0                 # eliminate the cubic velocity terms (periodic boxes only)
 
 
 @dataclass
@@ -331,6 +332,7 @@ class Params:
     open_sides: int
     rho_out: float
     T_open: float
+    cubic: int
 
 
 def _outflow_density(cfg: Config, T0, rv):
@@ -348,6 +350,12 @@ def _outflow_density(cfg: Config, T0, rv):
         raise ValueError("open sides need Tr_open > 0")
     ps = maxwell(T0, cfg.a_t, cfg.b_t, cfg.R)[2]
     return brentq(lambda r: p_eos(r, Tb, cfg.a_t, cfg.b_t, cfg.R) - ps, 1e-6 * rv, rv * T0 / Tb * 1.5)
+
+
+def _cubic_flag(cfg: Config) -> int:
+    if cfg.cubic and (cfg.walls or cfg.open_sides):
+        raise ValueError("the cubic-term elimination is built for periodic boxes only")
+    return 1 if cfg.cubic else 0
 
 
 def derive_params(cfg: Config) -> Params:
@@ -385,7 +393,8 @@ def derive_params(cfg: Config) -> Params:
         tauj_v=cfg.tau_j_v, tauj_l=cfg.tau_j_l, ax=cfg.accel_x, ay=cfg.accel_y,
         T_bottom=cfg.Tr_bottom * Tc, T_top=cfg.Tr_top * Tc, T_hot=cfg.Tr_hot * Tc,
         hot_x0=cfg.hot_x0, hot_len=cfg.hot_len,
-        open_sides=cfg.open_sides, rho_out=_outflow_density(cfg, T0, rv), T_open=cfg.Tr_open * Tc)
+        open_sides=cfg.open_sides, rho_out=_outflow_density(cfg, T0, rv), T_open=cfg.Tr_open * Tc,
+        cubic=_cubic_flag(cfg))
 
 
 def params_dict(p: Params) -> dict:

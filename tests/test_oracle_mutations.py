@@ -64,6 +64,15 @@ MUTATIONS = [
      "{q, P->gamma1 * q, P->gamma2 * q,", "{q, P->gamma2 * q, P->gamma1 * q,"),
     ("q_m: sign of the heat-flux rows flipped (SM Eq. S4b)",
      "q * uxh, -q * uxh, q * uyh, -q * uyh, 0.0, 0.0};", "-q * uxh, q * uxh, -q * uyh, q * uyh, 0.0, 0.0};"),
+    ("cubic-term source with the wrong sign",
+     "double Rxx = -P->c * dphix, Ryy = -P->c * dphiy;", "double Rxx = P->c * dphix, Ryy = P->c * dphiy;"),
+    ("cubic-term equilibrium of q_x dropped",
+     "meq[4] += 3.0 * rho * uxh * uyh * uyh;", "meq[4] += 0.0;"),
+    ("cubic-term rho u_x^3 with u not over c",
+     "double ux = s.ux / P->c, uy = s.uy / P->c;", "double ux = s.ux, uy = s.uy / P->c;"),
+    ("cubic-term difference along x one-sided",
+     "double dx = 0.5 * (phi[(size_t)y * nx + wrap(x + 1, nx)] - phi[(size_t)y * nx + wrap(x - 1, nx)]);",
+     "double dx = 0.5 * (phi[(size_t)y * nx + wrap(x + 1, nx)] - phi[(size_t)y * nx + x]);"),
     ("velocity without the half force (Eq. 14)",
      "s->ux = (jx + 0.5 * P->dt * s->Fx) / rho;", "s->ux = jx / rho;"),
 ]
@@ -83,6 +92,9 @@ PINS = [
     lambda: TS.test_bulk_phases_linearly_stable(0.8),
     TS.test_moving_vapour_linearly_stable,
     TS.test_sound_decays_alike_up_and_down_a_moving_vapour,
+    TS.test_cubic_terms_third_moments_of_the_equilibrium,
+    TS.test_cubic_source_cancels_most_of_the_u3_sound_asymmetry,
+    TS.test_cubic_terms_of_the_full_step_agree_with_the_linearised_step,
     TP.test_viscous_dissipation_term_gives_the_viscous_work,
     TP.test_density_wave_leaves_a_uniform_cross_flow_uniform,
     TP.test_poiseuille_flow_between_bounce_back_walls,
