@@ -127,6 +127,18 @@ typedef struct lbm_config {
     double rho_open;       /* density of the open sides; <= 0: the vapour
                               branch of Eq. 17 at Tr_open and the saturation
                               pressure at Tr0 */
+    int32_t cubic;         /* 1: eliminate the cubic velocity terms of the
+                              viscous stress (paragraph after Eq. 16; its
+                              details are in another paper, so this is the
+                              library's reading): the q_x, q_y equilibria
+                              gain 3 rho u_x u_y^2 and 3 rho u_y u_x^2 (u over
+                              c), and a source -c (d_x(rho u_x^3) -
+                              d_y(rho u_y^3)) enters the p_xx row of the f
+                              collision as dt (1 - s_p/2) R, from central
+                              differences of rho u^3 that a pass before each
+                              step computes. Periodic boxes only (walls = 0,
+                              no open sides), single cases only; 0 (default):
+                              the model as SM Eq. S3-S6 state it */
 } lbm_config;
 
 /* Quantities derived in lbm_init (Eq. 16-19, SM Eq. S3-S5 constants). */

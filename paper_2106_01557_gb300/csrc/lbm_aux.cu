@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -101,7 +103,7 @@ __global__ void k_init(const Launch L, const double* __restrict__ rho, const dou
         s.T = (C)T[idx];
         s.rek = r * k.cv * s.T + C(0.5) * r * (vx * vx + vy * vy);
         C meq[9], Fm[9], neq[9], qm[9], m[9], nn[9], f[9], g[9];
-        equilibria(k, s, meq, Fm, neq, qm);
+        equilibria(k, s, meq, Fm, neq, qm, L.cubic != 0);
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             m[j] = meq[j] - k.half_dt * Fm[j];
@@ -160,6 +162,32 @@ __global__ void k_rho(const Launch L, const S* __restrict__ buf, double* __restr
 #pragma unroll
         for (int i = 0; i < 9; ++i) r += load_c<S, C>(buf, G, i, x - ex_of(i), y - ey_of(i), (C)L.kf.rest[i]);
         rho[idx] = (double)r;
+    }
+}
+
+// rho u_x^3 and rho u_y^3 (u over c) of every node, phi [2][ny][nx], for
+// the cubic-term elimination; rho_f: the density field (k_rho). Periodic
+// boxes only.
+template <class S, class C>
+__global__ void k_phi(const Launch L, const S* __restrict__ buf, const double* __restrict__ rho_f,
+                      double* __restrict__ phi) {
+    const Geometry& G = L.geo;
+    const KC<C>& k = kc<C>(L);
+    const long long n = (long long)G.nx * G.ny;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % G.nx), y = (int)(idx / G.nx);
+        C f[9], g[9], rn[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            f[i] = load_c<S, C>(buf, G, i, x - ex_of(i), y - ey_of(i), (C)L.kf.rest[i]);
+            g[i] = C(0);
+            rn[i] = (C)rho_nb(rho_f, G, (double)L.kd.rho_open, x + ex_of(i), y + ey_of(i));
+        }
+        NodeMacro<C> s;
+        node_macro(k, f, g, rn, s);
+        phi[idx] = (double)(s.rho * s.uhx * s.uhx * s.uhx);
+        phi[n + idx] = (double)(s.rho * s.uhy * s.uhy * s.uhy);
     }
 }
 
@@ -276,6 +304,13 @@ struct AuxT {
         k_init<S, double><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, rho, ux, uy, T, static_cast<S*>(buf));
         return cudaGetLastError();
     }
+    // in the step's compute type: FP64 for FP64 storage, FP32 otherwise
+    static cudaError_t phi(const Launch& L, const void* buf, double* rho_scratch, double* out, cudaStream_t s) {
+        using C = typename std::conditional<sizeof(S) == 8, double, float>::type;
+        k_rho<S, C><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, static_cast<const S*>(buf), rho_scratch);
+        k_phi<S, C><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, static_cast<const S*>(buf), rho_scratch, out);
+        return cudaGetLastError();
+    }
     static cudaError_t set(const Launch& L, const double* f, const double* g, void* buf, cudaStream_t s) {
         k_set_pops<S><<<aux_blocks(L.geo), AUX_NT, 0, s>>>(L, f, g, static_cast<S*>(buf));
         return cudaGetLastError();
@@ -318,6 +353,10 @@ int moments_blocks(const Geometry& g) { return aux_blocks(g); }
 cudaError_t launch_init(int storage, const Launch& L, const double* rho, const double* ux, const double* uy,
                         const double* T, void* buf, cudaStream_t s, bool fast) {
     LBM_DISPATCH(storage, init(L, rho, ux, uy, T, buf, s, fast))
+}
+cudaError_t launch_cubic_phi(int storage, const Launch& L, const void* buf, double* rho_scratch, double* phi,
+                             cudaStream_t s) {
+    LBM_DISPATCH(storage, phi(L, buf, rho_scratch, phi, s))
 }
 cudaError_t launch_set_pops(int storage, const Launch& L, const double* f, const double* g, void* buf,
                             cudaStream_t s) {

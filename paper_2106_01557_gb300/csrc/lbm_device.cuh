@@ -233,10 +233,11 @@ __device__ __forceinline__ C p_BE(const K& k, C rho, C T) {
 }
 
 // Equilibria of f and g at one node, used by initialisation:
-// m^eq (SM Eq. S3a), F_m (S3b), n^eq (S4a), q_m (S4b).
+// m^eq (SM Eq. S3a), F_m (S3b), n^eq (S4a), q_m (S4b). cubic: the q_x, q_y
+// equilibria carry the cubic terms 3 rho u_x u_y^2, 3 rho u_y u_x^2.
 template <class C>
 __device__ __forceinline__ void equilibria(const KC<C>& k, const NodeMacro<C>& s, C meq[9], C Fm[9],
-                                           C neq[9], C qm[9]) {
+                                           C neq[9], C qm[9], bool cubic = false) {
     const C rho = s.rho, ux = s.uhx, uy = s.uhy;
     const C u2 = ux * ux + uy * uy;
     const C pbe = p_BE(k, rho, s.T);
@@ -251,6 +252,10 @@ __device__ __forceinline__ void equilibria(const KC<C>& k, const NodeMacro<C>& s
     meq[6] = -rho * uy;
     meq[7] = rho * (ux * ux - uy * uy);
     meq[8] = rho * ux * uy;
+    if (cubic) {
+        meq[4] += C(3) * rho * ux * uy * uy;
+        meq[6] += C(3) * rho * uy * ux * ux;
+    }
     const C Fx = s.Fhx, Fy = s.Fhy;
     const C FU = Fx * ux + Fy * uy;
     Fm[0] = C(0);
@@ -290,8 +295,12 @@ __device__ __forceinline__ void equilibria(const KC<C>& k, const NodeMacro<C>& s
 // and are not applied.
 // SH: on exit f and g hold the post-collision deviations from the rest
 // populations (the rest moments are taken off before the back-transform).
-template <bool SH = false, class C, class K>
-__device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMacro<C>& s) {
+// CUBIC: the cubic-term elimination: q_x, q_y equilibria with 3 rho u_x u_y^2,
+// 3 rho u_y u_x^2, and the source R7 = -c (d_x(rho u_x^3) - d_y(rho u_y^3))
+// in the p_xx row as dt (1 - s_p/2) R7 (R has no other component, and no
+// other row of S reads column p_xx).
+template <bool SH = false, bool CUBIC = false, class C, class K>
+__device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMacro<C>& s, C R7 = C(0)) {
     const C rho = s.rho, ux = s.uhx, uy = s.uhy;
     const C u2 = ux * ux + uy * uy;
     const C pbe = p_BE(k, rho, s.T);
@@ -315,8 +324,12 @@ __device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMa
     const C Q8 = k.qc * s.gx * s.gy;
     const C w1 = m[1] - meq1 + k.half_dt * Fm1 - Q1;
     const C w2 = m[2] - meq2 - k.half_dt * Fm1 + Q1;
-    const C w4 = m[4] + rho * ux - k.half_dt * Fx;
-    const C w6 = m[6] + rho * uy - k.half_dt * Fy;
+    C w4 = m[4] + rho * ux - k.half_dt * Fx;
+    C w6 = m[6] + rho * uy - k.half_dt * Fy;
+    if constexpr (CUBIC) {
+        w4 -= C(3) * rho * ux * uy * uy;
+        w6 -= C(3) * rho * uy * ux * ux;
+    }
     const C w7 = m[7] - meq7 + k.half_dt * Fm7 - Q7;
     const C w8 = m[8] - meq8 + k.half_dt * Fm8 - Q8;
     // S of SM Eq. S5a; omega_e = s_e/2 - 1, omega_p = s_p/2 - 1
@@ -333,6 +346,7 @@ __device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMa
     mb[5] = m[5] + k.dt * Fy;
     mb[6] = m[6] - k.dt * Fy - sqw6;
     mb[7] = m[7] + k.dt * Fm7 - Sw7;
+    if constexpr (CUBIC) mb[7] += k.dt * (R7 - C(0.5) * k.sp * R7);
     mb[8] = m[8] + k.dt * Fm8 - Sw8;
     // viscous-dissipation input of Eq. 12c: (m + m_bar)/2 - m^eq, columns e, pxx, pxy
     const C d1 = C(0.5) * (m[1] + mb[1]) - meq1;

@@ -259,6 +259,10 @@ static int derive(const lbm_config& c, lbm_params& p, Launch& L) {
     if ((c.open_sides & 12) && c.open_sides != 15)
         return fail(LBM_ERR_ARG, "open left and right sides come only with all four sides open");
     if (c.open_sides && !(c.Tr_open > 0)) return fail(LBM_ERR_ARG, "open sides need Tr_open > 0");
+    if (c.cubic != 0 && c.cubic != 1) return fail(LBM_ERR_ARG, "cubic must be 0 or 1");
+    if (c.cubic && (c.walls || c.open_sides))
+        return fail(LBM_ERR_ARG, "the cubic-term elimination is built for periodic boxes only");
+    L.cubic = c.cubic;
 
     // Eq. 17: a~ = A R^2 Tc^2 / pc, b~ = B R Tc / pc
     const double A = 0.4963880577294099, B = 0.1872945669467330;
@@ -678,8 +682,16 @@ int lbm_get_populations(lbm_handle* h, double* f, double* g) {
 }
 
 static cudaError_t step_once(lbm_handle* h, int from) {
+    const double* phi = nullptr;
+    if (h->L.cubic) {
+        // rho u^3 of the entering state, for the cubic-term source
+        const size_t n = (size_t)h->cfg.nx * h->cfg.ny;
+        cudaError_t e = launch_cubic_phi(h->storage, h->L, h->buf[from], h->scratch, h->scratch + n, h->stream);
+        if (e != cudaSuccess) return e;
+        phi = h->scratch + n;
+    }
     return launch_step(h->storage, h->L, &h->tmf[from], &h->tmg[from], h->buf[1 - from], h->partials, h->stats,
-                       h->counter, h->status, h->stream);
+                       h->counter, h->status, h->stream, phi);
 }
 
 static int build_graph(lbm_handle* h) {
@@ -791,7 +803,8 @@ static uint64_t config_hash(const lbm_config& c) {
             h *= 1099511628211ull;
         }
     };
-    const int32_t ints[] = {c.nx, c.ny, c.precision, c.walls, c.hot_x0, c.hot_len, c.rounding, c.open_sides};
+    const int32_t ints[] = {c.nx, c.ny, c.precision, c.walls, c.hot_x0, c.hot_len, c.rounding, c.open_sides,
+                            c.cubic};
     const double dbl[] = {c.a_t, c.b_t, c.R, c.K_EOS, c.K_INT, c.Tr0, c.varpi, c.gamma1, c.gamma2,
                           c.s_p, c.s_eps, c.sig_e, c.sig_eps, c.sig_p, c.tau_j_v, c.tau_j_l, c.c_v,
                           c.C_ref, c.accel_x, c.accel_y, c.Tr_bottom, c.Tr_top, c.Tr_hot, c.rho_ref,
@@ -961,6 +974,7 @@ int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out) {
             return fail(LBM_ERR_ARG, "batch cases must be periodic (walls = 0, no open sides)");
         }
         if (cfgs[i].rounding != cfgs[0].rounding) { delete b; return fail(LBM_ERR_ARG, "all batch cases need one rounding"); }
+        if (cfgs[i].cubic) { delete b; return fail(LBM_ERR_ARG, "the cubic-term elimination is built for single cases"); }
         std::memset(&b->L[i], 0, sizeof(Launch));
         int rc = derive(cfgs[i], b->prm[i], b->L[i]);
         if (rc) { delete b; return rc; }

@@ -70,6 +70,7 @@ struct Launch {
     // bound in ns on each wait of the step kernel for a tile's copies; 0: the
     // copies must already have landed when the tile's turn comes (no waiting)
     unsigned long long tile_wait_ns;
+    int cubic;  // eliminate the cubic velocity terms (periodic single cases)
 };
 
 // default tile-wait bound: 2 s
@@ -79,9 +80,15 @@ constexpr unsigned long long TILE_WAIT_NS_DEFAULT = 2000000000ull;
 enum { S_F64 = 0, S_F32 = 1, S_F16 = 2, S_BF16 = 3 };
 
 // Host-side launchers (lbm_kernels.cu). All return cudaError_t of the launch.
+// phi: with L.cubic, [2][ny][nx] rho u_x^3 and rho u_y^3 (u over c) of the
+// state entering the step (launch_cubic_phi); otherwise unused
 cudaError_t launch_step(int storage, const Launch& L, const CUtensorMap* tmf, const CUtensorMap* tmg,
                         void* out, double* partials, double* stats, unsigned* counter, int* status,
-                        cudaStream_t s);
+                        cudaStream_t s, const double* phi = nullptr);
+// rho u_x^3 and rho u_y^3 of every node of a state (for the cubic-term
+// elimination): the density field into rho_scratch, then phi [2][ny][nx]
+cudaError_t launch_cubic_phi(int storage, const Launch& L, const void* buf, double* rho_scratch, double* phi,
+                             cudaStream_t s);
 void step_tile(int storage, int* bx, int* by, int* hx);
 int step_blocks(int storage, const Geometry& g);
 size_t step_smem_bytes(int storage);

@@ -175,13 +175,15 @@ __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& 
     }
 }
 
-// OPEN: the case has open sides (a separate instantiation, so that the
-// common path carries none of their code)
-template <class S, class C, bool OPEN>
+// OPEN: the case has open sides; CUBIC: the cubic-term elimination, with
+// phi = rho u_x^3, rho u_y^3 of the entering state (separate instantiations,
+// so that the common path carries none of their code)
+template <class S, class C, bool OPEN, bool CUBIC>
 __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     k_step(const __grid_constant__ CUtensorMap tmf, const __grid_constant__ CUtensorMap tmg,
            S* __restrict__ out, const __grid_constant__ Launch L, double* __restrict__ partials,
-           double* __restrict__ stats, unsigned* __restrict__ counter, int* __restrict__ status) {
+           double* __restrict__ stats, unsigned* __restrict__ counter, int* __restrict__ status,
+           const double* __restrict__ phi) {
     using SM = Smem<S, C>;
     constexpr int BX = SM::BX, BY = SM::BY, HX = SM::HX, WX = SM::WX;
     constexpr int FR = SM::FR, GR = SM::GR, RX = SM::RX, RY = SM::RY;
@@ -311,7 +313,17 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
                 acc.u2max = u2 > acc.u2max ? u2 : acc.u2max;
                 if (!(rho > C(0) && rho < C(1e30) && u2 < C(1e30))) acc.bad += C(1);  // also catches NaN
             }
-            collide<Store<S, C>::SHIFTED>(k, f, g, s);
+            C R7 = C(0);
+            if constexpr (CUBIC) {
+                // -c (d_x(rho u_x^3) - d_y(rho u_y^3)), periodic central differences
+                const long long n = (long long)G.nx * G.ny;
+                const int xm = x == 0 ? G.nx - 1 : x - 1, xp = x == G.nx - 1 ? 0 : x + 1;
+                const int ym = y == 0 ? G.ny - 1 : y - 1, yp = y == G.ny - 1 ? 0 : y + 1;
+                const double dpx = 0.5 * (__ldg(phi + (long long)y * G.nx + xp) - __ldg(phi + (long long)y * G.nx + xm));
+                const double dpy = 0.5 * (__ldg(phi + n + (long long)yp * G.nx + x) - __ldg(phi + n + (long long)ym * G.nx + x));
+                R7 = -k.c * ((C)dpx - (C)dpy);
+            }
+            collide<Store<S, C>::SHIFTED, CUBIC>(k, f, g, s, R7);
             store_node<S, C, OPEN>(out, G, k, x, y, f, g, s, sr, fmix32((uint32_t)(y * G.nx + x) ^ step_key));
         }
         if (NS == 1) {
@@ -395,17 +407,21 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
 
 template <class S, class C>
 cudaError_t launch_t(const Launch& L, const CUtensorMap* tmf, const CUtensorMap* tmg, void* out,
-                     double* partials, double* stats, unsigned* counter, int* status, cudaStream_t s) {
+                     double* partials, double* stats, unsigned* counter, int* status, cudaStream_t s,
+                     const double* phi) {
     using SM = Smem<S, C>;
     const int ntiles = ((L.geo.nx + SM::BX - 1) / SM::BX) * ((L.geo.ny + SM::BY - 1) / SM::BY);
     const int slots = Tile<S>::CPS * L.geo.sms;
     const int grid = ntiles < slots ? ntiles : slots;
     if (L.geo.open)
-        k_step<S, C, true><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats,
-                                                                counter, status);
+        k_step<S, C, true, false><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials,
+                                                                       stats, counter, status, phi);
+    else if (L.cubic)
+        k_step<S, C, false, true><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials,
+                                                                       stats, counter, status, phi);
     else
-        k_step<S, C, false><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials, stats,
-                                                                 counter, status);
+        k_step<S, C, false, false><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials,
+                                                                        stats, counter, status, phi);
     return cudaGetLastError();
 }
 
@@ -438,9 +454,11 @@ size_t step_smem_bytes(int storage) {
 
 template <class S, class C>
 cudaError_t attr_t(int smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_step<S, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_step<S, C, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_step<S, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_step<S, C, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_step<S, C, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t prepare_step(int storage) {
@@ -455,13 +473,15 @@ cudaError_t prepare_step(int storage) {
 }
 
 cudaError_t launch_step(int storage, const Launch& L, const CUtensorMap* tmf, const CUtensorMap* tmg, void* out,
-                        double* partials, double* stats, unsigned* counter, int* status, cudaStream_t s) {
+                        double* partials, double* stats, unsigned* counter, int* status, cudaStream_t s,
+                        const double* phi) {
+    if (L.cubic && !phi) return cudaErrorInvalidValue;
     switch (storage) {
-        case S_F64: return launch_t<double, double>(L, tmf, tmg, out, partials, stats, counter, status, s);
-        case S_F32: return launch_t<float, float>(L, tmf, tmg, out, partials, stats, counter, status, s);
-        case S_F16: return launch_t<__half, float>(L, tmf, tmg, out, partials, stats, counter, status, s);
+        case S_F64: return launch_t<double, double>(L, tmf, tmg, out, partials, stats, counter, status, s, phi);
+        case S_F32: return launch_t<float, float>(L, tmf, tmg, out, partials, stats, counter, status, s, phi);
+        case S_F16: return launch_t<__half, float>(L, tmf, tmg, out, partials, stats, counter, status, s, phi);
         case S_BF16:
-            return launch_t<__nv_bfloat16, float>(L, tmf, tmg, out, partials, stats, counter, status, s);
+            return launch_t<__nv_bfloat16, float>(L, tmf, tmg, out, partials, stats, counter, status, s, phi);
     }
     return cudaErrorInvalidValue;
 }

@@ -45,6 +45,7 @@ class LbmConfig(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("device", ctypes.c_int32), ("rounding", ctypes.c_int32),
         ("open_sides", ctypes.c_int32), ("Tr_open", ctypes.c_double), ("rho_open", ctypes.c_double),
+        ("cubic", ctypes.c_int32),
     ]
 
 

@@ -7,7 +7,7 @@ from paper_2106_01557_gb300 import inputs
 
 OPTS = ("walls", "accel_x", "accel_y", "Tr_bottom", "Tr_top", "Tr_hot", "hot_x0", "hot_len", "Tr0",
         "varpi", "gamma1", "gamma2", "s_p", "s_eps", "sig_e", "sig_eps", "sig_p", "tau_j_v", "tau_j_l",
-        "c_v", "C_ref", "open_sides", "Tr_open")
+        "c_v", "C_ref", "open_sides", "Tr_open", "cubic")
 
 
 def oracle_case(nx, ny, **kw):

@@ -53,9 +53,10 @@ def test_struct_layout_matches_header():
     #include <stddef.h>
     #include "lbm.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_config), offsetof(lbm_config, Tr_hot),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_config), offsetof(lbm_config, Tr_hot),
              offsetof(lbm_config, rho_ref), offsetof(lbm_config, stream), sizeof(lbm_params),
-             offsetof(lbm_params, sq), offsetof(lbm_config, open_sides), offsetof(lbm_config, rho_open));
+             offsetof(lbm_params, sq), offsetof(lbm_config, open_sides), offsetof(lbm_config, rho_open),
+             offsetof(lbm_config, cubic));
       return 0;
     }'''
     tmp = os.path.join(ROOT, "paper_2106_01557_gb300", "_build")
@@ -67,7 +68,7 @@ def test_struct_layout_matches_header():
     got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     C, P = lbm.LbmConfig, lbm.LbmParams
     assert got == [ctypes.sizeof(C), C.Tr_hot.offset, C.rho_ref.offset, C.stream.offset,
-                   ctypes.sizeof(P), P.sq.offset, C.open_sides.offset, C.rho_open.offset]
+                   ctypes.sizeof(P), P.sq.offset, C.open_sides.offset, C.rho_open.offset, C.cubic.offset]
 
 
 def test_default_config_and_argument_errors_without_gpu(lib):
