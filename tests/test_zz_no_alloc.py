@@ -11,14 +11,23 @@ from gpu_common import oracle_case, slab_fields
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_record_matches_handle_record(gpu_lib):
+# a periodic box, bounce-back walls (the pair force's density beyond a wall
+# is the adjacent node's) with a body force and a hot segment, and an open
+# bottom (the open state's density beyond it)
+CASES = {"periodic": {}, "walls": dict(walls=1, accel_y=-1e-4, Tr_bottom=0.8, Tr_hot=0.95, hot_x0=90, hot_len=20),
+         "open_bottom": dict(walls=1, open_sides=1, Tr_open=0.85)}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_noalloc_record_matches_handle_record(gpu_lib, case):
     import torch
     from paper_2106_01557_gb300 import lbm
 
     nx, ny = 100, 37
-    o = oracle_case(nx, ny)
+    kw = CASES[case]
+    o = oracle_case(nx, ny, **kw)
     fields = slab_fields(o, seed=31)
-    cfg = lbm.default_config(nx, ny, precision="f64")
+    cfg = lbm.default_config(nx, ny, precision="f64", **kw)
     h = lbm.Lattice(cfg)
     h.set_fields(*fields)
     out = torch.zeros(8, dtype=torch.float64, device="cuda")
