@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(T::NT, 1)
                     sg[i] = Store<S, C>::cvt(g[i]);
                 }
             }
-            const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
+            const bool interior = x >= GHOST_COLS && x < G.nx - GHOST_COLS && y >= 2 && y < G.ny - 2;
             if (interior) {
                 S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
 #pragma unroll

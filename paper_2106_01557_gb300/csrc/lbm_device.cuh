@@ -410,7 +410,6 @@ __device__ __forceinline__ void g_rest_wall(const KC<C>& k, C rho_w, C T_w, C& g
 template <class S, bool XOPEN = true>
 __device__ __forceinline__ void put(S* __restrict__ out, const Geometry& G, int p, int x, int y, S v) {
     S* base = out + (long long)p * G.plane;
-    const int HX = G.HX;
     int rows[2];
     int nr = 1;
     rows[0] = y;
@@ -424,8 +423,8 @@ __device__ __forceinline__ void put(S* __restrict__ out, const Geometry& G, int 
         S* row = base + (long long)(rows[r] + 2) * G.pitch + G.PX;
         row[x] = v;
         if (!(XOPEN && (G.open & 12))) {
-            if (x < HX) row[x + G.nx] = v;
-            if (x >= G.nx - HX) row[x - G.nx] = v;
+            if (x < GHOST_COLS) row[x + G.nx] = v;
+            if (x >= G.nx - GHOST_COLS) row[x - G.nx] = v;
         }
     }
 }

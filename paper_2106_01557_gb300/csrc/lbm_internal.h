@@ -43,6 +43,12 @@ struct KC {
     C mrest[3], nrest[3];  // moments 0-2 of the f and g rest populations (the others vanish)
 };
 
+// Ghost columns that hold periodic copies: a pull reads one column beyond
+// the lattice and the density of the step's one-node ring pulls from a
+// second; the other columns of the HX-wide ghost block exist only to keep
+// the tile copies 16-byte aligned and are never read.
+constexpr int GHOST_COLS = 2;
+
 struct Geometry {
     int nx, ny, walls, HX;  // HX: ghost columns on each side (16 bytes)
     int PX;          // elements before column x = 0 of a row (128 bytes), so

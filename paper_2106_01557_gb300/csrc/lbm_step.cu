@@ -124,8 +124,7 @@ __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& 
     const C rho = s.rho;
     const C* rest = k.rest;
     constexpr bool SH = Store<S, C>::SHIFTED;
-    const int HX = G.HX;
-    const bool interior = x >= HX && x < G.nx - HX && y >= 2 && y < G.ny - 2;
+    const bool interior = x >= GHOST_COLS && x < G.nx - GHOST_COLS && y >= 2 && y < G.ny - 2;
     // the values as stored: 16-bit storage rounds stochastically (sr, from
     // the node's seed), else to nearest
     S sf[9], sg[9];
