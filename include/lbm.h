@@ -301,6 +301,11 @@ int lbm_batch_get_populations(lbm_batch* b, int32_t i, double* f, double* g);
 int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[8]);
 /* Steps the batch has executed (host count; includes autotuner trials). */
 int64_t lbm_batch_step_count(const lbm_batch* b);
+/* As lbm_set_tile_wait, for the batch's step kernel: the bound on each wait
+ * for an item's copies (0: no waiting); a wait that runs out is reported as
+ * LBM_ERR_TIMEOUT by the next synchronising call, and the cases' states are
+ * undefined until set again. ns < 0: LBM_ERR_ARG. */
+int lbm_batch_set_tile_wait(lbm_batch* b, int64_t ns);
 /* Autotuner: times every candidate (tile shape x work-list order) for
  * trial_steps steps on the current state and keeps the fastest; the trial
  * steps are real steps of every case (the state advances). choice[0] =

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(T::NT, 1)
     k_batch_step(const BatchItem* __restrict__ items, int nitems, const BatchCase* __restrict__ cases,
                  const KC<float>* __restrict__ kcs, const CUtensorMap* __restrict__ maps, int from,
                  S* __restrict__ arena_out, float* __restrict__ partials, int* __restrict__ status,
-                 double* __restrict__ steps, unsigned* __restrict__ done, int rounding) {
+                 double* __restrict__ steps, unsigned* __restrict__ done, int rounding,
+                 unsigned long long tile_wait_ns) {
     using C = float;
     constexpr int BX = T::BX, BY = T::BY, HX = T::HX, WX = T::WX, NT = T::NT;
     constexpr int FR = T::FR, GR = T::GR, RX = T::RX, RY = T::RY;
@@ -118,9 +119,13 @@ __global__ void __launch_bounds__(T::NT, 1)
         bool timed_out = false;
         {
             const uint32_t parity = (it >> 1) & 1;
-            const uint64_t t0 = globaltimer_ns();
-            while (!mbar_try_wait(&bar[stage], parity)) {
-                if (globaltimer_ns() - t0 > WAIT_NS) { timed_out = true; break; }
+            if (tile_wait_ns == 0) {
+                timed_out = !mbar_test_wait(&bar[stage], parity);  // no waiting at all
+            } else {
+                const uint64_t t0 = globaltimer_ns();
+                while (!mbar_try_wait(&bar[stage], parity)) {
+                    if (globaltimer_ns() - t0 > tile_wait_ns) { timed_out = true; break; }
+                }
             }
         }
         const S* sf = reinterpret_cast<const S*>(smem + stage * T::STAGE);
@@ -234,7 +239,12 @@ __global__ void __launch_bounds__(T::NT, 1)
     if (ok && it > 0) flush(item_of(it - 1), (it - 1) & 1);
     if (!ok && tid == 0) {
         atomicOr(status, ST_TIMEOUT);
-        for (int j = it; j <= it + 1; ++j) {
+        // the copies issued and not yet consumed: items it and, at it = 0, 1
+        // (item it + 1 is issued only after iteration it's barrier); each
+        // drained within the full default bound
+        const int jend = it == 0 ? 1 : it;
+        for (int j = it; j <= jend; ++j) {
+            if (item_of(j) >= nitems) break;
             const uint64_t t0 = globaltimer_ns();
             while (!mbar_try_wait(&bar[j & 1], (j >> 1) & 1) && globaltimer_ns() - t0 < WAIT_NS) {}
         }
@@ -285,7 +295,7 @@ cudaError_t launch_bt(const BatchLaunch& B, int from, void* out, cudaStream_t s)
     const int grid = B.nitems < B.sms ? B.nitems : B.sms;
     k_batch_step<S, T><<<grid, T::NT, T::BYTES, s>>>(B.items, B.nitems, B.cases, B.kcs, B.maps, from,
                                                      static_cast<S*>(out), B.partials, B.status, B.steps,
-                                                     B.done, B.rounding);
+                                                     B.done, B.rounding, B.tile_wait_ns);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ struct BatchLaunch {
     double* steps;            // steps the batch has executed (device; keys stochastic rounding)
     unsigned* done;           // blocks of the current launch that have finished
     int rounding;             // 16-bit storage: 0 nearest, 1 stochastic
+    unsigned long long tile_wait_ns;  // bound on each wait for an item's copies; 0: no waiting
 };
 
 void batch_tile(int storage, int variant, int* bx, int* by);

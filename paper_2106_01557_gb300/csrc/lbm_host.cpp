@@ -908,6 +908,7 @@ struct lbm_batch {
     bool own_stream = false;
     int shape = 0, order = 1;
     int sms = 0;
+    unsigned long long tile_wait_ns = TILE_WAIT_NS_DEFAULT;
     cudaGraphExec_t graph = nullptr;
     int64_t steps = 0;
     static constexpr int GRAPH_STEPS = 20;
@@ -926,6 +927,7 @@ static BatchLaunch batch_launch(lbm_batch* b) {
     B.steps = b->d_steps;
     B.done = b->d_done;
     B.rounding = b->cfg[0].rounding;
+    B.tile_wait_ns = b->tile_wait_ns;
     return B;
 }
 
@@ -1227,6 +1229,19 @@ int lbm_batch_step_stats(lbm_batch* b, int32_t i, double out[8]) {
 }
 
 int64_t lbm_batch_step_count(const lbm_batch* b) { return b ? b->steps : -1; }
+
+int lbm_batch_set_tile_wait(lbm_batch* b, int64_t ns) {
+    if (!b) return fail(LBM_ERR_ARG, "null batch");
+    if (ns < 0) return fail(LBM_ERR_ARG, "negative wait bound");
+    if (b->tile_wait_ns == (unsigned long long)ns) return LBM_OK;
+    CK(cudaStreamSynchronize(b->stream));
+    if (b->graph) {  // the captured graph holds the launch parameters
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->tile_wait_ns = (unsigned long long)ns;
+    return LBM_OK;
+}
 
 int lbm_batch_select(lbm_batch* b, int32_t shape, int32_t order) {
     if (!b || shape < 0 || shape > 1 || order < 0 || order > 2) return fail(LBM_ERR_ARG, "bad candidate");

@@ -95,6 +95,7 @@ SIGNATURES = {
     "lbm_surface_tension": ([ctypes.POINTER(LbmConfig), ctypes.c_double, _DP], ctypes.c_int),
     "lbm_batch_nodes": ([_H], ctypes.c_int64),
     "lbm_batch_step_count": ([_H], ctypes.c_int64),
+    "lbm_batch_set_tile_wait": ([_H, ctypes.c_int64], ctypes.c_int),
     "lbm_batch_bytes_per_step": ([_H], ctypes.c_double),
     "lbm_batch_destroy": ([_H], ctypes.c_int),
     "lbm_surrogate_create": ([ctypes.c_void_p, ctypes.POINTER(_H)], ctypes.c_int),
@@ -381,6 +382,10 @@ class Batch:
     @property
     def steps(self) -> int:
         return int(self.lib.lbm_batch_step_count(self.h))
+
+    def set_tile_wait(self, ns: int):
+        """Bound (ns) on each wait of the batch kernel for an item's copies; 0: no waiting."""
+        _check(self.lib.lbm_batch_set_tile_wait(self.h, int(ns)))
 
     def autotune(self, trial_steps=10):
         choice = (ctypes.c_int32 * 2)()

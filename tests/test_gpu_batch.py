@@ -141,3 +141,34 @@ def test_batch_fp16_storage_matches_oracle(gpu_lib):
         print(f"batch f16s case {i}: rho {e_rho:.3e} T {e_T:.3e} u/c {e_u:.3e}")
         assert e_rho < 5e-3 and e_T < 8e-3 and e_u < 5e-4, (i, e_rho, e_T, e_u)
     assert b.steps == 100 and b.step_stats(0)[7] == 100
+
+
+def test_batch_tile_wait_that_runs_out_is_reported(gpu_lib):
+    # as for a single case: with no time to wait, the first item of every
+    # block times out, the launch ends after the copies in flight have
+    # landed, LBM_ERR_TIMEOUT is reported, and the batch then steps as a
+    # fresh one does, bit for bit
+    from paper_2106_01557_gb300 import lbm
+    cases = _cases()
+    cfgs = [lbm.default_config(nx, ny, precision="f32", Tr0=tr) for nx, ny, tr, _ in cases]
+    fields = [_fields(nx, ny, lbm.Lattice(c).params(), R, 70 + i) for i, (c, (nx, ny, tr, R)) in enumerate(zip(cfgs, cases))]
+    a = lbm.Batch(cfgs)
+    for i, fl in enumerate(fields):
+        a.set_fields(i, *fl)
+    a.set_tile_wait(0)
+    a.step(2)
+    with pytest.raises(lbm.LbmError) as e:
+        a.synchronize()
+    assert e.value.code == -5
+    a.set_tile_wait(2_000_000_000)
+    for i, fl in enumerate(fields):
+        a.set_fields(i, *fl)
+    a.step(25)
+    b = lbm.Batch(cfgs)
+    for i, fl in enumerate(fields):
+        b.set_fields(i, *fl)
+    b.step(25)
+    for i in range(len(cases)):
+        fa, ga = a.get_populations(i)
+        fb, gb = b.get_populations(i)
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), i
