@@ -125,8 +125,8 @@ METRIC = "MLUPS of the fused f+g step (FP32 plain)"
 # DRAM bytes (read + write) of one k_step launch on this workload, from one
 # ncu capture (profiles/k_step_f32_4096x1024_full.md), valid only for the
 # kernel sources it was taken on: any change to them makes it null.
-STEP_TRAFFIC = {"bytes_per_launch": 309387264 + 255035648,
-                "sources_sha256": "b485551e2a88545a6c8ed52728d22b68aef39e5d68fabd73a80eb5ad44fabc40"}
+STEP_TRAFFIC = {"bytes_per_launch": (309389056 + 255410688 + 308886784 + 253242368) // 2,
+                "sources_sha256": "995437ad3118a9b843fc16ccf2439e9e82b0de3894e4af3caaf2b640347f7e45"}
 STEP_SOURCES = ["lbm_step.cu", "lbm_device.cuh", "lbm_internal.h", "lbm_ptx.cuh"]
 
 
