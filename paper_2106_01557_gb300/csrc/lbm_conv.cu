@@ -8,7 +8,8 @@
 //                output. Also serves the input gradient (flipped weights).
 //   k_wgrad      weight gradient: per (tap, 16 output channels) a GEMM over
 //                pixels, warps splitting the pixels; each block writes its
-//                partial sums, which k_wgrad_sum adds in block order.
+//                partial sums, which k_wgrad_sum adds in block order (the
+//                64 -> 64 layers have a tcgen05 version in lbm_conv_tc.cu).
 //   k_bgrad      bias gradient (per-block partials, summed in block order).
 // No reduction uses atomics: the order of every sum is fixed, so training
 // is bit-for-bit reproducible.
@@ -656,6 +657,12 @@ cudaError_t launch_wgrad(int cin, int cout, const __nv_bfloat16* in, const __nv_
     if (cin == 64 && cout == 64) return wgrad_t<64, 64>(in, dout, N, H, W, in_relu, dw, part, s, sms);
     if (cin == 64 && cout == 16) return wgrad_t<64, 16>(in, dout, N, H, W, in_relu, dw, part, s, sms);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_wgrad_sum(const float* part, int nblk, int cc, float* dw, cudaStream_t s) {
+    if (nblk < 1 || cc < 1) return cudaErrorInvalidValue;
+    k_wgrad_sum<<<(9 * cc + 255) / 256, 256, 0, s>>>(part, nblk, cc, dw);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, float* part, cudaStream_t s) {

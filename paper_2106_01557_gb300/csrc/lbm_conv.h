@@ -39,6 +39,14 @@ cudaError_t launch_conv_tc(int cin, int cout, const ConvArgs& a, cudaStream_t s,
 size_t grad_scratch_floats(int sms);
 cudaError_t launch_wgrad(int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W,
                          int in_relu, float* dw, float* part, cudaStream_t s, int sms);
+// The 64 -> 64 weight gradient on tcgen05 MMAs with tensor-memory
+// accumulators (lbm_conv_tc.cu; the same partial layout and block order);
+// bit 0 of *status as for launch_conv_tc.
+cudaError_t launch_wgrad_tc(int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W,
+                            int in_relu, float* dw, float* part, cudaStream_t s, int sms, int* status);
+// dw[9][cc] += the sum over blocks 0 .. nblk - 1 (in that order) of the
+// partials part[nblk][3 dy][3 dx][cc]
+cudaError_t launch_wgrad_sum(const float* part, int nblk, int cc, float* dw, cudaStream_t s);
 cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* db, float* part, cudaStream_t s);
 // blocks per image of the mass layer's sums: part holds 2 MASS_BLOCKS N doubles
 constexpr int MASS_BLOCKS = 256;

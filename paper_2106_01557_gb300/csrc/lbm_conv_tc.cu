@@ -535,6 +535,199 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient of a 64 -> 64 convolution on the tensor cores:
+// dW[tap (dy, dx)][co][ci] = sum over pixels p of dOut[p][co] In[p + (dy, dx)][ci]
+// (In after the ReLU the forward applied). Block (x, y): filter row dy =
+// y - 1, a share x of the (image, row, 128-pixel strip) chunks. Per chunk
+// the dOut row segment [128 pixels][64 co] and the input row segment
+// [130 pixels][64 ci] (one pixel of halo each side, periodic) land by
+// cp.async in one of two stages, both as 128-byte rows per pixel with the
+// tensor core's 128-byte swizzle. The contraction runs over pixels, so both
+// operands are MN-major (the pixel index is the K index of their rows):
+//   D1[(dx, ci)][co], dx = -1, 0:  A = the input rows from pixel k (dx = -1)
+//       and the same rows one pixel on (dx = 0) as the two 64-row halves
+//       of M = 128 (leading byte offset 128: the second half starts one
+//       pixel row later), B = the dOut rows (N = 64);
+//   D2[(dx, ci)][co], dx = 0, +1: the same from one pixel on (its first
+//       half repeats dx = 0 and is not read).
+// One K step is 16 pixels (2048 bytes); 8 steps and 2 MMAs per chunk. The
+// accumulators live in tensor memory (128 lanes x 128 columns) for all of
+// the block's chunks; at the end they are read with tcgen05.ld and written
+// as the block's partial sums [block][dy][dx][co][ci], which
+// k_wgrad_sum adds in block order. The MMAs of chunk i are committed to
+// the mbarrier of its stage, which is refilled only after they completed.
+constexpr int WG_THREADS = 256;
+constexpr int WG_PIX = 128;
+constexpr int WG_D_BYTES = WG_PIX * 128;                        // 16 KB
+constexpr int WG_X_BYTES = ((WG_PIX + 2) * 128 + 1023) / 1024 * 1024;  // 17 KB
+constexpr int WG_STAGE = WG_D_BYTES + WG_X_BYTES;
+constexpr int WG_BYTES = 2 * WG_STAGE + 1024;
+
+__device__ __forceinline__ void wg_cp16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// MN-major operand in 128-byte swizzled rows (one row per K index): atoms of
+// 8 K rows (SBO = 1024 bytes); lbo: byte offset between the 64-wide halves
+// along M or N; swizzle mode 2 (bits 61-63)
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t lbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__global__ void __launch_bounds__(WG_THREADS, 1)
+    k_wgrad_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dout, int N, int H, int W,
+               int in_relu, float* __restrict__ part, int* __restrict__ status) {
+    constexpr int C = 64;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const uint32_t sbase = smem_u32(smem);
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int dy = (int)blockIdx.y - 1;
+    const int tiles_x = (W + WG_PIX - 1) / WG_PIX;
+    const long long nchunks = (long long)N * H * tiles_x;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(128u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    // D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both
+    // MN-major (bits 15, 16 = 1), N = 64 (N >> 3 at bits 17-22), M = 128
+    // (M >> 4 at bits 24-28)
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((64u >> 3) << 17) |
+                           ((128u >> 4) << 24);
+
+    // chunk ch into stage st: dOut row segment and halo'd input row segment
+    auto load = [&](long long ch, int st) {
+        if (ch < nchunks) {
+            const int x0 = (int)(ch % tiles_x) * WG_PIX;
+            const long long ry = ch / tiles_x;  // n * H + y
+            const int y = (int)(ry % H), n = (int)(ry / H);
+            int yy = y + dy;
+            yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+            const uint32_t sd = sbase + st * WG_STAGE, sx = sd + WG_D_BYTES;
+            const __nv_bfloat16* drow = dout + (size_t)ry * W * C;
+            const __nv_bfloat16* xrow = in + ((size_t)n * H + yy) * W * C;
+            for (int e = tid; e < WG_PIX * 8; e += WG_THREADS) {
+                const int px = e / 8, kg = e % 8;
+                const int x = x0 + px;
+                wg_cp16(sd + px * 128 + ((kg ^ (px & 7)) * 16), drow + (size_t)(x < W ? x : 0) * C + kg * 8,
+                        x < W ? 16 : 0);  // pixels past the image contribute nothing
+            }
+            for (int e = tid; e < (WG_PIX + 2) * 8; e += WG_THREADS) {
+                const int px = e / 8, kg = e % 8;
+                int x = x0 - 1 + px;
+                x = x < 0 ? x + W : (x >= W ? x % W : x);
+                wg_cp16(sx + px * 128 + ((kg ^ (px & 7)) * 16), xrow + (size_t)x * C + kg * 8, 16);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto relu_stage = [&](int st) {
+        unsigned char* sx = smem + st * WG_STAGE + WG_D_BYTES;
+        for (int e = tid; e < (WG_PIX + 2) * 8; e += WG_THREADS) {
+            uint4* v = reinterpret_cast<uint4*>(sx + e * 16);
+            *v = relu8(*v);
+        }
+    };
+
+    // thread 0 waits for the tensor core, the block learns the outcome at a
+    // barrier (every thread takes the same branch)
+    bool ok = true;
+    uint32_t pending = 0;  // bit b: a commit to bar[b] not yet waited for
+    int it = 0;
+    long long ch = blockIdx.x;
+    load(ch, 0);
+    for (; ch < nchunks; ch += gridDim.x, ++it) {
+        const int st = it & 1;
+        // the other stage is refilled once the MMAs of the chunk before have read it
+        if (it >= 1) {
+            const int late = tid == 0 && !bar_wait(&bar[st ^ 1], (uint32_t)((it - 1) >> 1) & 1u);
+            if (__syncthreads_or(late)) { ok = false; break; }
+            pending &= ~(1u << (st ^ 1));
+        }
+        load(ch + gridDim.x, st ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        if (in_relu) {
+            __syncthreads();  // every thread's copies have landed
+            relu_stage(st);
+        }
+        fence_proxy_async();  // the copies and the ReLU, for the tensor core's reads
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t sd = sbase + st * WG_STAGE, sx = sd + WG_D_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < WG_PIX / 16; ++kk) {
+                const uint64_t b = sdesc_mn_sw128(sd + kk * 16 * 128, 16);
+                const uint64_t a1 = sdesc_mn_sw128(sx + kk * 16 * 128, 128);
+                const uint64_t a2 = sdesc_mn_sw128(sx + (kk * 16 + 1) * 128, 128);
+                const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                tc_mma(tmem, a1, b, idesc, acc);
+                tc_mma(tmem + 64, a2, b, idesc, acc);
+            }
+            tc_commit(&bar[st]);
+        }
+        pending |= 1u << st;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // the last commits: every MMA done before the accumulators are read
+    int late = 0;
+    if (tid == 0)
+        for (uint32_t b = 0; b < 2; ++b)
+            if (pending & (1u << b)) {
+                const int last = (b == (uint32_t)((it - 1) & 1)) ? it - 1 : it - 2;
+                if (!bar_wait(&bar[b], (uint32_t)(last >> 1) & 1u)) late = 1;
+            }
+    if (__syncthreads_or(late)) ok = false;
+    tc_fence_after();
+    float* pb = part + ((size_t)blockIdx.x * 3 + blockIdx.y) * 3 * C * C;
+    if (warp < 4) {
+        // lane m = 32 warp + lane of D: (dx, ci) = (m / 64, m % 64) for D1 (dx = -1, 0)
+        // and (m / 64 + 1, m % 64) for D2 (dx = 0, +1: its upper half only)
+        const int m = 32 * warp + lane;
+        const int ci = m % 64;
+        const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && m < 64) continue;
+            const int dxi = m / 64 + h;  // 0, 1, 2 for dx = -1, 0, +1
+#pragma unroll
+            for (int c16 = 0; c16 < 4; ++c16) {
+                float v[16];
+                if (it > 0 && ok) tc_ld<16>(tl + h * 64 + c16 * 16, v);
+                else
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pb[((size_t)dxi * C + c16 * 16 + j) * C + ci] = v[j];
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicOr(status, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+    }
+}
+
 template <int CIN, int COUT>
 cudaError_t conv_tc_t(const ConvArgs& a, cudaStream_t s, int sms, int* status) {
     using Cf = TcCfg<CIN, COUT>;
@@ -552,6 +745,24 @@ cudaError_t conv_tc_t(const ConvArgs& a, cudaStream_t s, int sms, int* status) {
 }
 
 }  // namespace
+
+cudaError_t launch_wgrad_tc(int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, int H, int W,
+                            int in_relu, float* dw, float* part, cudaStream_t s, int sms, int* status) {
+    if (cin != 64 || cout != 64 || N < 1 || H < 1 || W < 16 || W % 16 != 0 || !status || sms < 1)
+        return cudaErrorInvalidValue;
+    static bool set = false;
+    if (!set) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_BYTES);
+        if (e != cudaSuccess) return e;
+        set = true;
+    }
+    const long long chunks = (long long)N * H * ((W + WG_PIX - 1) / WG_PIX);
+    long long gx = (2 * sms + 2) / 3;  // with the three filter rows: about two blocks per SM
+    if (gx > chunks) gx = chunks;
+    k_wgrad_tc<<<dim3((unsigned)gx, 3), WG_THREADS, WG_BYTES, s>>>(in, dout, N, H, W, in_relu, part, status);
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : launch_wgrad_sum(part, (int)gx, cout * cin, dw, s);
+}
 
 cudaError_t launch_conv_tc(int cin, int cout, const ConvArgs& a, cudaStream_t s, int sms, int* status) {
     if (a.N < 1 || a.H < 1 || a.W < 16 || a.W % 16 != 0 || !status || sms < 1) return cudaErrorInvalidValue;

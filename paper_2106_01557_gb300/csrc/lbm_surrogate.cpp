@@ -1,8 +1,9 @@
 // Host runtime of the learned surrogate: parameters (FP32 master copies,
 // Adam moments, BF16 forward and flipped copies), activation buffers, the
 // forward and backward passes built from the BF16 tensor-core kernels of
-// lbm_conv_tc.cu (tcgen05) or lbm_conv.cu (mma.sync; weight gradients and
-// the elementwise kernels), and the rollout with LB fallback.
+// lbm_conv_tc.cu (tcgen05: convolutions, 64 -> 64 weight gradients) or
+// lbm_conv.cu (mma.sync; the other weight gradients and the elementwise
+// kernels), and the rollout with LB fallback.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -153,6 +154,23 @@ static int conv(lbm_surrogate* s, int cin, int cout, const ConvArgs& a) {
     return LBM_OK;
 }
 
+// weight gradient: the 64 -> 64 layers on tcgen05 with the tensor-core path
+static int wgrad(lbm_surrogate* s, int cin, int cout, const __nv_bfloat16* in, const __nv_bfloat16* dout, int N,
+                 int H, int W, int relu, float* gw) {
+    if (s->cfg.conv_path == 0 && cin == 64 && cout == 64) {
+        SCK(launch_wgrad_tc(cin, cout, in, dout, N, H, W, relu, gw, s->gpart, s->stream, s->sms, s->d_status));
+    } else {
+        SCK(launch_wgrad(cin, cout, in, dout, N, H, W, relu, gw, s->gpart, s->stream, s->sms));
+    }
+    return LBM_OK;
+}
+
+#define WGRAD(cin, cout, in, dout, relu, gw)                          \
+    do {                                                              \
+        int rc_ = wgrad(s, cin, cout, in, dout, N, H, W, relu, gw);   \
+        if (rc_) return rc_;                                          \
+    } while (0)
+
 #define CONV(cin, cout, a)                \
     do {                                  \
         int rc_ = conv(s, cin, cout, a);  \
@@ -209,7 +227,7 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
     }
     // projection: its input is relu(h_B)
     Layer& proj = s->layers.back();
-    SCK(launch_wgrad(C, 16, s->h[B], s->dy16, N, H, W, 1, proj.gw, s->gpart, s->stream, s->sms));
+    WGRAD(C, 16, s->h[B], s->dy16, 1, proj.gw);
     SCK(launch_bgrad(s->dy16, P, 16, proj.gb, s->gpart, s->stream));
     ConvArgs a = cargs(s->dy16, proj.wflip, nullptr, N, H, W, 0);
     a.mask = s->h[B];
@@ -221,13 +239,13 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
         Layer& L1 = s->layers[1 + 2 * b];
         Layer& L2 = s->layers[2 + 2 * b];
         // h_{b+1} = h_b + conv2(relu(z1)); d z2 = d h_{b+1}
-        SCK(launch_wgrad(C, C, s->z1[b], dh, N, H, W, 1, L2.gw, s->gpart, s->stream, s->sms));
+        WGRAD(C, C, s->z1[b], dh, 1, L2.gw);
         SCK(launch_bgrad(dh, P, C, L2.gb, s->gpart, s->stream));
         a = cargs(dh, L2.wflip, nullptr, N, H, W, 0);
         a.mask = s->z1[b];
         a.out16 = s->g1;  // d z1
         CONV(C, C, a);
-        SCK(launch_wgrad(C, C, s->h[b], s->g1, N, H, W, 1, L1.gw, s->gpart, s->stream, s->sms));
+        WGRAD(C, C, s->h[b], s->g1, 1, L1.gw);
         SCK(launch_bgrad(s->g1, P, C, L1.gb, s->gpart, s->stream));
         a = cargs(s->g1, L1.wflip, nullptr, N, H, W, 0);
         a.mask = s->h[b];
@@ -237,7 +255,7 @@ static int run_backward(lbm_surrogate* s, int N, int H, int W) {
         std::swap(dh, spare);
     }
     Layer& lift = s->layers[0];
-    SCK(launch_wgrad(16, C, s->x16, dh, N, H, W, 0, lift.gw, s->gpart, s->stream, s->sms));
+    WGRAD(16, C, s->x16, dh, 0, lift.gw);
     SCK(launch_bgrad(dh, P, C, lift.gb, s->gpart, s->stream));
     return LBM_OK;
 }
