@@ -16,12 +16,22 @@
 //  4. The conservation sums of the state entering the step are reduced in
 //     FP64 (warp shuffles, then a fixed-order last-block pass), so the
 //     result is deterministic.
+//
+// With 16-bit storage the common case (no open sides, no cubic terms) runs
+// the pair form: 384 threads, each updating two neighbouring nodes (x, x + 1)
+// with the packed FP32 instructions (lbm_f2.cuh) and storing each population
+// of the pair as one 32-bit word. It issues a third fewer instructions per
+// node; the packed instructions take the FMA pipe for two cycles each, so
+// the step, bound by its FP32 arithmetic, gains only a few per cent.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
+#include "lbm_f2.cuh"
 #include "lbm_ptx.cuh"
 
 namespace lbm {
@@ -36,20 +46,21 @@ __host__ __device__ constexpr int EYf(int i) { return (i == 2 || i == 5 || i == 
 
 
 // Tile shape per storage type: BX x BY nodes, HX staged halo columns (16
-// bytes), NT threads, NS staging buffers per CTA, CPS resident CTAs per SM.
+// bytes), NT threads, NS staging buffers per CTA, CPS resident CTAs per SM;
+// NTP: threads of the pair form (16-bit storage; 0: not used).
 // With NS >= 2 the copies of the next NS - 1 tiles land while this one
 // computes; with NS = 1 and CPS = 2 the two CTAs of an SM cover each
 // other's waits.
 template <class S>
 struct Tile;
 template <>
-struct Tile<double> { static constexpr int BX = 32, BY = 16, HX = 2, NT = 512, NS = 2, CPS = 1; };
+struct Tile<double> { static constexpr int BX = 32, BY = 16, HX = 2, NT = 512, NS = 2, CPS = 1, NTP = 0; };
 template <>
-struct Tile<float> { static constexpr int BX = 64, BY = 16, HX = 4, NT = 512, NS = 2, CPS = 1; };
+struct Tile<float> { static constexpr int BX = 64, BY = 16, HX = 4, NT = 512, NS = 2, CPS = 1, NTP = 0; };
 template <>
-struct Tile<__half> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512, NS = 2, CPS = 1; };
+struct Tile<__half> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512, NS = 2, CPS = 1, NTP = 384; };
 template <>
-struct Tile<__nv_bfloat16> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512, NS = 2, CPS = 1; };
+struct Tile<__nv_bfloat16> { static constexpr int BX = 64, BY = 32, HX = 8, NT = 512, NS = 2, CPS = 1, NTP = 384; };
 
 template <class S, class C>
 struct Smem {
@@ -174,11 +185,131 @@ __device__ __forceinline__ void store_node(S* __restrict__ out, const Geometry& 
     }
 }
 
+// One population of a node pair (x even, x + 1) as stored: a 64-bit word of
+// two FP32 values, or a 32-bit word of two 16-bit values with node x in the
+// low half; nearest rounding (rn) or stochastic (sr, 32 random bits: the
+// upper 16 drive node x + 1, the lower 16 node x).
+template <class S>
+struct PairWord;
+template <>
+struct PairWord<float> {
+    using W = float2;
+    static __device__ __forceinline__ W rn(F2 v) { return v.v; }
+    static __device__ __forceinline__ W sr(F2 v, uint32_t) { return v.v; }
+};
+template <>
+struct PairWord<__half> {
+    using W = uint32_t;
+    static __device__ __forceinline__ W rn(F2 v) {
+        uint32_t d;
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x));
+        return d;
+    }
+    static __device__ __forceinline__ W sr(F2 v, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x), "r"(r));
+        return d;
+    }
+};
+template <>
+struct PairWord<__nv_bfloat16> {
+    using W = uint32_t;
+    static __device__ __forceinline__ W rn(F2 v) {
+        uint32_t d;
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x));
+        return d;
+    }
+    static __device__ __forceinline__ W sr(F2 v, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x), "r"(r));
+        return d;
+    }
+};
+
+// Two neighbouring staged values as FP32, p at an even element index: one
+// 32-bit (16-bit storage) or 64-bit (FP32) shared-memory load
+template <class S>
+__device__ __forceinline__ F2 ld_pair(const S* p);
+template <>
+__device__ __forceinline__ F2 ld_pair<float>(const float* p) { return F2(*reinterpret_cast<const float2*>(p)); }
+template <>
+__device__ __forceinline__ F2 ld_pair<__half>(const __half* p) {
+    return F2(__half22float2(*reinterpret_cast<const __half2*>(p)));
+}
+template <>
+__device__ __forceinline__ F2 ld_pair<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)));
+}
+// the same where the index parity is known at compile time: odd indices
+// take two loads
+template <class S, bool EVEN>
+__device__ __forceinline__ F2 ld_pair_at(const S* p) {
+    if constexpr (EVEN) return ld_pair<S>(p);
+    else return F2(Store<S, float>::raw(p[0]), Store<S, float>::raw(p[1]));
+}
+
+// Post-collision populations of the pair (x, x + 1) at row y. Pairs whose
+// nodes and ghost copies all lie inside the interior band store each
+// population as one word; the others (next to the edges of the lattice, or
+// with x + 1 outside it: v1 false) go node by node through store_node. With
+// stochastic rounding the interior pair draws its 18 words from one seed h
+// (multiplicative hashing with 18 fixed odd constants), the node-by-node
+// path from each node's own seed.
+template <class S>
+__device__ __forceinline__ void store_pair(S* __restrict__ out, const Geometry& G, const KC<float>& k, int x, int y,
+                                           bool v1, const F2 f[9], const F2 g[9], F2 rho, bool sr,
+                                           uint32_t step_key) {
+    const bool interior = v1 && x >= GHOST_COLS && x + 1 < G.nx - GHOST_COLS && y >= 2 && y < G.ny - 2;
+    if (interior) {
+        using PW = PairWord<S>;
+        using W = typename PW::W;
+        S* o = out + (long long)(y + 2) * G.pitch + G.PX + x;
+        if (Store<S, float>::SHIFTED && sr) {
+            const uint32_t h = fmix32((uint32_t)(y * G.nx + x) ^ step_key);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                *reinterpret_cast<W*>(o + i * G.plane) = PW::sr(f[i], h * (0x9e3779b9u * (2u * i + 1u)));
+                *reinterpret_cast<W*>(o + (9 + i) * G.plane) = PW::sr(g[i], h * (0x9e3779b9u * (2u * i + 19u)));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                *reinterpret_cast<W*>(o + i * G.plane) = PW::rn(f[i]);
+                *reinterpret_cast<W*>(o + (9 + i) * G.plane) = PW::rn(g[i]);
+            }
+        }
+        return;
+    }
+    float fl[9], gl[9];
+    NodeMacro<float> s;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        fl[i] = f[i].v.x;
+        gl[i] = g[i].v.x;
+    }
+    s.rho = rho.v.x;
+    store_node<S, float, false>(out, G, k, x, y, fl, gl, s, sr, fmix32((uint32_t)(y * G.nx + x) ^ step_key));
+    if (v1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            fl[i] = f[i].v.y;
+            gl[i] = g[i].v.y;
+        }
+        s.rho = rho.v.y;
+        store_node<S, float, false>(out, G, k, x + 1, y, fl, gl, s, sr,
+                                    fmix32((uint32_t)(y * G.nx + x + 1) ^ step_key));
+    }
+}
+
+// threads of a step CTA: the pair form takes half
+template <class S, bool PAIR>
+__host__ __device__ constexpr int step_threads() { return PAIR ? Tile<S>::NTP : Tile<S>::NT; }
+
 // OPEN: the case has open sides; CUBIC: the cubic-term elimination, with
 // phi = rho u_x^3, rho u_y^3 of the entering state (separate instantiations,
 // so that the common path carries none of their code)
-template <class S, class C, bool OPEN, bool CUBIC>
-__global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
+template <class S, class C, bool OPEN, bool CUBIC, bool PAIR>
+__global__ void __launch_bounds__(step_threads<S, PAIR>(), Tile<S>::CPS)
     k_step(const __grid_constant__ CUtensorMap tmf, const __grid_constant__ CUtensorMap tmg,
            S* __restrict__ out, const __grid_constant__ Launch L, double* __restrict__ partials,
            double* __restrict__ stats, unsigned* __restrict__ counter, int* __restrict__ status,
@@ -186,8 +317,10 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     using SM = Smem<S, C>;
     constexpr int BX = SM::BX, BY = SM::BY, HX = SM::HX, WX = SM::WX;
     constexpr int FR = SM::FR, GR = SM::GR, RX = SM::RX, RY = SM::RY;
-    constexpr int NT = Tile<S>::NT, NS = SM::NS;
-    static_assert(NT % BX == 0, "whole tile rows per thread sweep");
+    constexpr int NT = step_threads<S, PAIR>(), NS = SM::NS;
+    constexpr int TPR = PAIR ? BX / 2 : BX;  // threads per tile row
+    static_assert(NT % TPR == 0 && BX % 2 == 0, "whole tile rows per thread sweep");
+    static_assert(!PAIR || (std::is_same<C, float>::value && !OPEN && !CUBIC), "pair form: FP32 arithmetic, common case");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[SM::NS];
     __shared__ C red[NT / 32][7];
@@ -222,6 +355,7 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
     }
 
     Acc<C> acc = {0, 0, 0, 0, 0, 0, 0};
+    Acc<F2> acc2 = {0, 0, 0, 0, 0, 0, 0};  // pair form: one lane per node of the pair
     bool ok = true;
     int it = 0;
     // stochastic rounding of 16-bit storage: the step count (kept in the
@@ -254,6 +388,30 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
         // ---- density on tile + ring (pull sums from staged f) --------------
         // (after a timed-out wait these reads see stale data; the pass is
         // discarded at the barrier below)
+        if constexpr (PAIR) {
+            // node pairs (rx, rx + 1) of the ring-extended tile (RX even); the
+            // staged column of node rx - 1 + HX - e_x is even for e_x = +-1
+            static_assert(RX % 2 == 0 && HX % 2 == 0 && WX % 2 == 0, "pair alignment");
+#pragma unroll 1
+            for (int idx = tid; idx < (RX / 2) * RY; idx += NT) {
+                const int rx = 2 * (idx % (RX / 2)), ry = idx / (RX / 2);
+                const int gy = ty0 + ry - 1;
+                int sy = ry + 1;
+                if (G.walls) {
+                    if (gy < 0) sy -= gy;
+                    else if (gy >= G.ny) sy -= gy - (G.ny - 1);
+                }
+                const S* p = sf + sy * WX + rx - 1 + HX;
+                F2 r = F2(Store<S, C>::SHIFTED ? (float)k.mrest[0] : 0.f);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int o = i * FR * WX - EYf(i) * WX - EXf(i);
+                    if (EXf(i) != 0) r += ld_pair_at<S, true>(p + o);
+                    else r += ld_pair_at<S, false>(p + o);
+                }
+                *reinterpret_cast<float2*>(reinterpret_cast<float*>(srho) + ry * RX + rx) = r.v;
+            }
+        } else {
 #pragma unroll 1
         for (int idx = tid; idx < RX * RY; idx += NT) {
             const int rx = idx % RX, ry = idx / RX;
@@ -274,12 +432,72 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
             for (int i = 0; i < 9; ++i) r += Store<S, C>::raw(p[i * FR * WX - EYf(i) * WX - EXf(i)]);
             srho[idx] = r;
         }
+        }
         if (__syncthreads_or(timed_out)) { ok = false; break; }
         if (NS >= 2 && tid == 0) {
             const int ahead = tile + (NS - 1) * gridDim.x;  // tile it+NS-1 goes into the stage tile it-1 used
             if (it > 0 && ahead < ntiles) issue(ahead, (it - 1) % NS);
         }
 
+        if constexpr (PAIR) {
+            const int lx = 2 * (tid % TPR);
+            const int x = tx0 + lx;
+#pragma unroll 1
+            for (int ly = tid / TPR; ly < BY; ly += NT / TPR) {
+                const int y = ty0 + ly;
+                if (x >= G.nx || y >= G.ny) continue;
+                const bool v1 = x + 1 < G.nx;  // the pair's second node is in the lattice
+                F2 f[9], g[9], rn[9];
+                const S* pf = sf + (ly + 2) * WX + lx + HX;
+                const S* pg = sg + (ly + 1) * WX + lx + HX;
+                const float* pr = reinterpret_cast<const float*>(srho) + (ly + 1) * RX + lx + 1;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int of = i * FR * WX - EYf(i) * WX - EXf(i), og = i * GR * WX - EYf(i) * WX - EXf(i);
+                    // the staged column lx + HX - e_x is even for e_x = 0
+                    if (EXf(i) == 0) {
+                        f[i] = ld_pair_at<S, true>(pf + of);
+                        g[i] = ld_pair_at<S, true>(pg + og);
+                    } else {
+                        f[i] = ld_pair_at<S, false>(pf + of);
+                        g[i] = ld_pair_at<S, false>(pg + og);
+                    }
+                    // the density tile's pairs start on 8 bytes where x - 1 + e_x is even
+                    const int orr = EYf(i) * RX + EXf(i);
+                    if (EXf(i) != 0)
+                        rn[i] = F2(*reinterpret_cast<const float2*>(pr + orr));
+                    else
+                        rn[i] = F2(pr[orr], pr[orr + 1]);
+                }
+                NodeMacro<F2> s;
+                node_macro<Store<S, C>::SHIFTED>(k, f, g, rn, s);
+                {   // conservation record of the entering state (lane 1 only where v1)
+                    const F2 rho = s.rho;
+                    const F2 third = F2(1.0 / 3.0), twelfth = F2(1.0 / 12.0);
+                    const F2 lap = F2(2.0f) * (third * ((rn[1] + rn[2]) + (rn[3] + rn[4])) +
+                                               twelfth * ((rn[5] + rn[6]) + (rn[7] + rn[8])) - F2(5.0 / 3.0) * rho);
+                    F2 cm = rho, cx = rho * s.uhx, cy = rho * s.uhy, ce = s.rek;
+                    F2 et = s.rek - k.a * rho * rho - k.half_kappa * rho * lap;
+                    F2 u2 = s.uhx * s.uhx + s.uhy * s.uhy;
+                    const float r0 = rho.v.x, r1 = rho.v.y;
+                    F2 bad = F2(!(r0 > 0.f && r0 < 1e30f && u2.v.x < 1e30f) ? 1.f : 0.f,
+                                !(r1 > 0.f && r1 < 1e30f && u2.v.y < 1e30f) ? 1.f : 0.f);
+                    if (!v1) {
+                        cm.v.y = cx.v.y = cy.v.y = ce.v.y = et.v.y = u2.v.y = bad.v.y = 0.f;
+                    }
+                    acc2.mass += cm;
+                    acc2.mx += cx;
+                    acc2.my += cy;
+                    acc2.ek += ce;
+                    acc2.et += et;
+                    acc2.u2max = F2(u2.v.x > acc2.u2max.v.x ? u2.v.x : acc2.u2max.v.x,
+                                    u2.v.y > acc2.u2max.v.y ? u2.v.y : acc2.u2max.v.y);
+                    acc2.bad += bad;
+                }
+                collide<Store<S, C>::SHIFTED, false>(k, f, g, s, F2(0.f));
+                store_pair<S>(out, G, k, x, y, v1, f, g, s.rho, sr, step_key);
+            }
+        } else {
         const int lx = tid % BX;
         const int x = tx0 + lx;
 #pragma unroll 1
@@ -325,6 +543,7 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
             collide<Store<S, C>::SHIFTED, CUBIC>(k, f, g, s, R7);
             store_node<S, C, OPEN>(out, G, k, x, y, f, g, s, sr, fmix32((uint32_t)(y * G.nx + x) ^ step_key));
         }
+        }
         if (NS == 1) {
             __syncthreads();  // every thread is done with the stage: refill it
             if (tid == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, 0);
@@ -341,6 +560,16 @@ __global__ void __launch_bounds__(Tile<S>::NT, Tile<S>::CPS)
             const uint64_t t0 = globaltimer_ns();
             while (!mbar_try_wait(&bar[j % NS], (uint32_t)(j / NS) & 1u) && globaltimer_ns() - t0 < WAIT_NS) {}
         }
+    }
+
+    if constexpr (PAIR) {  // the pair lanes into the scalar record
+        acc.mass = acc2.mass.v.x + acc2.mass.v.y;
+        acc.mx = acc2.mx.v.x + acc2.mx.v.y;
+        acc.my = acc2.my.v.x + acc2.my.v.y;
+        acc.ek = acc2.ek.v.x + acc2.ek.v.y;
+        acc.et = acc2.et.v.x + acc2.et.v.y;
+        acc.u2max = acc2.u2max.v.x > acc2.u2max.v.y ? acc2.u2max.v.x : acc2.u2max.v.y;
+        acc.bad = acc2.bad.v.x + acc2.bad.v.y;
     }
 
     // ---- block reduction: compute type within warps, FP64 across warps -----
@@ -412,15 +641,16 @@ cudaError_t launch_t(const Launch& L, const CUtensorMap* tmf, const CUtensorMap*
     const int ntiles = ((L.geo.nx + SM::BX - 1) / SM::BX) * ((L.geo.ny + SM::BY - 1) / SM::BY);
     const int slots = Tile<S>::CPS * L.geo.sms;
     const int grid = ntiles < slots ? ntiles : slots;
+    constexpr bool P = Tile<S>::NTP > 0;  // the pair form for 16-bit storage
     if (L.geo.open)
-        k_step<S, C, true, false><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials,
-                                                                       stats, counter, status, phi);
+        k_step<S, C, true, false, false><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L,
+                                                                              partials, stats, counter, status, phi);
     else if (L.cubic)
-        k_step<S, C, false, true><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials,
-                                                                       stats, counter, status, phi);
+        k_step<S, C, false, true, false><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L,
+                                                                              partials, stats, counter, status, phi);
     else
-        k_step<S, C, false, false><<<grid, Tile<S>::NT, SM::BYTES, s>>>(*tmf, *tmg, static_cast<S*>(out), L, partials,
-                                                                        stats, counter, status, phi);
+        k_step<S, C, false, false, P><<<grid, step_threads<S, P>(), SM::BYTES, s>>>(
+            *tmf, *tmg, static_cast<S*>(out), L, partials, stats, counter, status, phi);
     return cudaGetLastError();
 }
 
@@ -453,11 +683,13 @@ size_t step_smem_bytes(int storage) {
 
 template <class S, class C>
 cudaError_t attr_t(int smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_step<S, C, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    constexpr bool P = Tile<S>::NTP > 0;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_step<S, C, false, false, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_step<S, C, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_step<S, C, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_step<S, C, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(k_step<S, C, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t prepare_step(int storage) {

@@ -30,6 +30,12 @@ def _fields(nx, ny, p, R, seed):
 def test_batch_equals_single_cases(gpu_lib, prec):
     from paper_2106_01557_gb300 import lbm
     cfgs = [lbm.default_config(nx, ny, precision=prec, Tr0=tr) for nx, ny, tr, _ in _cases()]
+    # 16-bit storage rounded to nearest: the single-lattice kernel draws the
+    # stochastic-rounding dither per node pair, the batch per node, so with
+    # stochastic rounding the two are compared through the oracle instead
+    # (test_batch_fp16_storage_matches_oracle, test_gpu_precision)
+    for c in cfgs:
+        c.rounding = 0
     singles = [lbm.Lattice(c) for c in cfgs]
     fields = []
     for k, (s, (nx, ny, tr, R)) in enumerate(zip(singles, _cases())):
@@ -47,7 +53,9 @@ def test_batch_equals_single_cases(gpu_lib, prec):
                 fb, gb = b.get_populations(i)
                 fs, gs = s.get_populations()
                 # FP16 storage rounds every population to 11 bits each step,
-                # so a rounding-order difference shows at that level
+                # so a difference in the last FP32 bit (the kernels fuse their
+                # products differently) shows at that level where it flips a
+                # rounding
                 tol = 1e-5 if prec == "f32" else 1e-2
                 assert rel_err(fb, fs) < tol and rel_err(gb, gs) < tol, (shape, order, i)
             b.close()
