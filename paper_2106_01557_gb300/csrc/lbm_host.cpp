@@ -454,9 +454,11 @@ static int make_maps(lbm_handle* h) {
                              : h->storage == S_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                              : h->storage == S_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    // map x = 0 is the first ghost column (row element PX - HX, 16-byte aligned)
+    // map x = 0 is the first ghost column (row element PX - HX, 16-byte aligned);
+    // the map ends after the right ghost block, so that a box reaching into
+    // the row padding reads the out-of-bounds fill instead of memory
     const int x0 = G.PX - G.HX;
-    cuuint64_t dims[3] = {(cuuint64_t)(G.pitch - x0), (cuuint64_t)G.nyp, 18};
+    cuuint64_t dims[3] = {(cuuint64_t)((G.nx > bx ? G.nx : bx) + 2 * G.HX), (cuuint64_t)G.nyp, 18};
     cuuint64_t strides[2] = {(cuuint64_t)G.pitch * h->esize, (cuuint64_t)G.plane * h->esize};
     cuuint32_t estr[3] = {1, 1, 1};
     cuuint32_t boxf[3] = {(cuuint32_t)(bx + 2 * hx), (cuuint32_t)(by + 4), 9};
@@ -1067,7 +1069,9 @@ int lbm_batch_init(const lbm_config* cfgs, int32_t ncases, lbm_batch** out) {
         for (int i = 0; i < ncases; ++i) {
             const Geometry& G = b->L[i].geo;
             const int x0 = G.PX - G.HX;  // map x = 0: the first ghost column
-            cuuint64_t dims[3] = {(cuuint64_t)(G.pitch - x0), (cuuint64_t)G.nyp, 18};
+            // up to the right ghost block: boxes of ragged tiles read the
+            // out-of-bounds fill, not the row padding
+            cuuint64_t dims[3] = {(cuuint64_t)((G.nx > bx ? G.nx : bx) + 2 * G.HX), (cuuint64_t)G.nyp, 18};
             cuuint64_t strides[2] = {(cuuint64_t)G.pitch * b->esize, (cuuint64_t)G.plane * b->esize};
             cuuint32_t estr[3] = {1, 1, 1};
             cuuint32_t boxf[3] = {(cuuint32_t)(bx + 2 * G.HX), (cuuint32_t)(by + 4), 9};
