@@ -309,6 +309,7 @@ __global__ void k_wgrad_sum(const float* __restrict__ part, int nblk, int cc, fl
         const int tp = e / cc, rem = e % cc;
         const int by = tp / 3, tl = tp % 3;
         float s = 0.f;
+#pragma unroll 8
         for (int b = 0; b < nblk; ++b) s += part[(((size_t)b * 3 + by) * 3 + tl) * cc + rem];
         dw[e] += s;
     }
@@ -343,21 +344,29 @@ __global__ void k_bgrad(const __nv_bfloat16* __restrict__ dout, long long P, int
 }
 
 // db[c] += sum over blocks b = 0, 1, ... of part[b][c]
+// One warp per channel: lane l adds the partials of blocks l, l + 32, ...
+// in that order, then a butterfly over the lanes; lane 0's result is the
+// same on every run (a fixed order, not a sequential one)
 __global__ void k_bgrad_sum(const float* __restrict__ part, int nblk, int C, float* __restrict__ db) {
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float t = 0.f;
-        for (int b = 0; b < nblk; ++b) t += part[(size_t)b * C + c];
-        db[c] += t;
-    }
+    const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) / 32), lane = threadIdx.x % 32;
+    if (c >= C) return;
+    float t = 0.f;
+    for (int b = lane; b < nblk; b += 32) t += part[(size_t)b * C + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) db[c] += t;
 }
 
-// *out += sum over i = 0 .. n-1 of part[i] (one thread, a fixed order)
+// *out += sum over i = 0 .. n-1 of part[i], by one warp in a fixed order
+// (lane l: i = l, l + 32, ...; then a butterfly)
 __global__ void k_sum_in_order(const double* __restrict__ part, int n, double* __restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < n; ++i) t += part[i];
-        *out += t;
-    }
+    const int lane = threadIdx.x;
+    if (blockIdx.x != 0 || lane >= 32) return;
+    double t = 0.0;
+    for (int i = lane; i < n; i += 32) t += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) *out += t;
 }
 
 // loss = mean over P pixels and 4 channels of (out - target)^2; dout = d loss / d out.
@@ -478,16 +487,25 @@ __global__ void k_mass_stats(const float* __restrict__ y, const float* __restric
     }
 }
 
+// one warp per image: lane l adds blocks l, l + 32, ..., then a butterfly
+// (a fixed order)
 __global__ void k_mass_sums(const double* __restrict__ part, int N, int nblk, int with_t, double* __restrict__ sums) {
-    const int n = threadIdx.x + blockIdx.x * blockDim.x;
+    const int n = (int)((blockIdx.x * blockDim.x + threadIdx.x) / 32), lane = threadIdx.x % 32;
     if (n >= N) return;
     double a = 0.0, b = 0.0;
-    for (int k = 0; k < nblk; ++k) {
+    for (int k = lane; k < nblk; k += 32) {
         a += part[((size_t)n * nblk + k) * 2];
         b += part[((size_t)n * nblk + k) * 2 + 1];
     }
-    sums[n] = a;
-    if (with_t) sums[N + n] = b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        sums[n] = a;
+        if (with_t) sums[N + n] = b;
+    }
 }
 
 __global__ void k_mass_apply(float* __restrict__ y, long long P, long long HW, const double* __restrict__ sums) {
@@ -622,7 +640,7 @@ cudaError_t launch_mass_layer(float* y, const float* x, const float* t, int N, l
     long long gx = (HW + 255) / 256;
     if (gx > MASS_BLOCKS) gx = MASS_BLOCKS;
     k_mass_stats<<<dim3((unsigned)gx, (unsigned)N), 256, 0, s>>>(y, x, t, N, HW, part);
-    k_mass_sums<<<(N + 127) / 128, 128, 0, s>>>(part, N, (int)gx, t != nullptr, sums);
+    k_mass_sums<<<(32 * N + 127) / 128, 128, 0, s>>>(part, N, (int)gx, t != nullptr, sums);
     const long long P = (long long)N * HW;
     long long g = (P + 255) / 256;
     if (g > 2048) g = 2048;
@@ -671,7 +689,7 @@ cudaError_t launch_bgrad(const __nv_bfloat16* dout, long long P, int C, float* d
     long long g = (P + per - 1) / per;
     if (g > 608) g = 608;
     k_bgrad<<<(unsigned)g, 256, 0, s>>>(dout, P, C, part);
-    k_bgrad_sum<<<1, 256, 0, s>>>(part, (int)g, C, db);
+    k_bgrad_sum<<<(C * 32 + 255) / 256, 256, 0, s>>>(part, (int)g, C, db);
     return cudaGetLastError();
 }
 

@@ -542,8 +542,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // y - 1, a share x of the (image, row, 128-pixel strip) chunks. Per chunk
 // the dOut row segment [128 pixels][64 co] and the input row segment
 // [130 pixels][64 ci] (one pixel of halo each side, periodic) land by
-// cp.async in one of two stages, both as 128-byte rows per pixel with the
-// tensor core's 128-byte swizzle. The contraction runs over pixels, so both
+// cp.async in one of WG_NS stages (the next chunk in flight while one is
+// multiplied), both as 128-byte rows per pixel with the tensor core's
+// 128-byte swizzle. The contraction runs over pixels, so both
 // operands are MN-major (the pixel index is the K index of their rows):
 //   D1[(dx, ci)][co], dx = -1, 0:  A = the input rows from pixel k (dx = -1)
 //       and the same rows one pixel on (dx = 0) as the two 64-row halves
@@ -562,7 +563,8 @@ constexpr int WG_PIX = 128;
 constexpr int WG_D_BYTES = WG_PIX * 128;                        // 16 KB
 constexpr int WG_X_BYTES = ((WG_PIX + 2) * 128 + 1023) / 1024 * 1024;  // 17 KB
 constexpr int WG_STAGE = WG_D_BYTES + WG_X_BYTES;
-constexpr int WG_BYTES = 2 * WG_STAGE + 1024;
+constexpr int WG_NS = 2;                                        // stages (a third measured slower)
+constexpr int WG_BYTES = WG_NS * WG_STAGE + 1024;
 
 __device__ __forceinline__ void wg_cp16(uint32_t dst, const void* src, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
                int in_relu, float* __restrict__ part, int* __restrict__ status) {
     constexpr int C = 64;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[WG_NS];
     __shared__ uint32_t tmem_base;
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = smem_u32(smem);
@@ -597,8 +599,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < WG_NS; ++b) mbar_init(&bar[b], 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -651,17 +652,19 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     uint32_t pending = 0;  // bit b: a commit to bar[b] not yet waited for
     int it = 0;
     long long ch = blockIdx.x;
-    load(ch, 0);
+    for (int j = 0; j < WG_NS - 1; ++j) load(ch + (long long)j * gridDim.x, j);
     for (; ch < nchunks; ch += gridDim.x, ++it) {
-        const int st = it & 1;
-        // the other stage is refilled once the MMAs of the chunk before have read it
+        const int st = it % WG_NS;
+        const int sp = (it + WG_NS - 1) % WG_NS;  // stage of chunk it - 1, refilled with chunk it + WG_NS - 1
+        // it is refilled once the MMAs of chunk it - 1 have read it
         if (it >= 1) {
-            const int late = tid == 0 && !bar_wait(&bar[st ^ 1], (uint32_t)((it - 1) >> 1) & 1u);
+            const int late = tid == 0 && !bar_wait(&bar[sp], (uint32_t)((it - 1) / WG_NS) & 1u);
             if (__syncthreads_or(late)) { ok = false; break; }
-            pending &= ~(1u << (st ^ 1));
+            pending &= ~(1u << sp);
         }
-        load(ch + gridDim.x, st ^ 1);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        load(ch + (long long)(WG_NS - 1) * gridDim.x, sp);
+        // one commit group per load: all but the newest WG_NS - 1 have landed
+        asm volatile("cp.async.wait_group %0;" ::"n"(WG_NS - 1) : "memory");
         if (in_relu) {
             __syncthreads();  // every thread's copies have landed
             relu_stage(st);
@@ -689,10 +692,10 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     // the last commits: every MMA done before the accumulators are read
     int late = 0;
     if (tid == 0)
-        for (uint32_t b = 0; b < 2; ++b)
+        for (int b = 0; b < WG_NS; ++b)
             if (pending & (1u << b)) {
-                const int last = (b == (uint32_t)((it - 1) & 1)) ? it - 1 : it - 2;
-                if (!bar_wait(&bar[b], (uint32_t)(last >> 1) & 1u)) late = 1;
+                const int last = b + WG_NS * ((it - 1 - b) / WG_NS);  // the last chunk in stage b
+                if (!bar_wait(&bar[b], (uint32_t)(last / WG_NS) & 1u)) late = 1;
             }
     if (__syncthreads_or(late)) ok = false;
     tc_fence_after();
