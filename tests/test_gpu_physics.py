@@ -5,22 +5,32 @@ temperatures. After 60,000 steps the pressure jump, from the EOS (Eq. 17) at
 each bulk's measured density and temperature, against 1/R (R the equimolar
 radius) has the slope of the surface tension that gradient theory gives for
 the configured K_EOS and K_INT (the paragraph after Eq. 19 prescribes
-sigma = 0.01 at T_r = 0.8 and reports 0.0101676 measured). The bound is 15%:
-the droplets end slightly warmer than the vapour (the total-energy drift of
-the scheme), and the liquid's stiff EOS turns that into a pressure error; the
-oracle's small-droplet pin is looser still (20%)."""
+sigma = 0.01 at T_r = 0.8 and reports 0.0101676 measured). Measured excess:
++9.3% at T_r 0.7 (wider rates), +6.7% at 0.8, +8.4% at 0.9, +6.6% at 0.8 with
+the cubic-term elimination (the droplets are at rest, so the u^3 terms it
+removes are negligible here). The bound is 12%: the droplets end slightly
+warmer than the vapour (the total-energy drift of the scheme), and the
+liquid's stiff EOS turns that into a pressure excess; the oracle's
+small-droplet pin is looser (20%)."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("tr", [0.7, 0.8, 0.9])
-def test_laplace_law_large_droplets(gpu_lib, tr):
+# T_r = 0.7 with the wider rates sigma_eps = 1.4, sigma_p = 1.8: with the
+# default rates the liquid is linearly unstable below T_r = 0.75; the last
+# case switches on the cubic-term elimination, as the paper's own runs do
+# (paragraph after Eq. 19)
+LAPLACE_CASES = [(0.7, dict(sig_eps=1.4, sig_p=1.8)), (0.8, {}), (0.9, {}), (0.8, dict(cubic=1))]
+
+
+@pytest.mark.parametrize("tr,opts", LAPLACE_CASES)
+def test_laplace_law_large_droplets(gpu_lib, tr, opts):
     from oracle import thermo
     from gpu_common import gpu_case, oracle_case
     N, steps = 512, 60000
-    o = oracle_case(N, N, Tr0=tr)
+    o = oracle_case(N, N, Tr0=tr, **opts)
     p = o.p
     K_EOS, K_INT = o.cfg.K_EOS, o.cfg.K_INT
     sigma, _ = thermo.surface_tension_and_width(p.T0, 1.0, 4.0, 1.0, K_EOS, K_INT)
@@ -30,7 +40,7 @@ def test_laplace_law_large_droplets(gpu_lib, tr):
     inv_r, dp = [], []
     for R in (40.0, 60.0, 80.0, 100.0):
         rho = thermo.planar_profile(p.T0, 1.0, 4.0, 1.0, K_EOS, K_INT, R - rr)
-        g = gpu_case(N, N, "f32", Tr0=tr)
+        g = gpu_case(N, N, "f32", Tr0=tr, **opts)
         g.set_fields(rho, 0 * rho, 0 * rho, 0 * rho + p.T0)
         g.step(steps)
         m = g.moments()
@@ -43,7 +53,8 @@ def test_laplace_law_large_droplets(gpu_lib, tr):
         # spurious currents stay small against the lattice speed
         assert np.hypot(m["ux"], m["uy"]).max() < 1e-2 * p.c
     slope, icpt = np.polyfit(np.array(inv_r), np.array(dp), 1)
-    assert slope == pytest.approx(sigma, rel=0.15)
+    print(f"T_r {tr} {opts}: Laplace slope / sigma - 1 = {slope / sigma - 1:+.4f}, intercept / dp_min = {icpt / min(dp):+.3f}")
+    assert slope == pytest.approx(sigma, rel=0.12)
     assert abs(icpt) < 0.2 * min(dp)
 
 
