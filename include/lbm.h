@@ -52,7 +52,7 @@ extern "C" {
 #define LBM_ERR_ARG (-1)      /* invalid argument or configuration */
 #define LBM_ERR_CUDA (-2)     /* a CUDA runtime or driver call failed */
 #define LBM_ERR_OOM (-3)      /* device or host allocation failed */
-#define LBM_ERR_DIVERGED (-4) /* non-finite or non-positive density seen */
+#define LBM_ERR_DIVERGED (-4) /* non-finite or non-positive density or temperature seen */
 #define LBM_ERR_TIMEOUT (-5)  /* a device-side wait ran out its bound */
 #define LBM_ERR_STATE (-6)    /* call not valid in the handle's state */
 #define LBM_ERR_IO (-7)       /* checkpoint file could not be read/written */
@@ -219,9 +219,11 @@ int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy,
 int lbm_conservation(lbm_handle* h, double out[6]);
 
 /* The same record, as reduced inside the most recent time step for the
- * state that step started from; out[6] = number of nodes with a non-finite
- * or non-positive density in it, out[7] = number of time steps the handle
- * has executed. Synchronous. */
+ * state that step started from; out[6] = number of nodes in it with a
+ * non-finite or non-positive density or temperature or a non-finite
+ * velocity (any such node makes the step's synchronising call return
+ * LBM_ERR_DIVERGED), out[7] = number of time steps the handle has
+ * executed. Synchronous. */
 int lbm_step_stats(lbm_handle* h, double out[8]);
 
 /* Read / write the post-streaming populations, host arrays [9][ny][nx]
@@ -428,7 +430,8 @@ int lbm_surrogate_destroy(lbm_surrogate* s);
  *          (the layout of lbm_get_populations), read only.
  *   out    device array of at least 7 doubles, written asynchronously:
  *          out[0..5] as lbm_conservation, out[6] the number of nodes with a
- *          non-finite or non-positive density.
+ *          non-finite or non-positive density or temperature or a
+ *          non-finite velocity.
  *   stream cudaStream_t to run on (NULL: the legacy default stream); the
  *          work runs on the calling thread's current device.
  * Scratch: a fixed device array inside the library (about 8.3 MiB on every

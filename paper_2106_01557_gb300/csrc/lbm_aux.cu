@@ -227,7 +227,10 @@ __global__ void __launch_bounds__(AUX_NT) k_moments(const Launch L, const S* __r
         acc[3] += (double)s.rek;
         acc[4] += (double)(s.rek - k.a * s.rho * s.rho - k.half_kappa * s.rho * lap);
         acc[5] = fmax(acc[5], (double)(k.c2 * (s.uhx * s.uhx + s.uhy * s.uhy)));
-        if (!(s.rho > C(0)) || !isfinite((double)s.rho)) acc[6] += 1.0;
+        // as the step kernel counts them: density, temperature, velocity (NaN included)
+        if (!(s.rho > C(0) && s.rho < C(1e30) && s.T > C(0) && s.T < C(1e30) &&
+              s.uhx * s.uhx + s.uhy * s.uhy < C(1e30)))
+            acc[6] += 1.0;
     }
     if (!partials) return;
     __shared__ double red[AUX_NT / 32][7];

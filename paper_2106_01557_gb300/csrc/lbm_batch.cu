@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(T::NT, 1)
                 a_et += s.rek - k.a * rho * rho - k.half_kappa * rho * lap;
                 const float u2 = s.uhx * s.uhx + s.uhy * s.uhy;
                 a_u2 = fmaxf(a_u2, u2);
-                if (!(rho > 0.f && rho < 1e30f && u2 < 1e30f)) a_bad += 1.f;  // also catches NaN
+                // as for a single case: density, temperature, velocity (NaN included)
+                if (!(rho > 0.f && rho < 1e30f && s.T > 0.f && s.T < 1e30f && u2 < 1e30f)) a_bad += 1.f;
             }
             // shifted formats: f and g leave the collision as deviations from the rest populations
             collide<Store<S, C>::SHIFTED>(k, f, g, s);

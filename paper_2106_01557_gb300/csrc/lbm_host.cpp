@@ -620,7 +620,7 @@ static int check_status(lbm_handle* h) {
     if (st) {
         CK(cudaMemset(h->status, 0, sizeof(int)));
         if (st & ST_TIMEOUT) return fail(LBM_ERR_TIMEOUT, "a device-side wait exceeded its bound");
-        if (st & ST_NONFINITE) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density");
+        if (st & ST_NONFINITE) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density or temperature");
     }
     return LBM_OK;
 }
@@ -755,7 +755,7 @@ int lbm_conservation(lbm_handle* h, double out[6]) {
     int rc = check_status(h);
     if (rc) return rc;
     for (int k = 0; k < 6; ++k) out[k] = s[k];
-    if (s[6] > 0) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density");
+    if (s[6] > 0) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density or temperature");
     return LBM_OK;
 }
 
@@ -1352,7 +1352,7 @@ int lbm_internal_read_fast(lbm_handle* h, double* fields, double out[6]) {
     int rc = check_status(h);
     if (rc) return rc;
     for (int k = 0; k < 6; ++k) out[k] = st[k];
-    if (st[6] > 0) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density");
+    if (st[6] > 0) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density or temperature");
     return LBM_OK;
 }
 

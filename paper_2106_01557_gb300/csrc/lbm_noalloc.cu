@@ -97,7 +97,9 @@ __global__ void __launch_bounds__(NA_NT) k_na_record(const Launch L, const doubl
         acc[3] += s.rek;
         acc[4] += s.rek - k.a * s.rho * s.rho - k.half_kappa * s.rho * lap;
         acc[5] = fmax(acc[5], k.c2 * (s.uhx * s.uhx + s.uhy * s.uhy));
-        if (!(s.rho > 0.0) || !isfinite(s.rho)) acc[6] += 1.0;
+        // as the step kernel counts them: density, temperature, velocity (NaN included)
+        if (!(s.rho > 0.0 && s.rho < 1e30 && s.T > 0.0 && s.T < 1e30 && s.uhx * s.uhx + s.uhy * s.uhy < 1e30))
+            acc[6] += 1.0;
     }
     __shared__ double red[NA_NT / 32][7];
     __shared__ bool last;

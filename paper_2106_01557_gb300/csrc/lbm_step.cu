@@ -479,9 +479,9 @@ __global__ void __launch_bounds__(step_threads<S, PAIR>(), Tile<S>::CPS)
                     F2 cm = rho, cx = rho * s.uhx, cy = rho * s.uhy, ce = s.rek;
                     F2 et = s.rek - k.a * rho * rho - k.half_kappa * rho * lap;
                     F2 u2 = s.uhx * s.uhx + s.uhy * s.uhy;
-                    const float r0 = rho.v.x, r1 = rho.v.y;
-                    F2 bad = F2(!(r0 > 0.f && r0 < 1e30f && u2.v.x < 1e30f) ? 1.f : 0.f,
-                                !(r1 > 0.f && r1 < 1e30f && u2.v.y < 1e30f) ? 1.f : 0.f);
+                    const float r0 = rho.v.x, r1 = rho.v.y, T0 = s.T.v.x, T1 = s.T.v.y;
+                    F2 bad = F2(!(r0 > 0.f && r0 < 1e30f && T0 > 0.f && T0 < 1e30f && u2.v.x < 1e30f) ? 1.f : 0.f,
+                                !(r1 > 0.f && r1 < 1e30f && T1 > 0.f && T1 < 1e30f && u2.v.y < 1e30f) ? 1.f : 0.f);
                     if (!v1) {
                         cm.v.y = cx.v.y = cy.v.y = ce.v.y = et.v.y = u2.v.y = bad.v.y = 0.f;
                     }
@@ -528,7 +528,9 @@ __global__ void __launch_bounds__(step_threads<S, PAIR>(), Tile<S>::CPS)
                 acc.et += s.rek - k.a * s.rho * s.rho - k.half_kappa * s.rho * lap;
                 const C u2 = s.uhx * s.uhx + s.uhy * s.uhy;
                 acc.u2max = u2 > acc.u2max ? u2 : acc.u2max;
-                if (!(rho > C(0) && rho < C(1e30) && u2 < C(1e30))) acc.bad += C(1);  // also catches NaN
+                // a non-positive or non-finite density or temperature, or a
+                // runaway velocity (the comparisons also catch NaN)
+                if (!(rho > C(0) && rho < C(1e30) && s.T > C(0) && s.T < C(1e30) && u2 < C(1e30))) acc.bad += C(1);
             }
             C R7 = C(0);
             if constexpr (CUBIC) {

@@ -227,6 +227,27 @@ def test_divergence_is_reported(gpu_lib):
     assert e.value.code == -4
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16s"])
+def test_negative_temperature_is_reported(gpu_lib, prec):
+    # a host-made fault in the energy field alone: one node's g populations
+    # set to minus their value (rho e_k < 0, so T < 0), the density untouched;
+    # the step's record counts it (out[6]) and the synchronising call reports
+    # divergence. The separate record of the state counts it too.
+    from paper_2106_01557_gb300 import lbm
+    o = oracle_case(64, 64)
+    fields = slab_fields(o, seed=13)
+    g = gpu_case(64, 64, prec)
+    g.set_fields(*fields)
+    f, gg = g.get_populations()
+    gg[:, 20, 30] = -gg[:, 20, 30]
+    g.set_populations(f, gg)
+    g.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        g.synchronize()
+    assert e.value.code == -4
+    assert g.step_stats()[6] >= 1
+
+
 def test_tile_wait_that_runs_out_is_reported(gpu_lib):
     # Failure detection of the step kernel's bounded waits, without a fault:
     # with a zero bound a tile whose copies have not landed when its turn
