@@ -603,7 +603,7 @@ cudaError_t wgrad_t(const __nv_bfloat16* in, const __nv_bfloat16* dout, int N, i
         set = true;
     }
     const long long chunks = (long long)N * H * ((W + WCH - 1) / WCH);
-    long long gx = (2 * sms + 2) / 3;  // with the three filter rows: about two CTAs per SM
+    long long gx = (2 * sms) / 3;  // with the three filter rows: two CTAs per SM, as in the tcgen05 path
     if (gx > chunks) gx = chunks;
     if (gx < 1) gx = 1;
     k_wgrad<CIN, COUT><<<dim3((unsigned)gx, 3), WT, 2 * Cf::STAGE, s>>>(in, dout, N, H, W, in_relu, part);

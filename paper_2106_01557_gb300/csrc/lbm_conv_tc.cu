@@ -563,7 +563,9 @@ constexpr int WG_PIX = 128;
 constexpr int WG_D_BYTES = WG_PIX * 128;                        // 16 KB
 constexpr int WG_X_BYTES = ((WG_PIX + 2) * 128 + 1023) / 1024 * 1024;  // 17 KB
 constexpr int WG_STAGE = WG_D_BYTES + WG_X_BYTES;
-constexpr int WG_NS = 2;                                        // stages (a third measured slower)
+constexpr int WG_NS = 2;     // stages (three, loading one or two chunks ahead, measured the same)
+constexpr int WG_AHEAD = 1;  // chunks loaded ahead: the stage refilled is that of chunk
+                             // it + WG_AHEAD - WG_NS
 constexpr int WG_BYTES = WG_NS * WG_STAGE + 1024;
 
 __device__ __forceinline__ void wg_cp16(uint32_t dst, const void* src, int src_bytes) {
@@ -590,7 +592,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int dy = (int)blockIdx.y - 1;
     const int tiles_x = (W + WG_PIX - 1) / WG_PIX;
-    const long long nchunks = (long long)N * H * tiles_x;
+    const int nchunks = N * H * tiles_x;  // below 2^31 (checked by the launcher)
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -613,11 +615,13 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
                            ((128u >> 4) << 24);
 
     // chunk ch into stage st: dOut row segment and halo'd input row segment
-    auto load = [&](long long ch, int st) {
+    // (32-bit index arithmetic: every thread works out the chunk's position)
+    auto load = [&](int ch, int st) {
         if (ch < nchunks) {
-            const int x0 = (int)(ch % tiles_x) * WG_PIX;
-            const long long ry = ch / tiles_x;  // n * H + y
-            const int y = (int)(ry % H), n = (int)(ry / H);
+            const unsigned ry = (unsigned)ch / (unsigned)tiles_x;  // n * H + y
+            const int x0 = (ch - (int)ry * tiles_x) * WG_PIX;
+            const unsigned n = ry / (unsigned)H;
+            const int y = (int)(ry - n * (unsigned)H);
             int yy = y + dy;
             yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
             const uint32_t sd = sbase + st * WG_STAGE, sx = sd + WG_D_BYTES;
@@ -651,20 +655,21 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     bool ok = true;
     uint32_t pending = 0;  // bit b: a commit to bar[b] not yet waited for
     int it = 0;
-    long long ch = blockIdx.x;
-    for (int j = 0; j < WG_NS - 1; ++j) load(ch + (long long)j * gridDim.x, j);
+    int ch = blockIdx.x;
+    for (int j = 0; j < WG_AHEAD; ++j) load(ch + j * (int)gridDim.x, j);
     for (; ch < nchunks; ch += gridDim.x, ++it) {
         const int st = it % WG_NS;
-        const int sp = (it + WG_NS - 1) % WG_NS;  // stage of chunk it - 1, refilled with chunk it + WG_NS - 1
-        // it is refilled once the MMAs of chunk it - 1 have read it
-        if (it >= 1) {
-            const int late = tid == 0 && !bar_wait(&bar[sp], (uint32_t)((it - 1) / WG_NS) & 1u);
+        const int sp = (it + WG_AHEAD) % WG_NS;  // refilled with chunk it + WG_AHEAD
+        const int prev = it + WG_AHEAD - WG_NS;  // the chunk that stage held
+        // it is refilled once the MMAs of that chunk have read it
+        if (prev >= 0) {
+            const int late = tid == 0 && !bar_wait(&bar[sp], (uint32_t)(prev / WG_NS) & 1u);
             if (__syncthreads_or(late)) { ok = false; break; }
             pending &= ~(1u << sp);
         }
-        load(ch + (long long)(WG_NS - 1) * gridDim.x, sp);
-        // one commit group per load: all but the newest WG_NS - 1 have landed
-        asm volatile("cp.async.wait_group %0;" ::"n"(WG_NS - 1) : "memory");
+        load(ch + WG_AHEAD * (int)gridDim.x, sp);
+        // one commit group per load: all but the newest WG_AHEAD have landed
+        asm volatile("cp.async.wait_group %0;" ::"n"(WG_AHEAD) : "memory");
         if (in_relu) {
             __syncthreads();  // every thread's copies have landed
             relu_stage(st);
@@ -760,7 +765,12 @@ cudaError_t launch_wgrad_tc(int cin, int cout, const __nv_bfloat16* in, const __
         set = true;
     }
     const long long chunks = (long long)N * H * ((W + WG_PIX - 1) / WG_PIX);
-    long long gx = (2 * sms + 2) / 3;  // with the three filter rows: about two blocks per SM
+    if (chunks + (long long)WG_NS * (2 * sms + 2) / 3 >= (1ll << 31)) return cudaErrorInvalidValue;  // 32-bit chunk indices
+    // with the three filter rows: two blocks per SM, all in one wave (the
+    // mma.sync weight gradient splits the pixels the same way, so the two
+    // paths sum the same partials in the same order)
+    long long gx = (2 * sms) / 3;
+    if (gx < 1) gx = 1;
     if (gx > chunks) gx = chunks;
     k_wgrad_tc<<<dim3((unsigned)gx, 3), WG_THREADS, WG_BYTES, s>>>(in, dout, N, H, W, in_relu, part, status);
     const cudaError_t e = cudaGetLastError();
