@@ -562,7 +562,8 @@ int lbm_surrogate_rollout(lbm_surrogate* s, lbm_handle* h, int32_t njumps, int32
             if (rc) return rc;
             tv = clk::now();
             // the LB re-runs from the surrogate state: a state it cannot
-            // advance (non-finite or non-positive density) is a rejected jump
+            // advance (non-finite or non-positive density or temperature) is a
+            // rejected jump
             if (verify_steps > 0) {
                 rc = lbm_step(h, verify_steps);
                 if (rc) return rc;
