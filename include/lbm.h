@@ -194,6 +194,12 @@ int lbm_coexistence(const lbm_config* cfg, double Tr, double dp, double out[3]);
  * the paper prescribes). Host only. */
 int lbm_surface_tension(const lbm_config* cfg, double Tr, double* sigma);
 
+/* The full EOS of cfg (Eq. 17: p = K_EOS (p_CS - a~ rho^2), p_CS the
+ * Carnahan-Starling term) at density rho and temperature T, both in the
+ * units lbm_moments reports (T absolute, not reduced). Host only;
+ * LBM_ERR_ARG for a null pointer or rho outside (0, 4 / b~). */
+int lbm_eos_pressure(const lbm_config* cfg, double rho, double T, double* p);
+
 /* Initial populations from macroscopic fields (rho, u_x, u_y, T), each
  * [ny][nx] double: m = m^eq - dt/2 F_m and n = n^eq - dt/2 q_m at every
  * node (SM Eq. S3, S4), so that Eq. 14 returns the given fields to the

@@ -601,6 +601,15 @@ int lbm_surface_tension(const lbm_config* cfg, double Tr, double* sigma) {
     return LBM_OK;
 }
 
+int lbm_eos_pressure(const lbm_config* cfg, double rho, double T, double* p) {
+    if (!cfg || !p) return fail(LBM_ERR_ARG, "null argument");
+    if (!(rho > 0.0 && rho < 4.0 / cfg->b_t) || !std::isfinite(T))
+        return fail(LBM_ERR_ARG, "density outside (0, 4 / b) or non-finite temperature");
+    Eos e{cfg->a_t, cfg->b_t, cfg->R, T};
+    *p = cfg->K_EOS * e.p(rho);
+    return LBM_OK;
+}
+
 int lbm_maxwell(const lbm_config* cfg, double Tr, double out[3]) {
     if (!cfg || !out) return fail(LBM_ERR_ARG, "null argument");
     if (!(Tr > 0.3 && Tr < 1.0)) return fail(LBM_ERR_ARG, "Tr must lie in (0.3, 1)");

@@ -93,6 +93,7 @@ SIGNATURES = {
     "lbm_maxwell": ([ctypes.POINTER(LbmConfig), ctypes.c_double, _DP], ctypes.c_int),
     "lbm_coexistence": ([ctypes.POINTER(LbmConfig), ctypes.c_double, ctypes.c_double, _DP], ctypes.c_int),
     "lbm_surface_tension": ([ctypes.POINTER(LbmConfig), ctypes.c_double, _DP], ctypes.c_int),
+    "lbm_eos_pressure": ([ctypes.POINTER(LbmConfig), ctypes.c_double, ctypes.c_double, _DP], ctypes.c_int),
     "lbm_batch_nodes": ([_H], ctypes.c_int64),
     "lbm_batch_step_count": ([_H], ctypes.c_int64),
     "lbm_batch_set_tile_wait": ([_H, ctypes.c_int64], ctypes.c_int),
@@ -186,6 +187,13 @@ def surface_tension(cfg: LbmConfig, Tr: float) -> float:
     """Planar surface tension at Tr from square-gradient theory (library host code)."""
     out = np.zeros(1)
     _check(load().lbm_surface_tension(ctypes.byref(cfg), float(Tr), _host_ptr(out)))
+    return float(out[0])
+
+
+def eos_pressure(cfg: LbmConfig, rho: float, T: float) -> float:
+    """The full EOS (Eq. 17) at density rho and temperature T (library host code)."""
+    out = np.zeros(1)
+    _check(load().lbm_eos_pressure(ctypes.byref(cfg), float(rho), float(T), _host_ptr(out)))
     return float(out[0])
 
 

@@ -141,6 +141,27 @@ def test_library_laplace_coexistence_and_surface_tension_on_host(lib):
     assert lbm.coexistence(cfg, 0.8, 0.0)[:2] == pytest.approx(lbm.maxwell(cfg, 0.8)[:2], rel=1e-14)
 
 
+def test_library_eos_pressure_on_host(lib):
+    # the library's Eq. 17 against the oracle's, on both branches and in the
+    # spinodal region, with K_EOS away from 1; it equals the saturation
+    # pressure at both Maxwell densities; out-of-range densities are refused
+    from oracle import thermo
+    from paper_2106_01557_gb300 import lbm
+    cfg = lbm.default_config(64, 64)
+    cfg.K_EOS = 0.7
+    Tc, _ = thermo.critical_point(1.0, 4.0, 1.0)
+    for Tr in (0.65, 0.8, 0.95):
+        T = Tr * Tc
+        for rho in (0.01, 0.1, 0.3, 0.6, 0.9):
+            assert lbm.eos_pressure(cfg, rho, T) == pytest.approx(thermo.p_eos(rho, T, 1.0, 4.0, 1.0, 0.7), rel=1e-13)
+        rv, rl, ps = lbm.maxwell(cfg, Tr)
+        assert lbm.eos_pressure(cfg, rv, T) == pytest.approx(ps, rel=1e-10)
+        assert lbm.eos_pressure(cfg, rl, T) == pytest.approx(ps, rel=1e-9)
+    for bad in (0.0, -0.1, 1.0, 2.0):
+        with pytest.raises(lbm.LbmError):
+            lbm.eos_pressure(cfg, bad, 0.1)
+
+
 def test_null_arguments_are_rejected_without_gpu(lib):
     # every entry point checks its handle and required pointers before any
     # device work: LBM_ERR_ARG, a no-op for the destroy calls, -1 or 0 for the
