@@ -16,6 +16,10 @@ Studies (one JSON line each, no timing contract):
   --batch-study STEPS      the 256-case sweep against the Maxwell densities
   --precision-study STEPS  the storage formats (16-bit with stochastic and
                            nearest rounding) side by side against FP64
+  --laplace-study STEPS    eight static droplets in one periodic 512 x 512 box
+                           at T/Tc 0.7, 0.8, 0.9: pressure jump against 1/R,
+                           spurious currents, FP32 against FP64
+  --stefan-study, --droplet-study N   the open heated sides (Eq. 20, D^2 law)
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload (the method has no exchange between independent cases); the value
@@ -501,6 +505,98 @@ def droplet_study(n=1024, D0=256.0, Tr1=0.85, cv=11.2, precision="f32", samples=
             "wall_s": time.perf_counter() - t_start, "fit": fit, "samples": rows}
 
 
+def _periodic_labels(mask):
+    """Connected components of a periodic 2-D mask (4-connectivity, labels
+    joined across both edges); 0 outside the mask."""
+    from scipy import ndimage
+    lab, n = ndimage.label(mask)
+    parent = list(range(n + 1))
+
+    def root(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+    for a, b in list(zip(lab[:, 0], lab[:, -1])) + list(zip(lab[0, :], lab[-1, :])):
+        if a and b:
+            ra, rb = root(a), root(b)
+            if ra != rb:
+                parent[max(ra, rb)] = min(ra, rb)
+    m = np.array([root(a) for a in range(n + 1)])
+    out = m[lab]
+    ids = [k for k in np.unique(out) if k]
+    return out, ids
+
+
+def laplace_study(steps=50_000, n=512, ndrop=8, seed=2, temps=(0.7, 0.8, 0.9), precisions=("f64", "f32")):
+    """Static droplets in one periodic box: ndrop droplets of radius
+    U[20, 80] (seeded, centres by rejection sampling with a periodic gap of
+    R1 + R2 + 8), tanh edges of width 4 between the Maxwell densities, u = 0,
+    uniform T, for `steps` steps at each T/Tc in `temps` (T/Tc = 0.7 with the
+    g rates sigma_eps = 1.4, sigma_p = 1.8, inside the model's stable range),
+    FP64 and FP32 storage. Per droplet (periodic connected components of
+    rho > (rho_v + rho_l) / 2): the interior state at its densest node, the
+    equimolar radius R = sqrt(A / pi) with A the sum of (rho - rho_vb) /
+    (rho_in - rho_vb) over the droplet grown by 4 nodes, and the pressure jump
+    p(rho_in, T_in) - p(rho_vb, T_vb) from Eq. 17 (library host code), rho_vb,
+    T_vb the medians over vapour nodes at least 12 nodes from any liquid. The
+    slope of dp against 1/R is compared with the square-gradient surface
+    tension at the vapour's temperature; spurious currents are max |u| / c."""
+    import torch
+    from scipy import ndimage
+    from paper_2106_01557_gb300 import inputs, lbm
+    rows = []
+    for tr in temps:
+        rates = SWEEP_RATES if tr < 0.75 else {}
+        res = {"Tr": tr, "rates": rates}
+        fields = {}
+        for prec in precisions:
+            cfg = lbm.default_config(n, n, precision=prec, Tr0=tr, **rates)
+            lat = lbm.Lattice(cfg)
+            p = lat.params()
+            centers, radii = inputs.place_droplets(n, n, ndrop, 20.0, 80.0, 8.0, seed)
+            rho = inputs.droplets(n, n, p["rho_v"], p["rho_l"], centers, radii, 4.0)
+            z = np.zeros_like(rho)
+            lat.set_fields(rho, z, z, z + p["T0"])
+            t0 = time.perf_counter()
+            lat.step(steps)
+            lat.synchronize()
+            wall = time.perf_counter() - t0
+            m = lat.moments()
+            lat.close()
+            r, T = m["rho"], m["T"]
+            fields[prec] = r
+            mid = 0.5 * (p["rho_v"] + p["rho_l"])
+            lab, ids = _periodic_labels(r > mid)
+            vap = ndimage.distance_transform_edt(r <= mid) >= 12.0
+            rvb, Tvb = float(np.median(r[vap])), float(np.median(T[vap]))
+            pv = lbm.eos_pressure(cfg, rvb, Tvb)
+            drops = []
+            for k in ids:
+                own = lab == k
+                iy, ix = np.unravel_index(np.argmax(np.where(own, r, -1.0)), r.shape)
+                rin, Tin = float(r[iy, ix]), float(T[iy, ix])
+                grown = ndimage.binary_dilation(own, iterations=4)
+                area = float(((r[grown] - rvb) / (rin - rvb)).sum())
+                R = math.sqrt(max(area, 1e-12) / math.pi)
+                drops.append({"R": R, "rho_in": rin, "T_in": Tin, "dp": lbm.eos_pressure(cfg, rin, Tin) - pv})
+            inv_r = np.array([1.0 / d["R"] for d in drops])
+            dp = np.array([d["dp"] for d in drops])
+            sigma = lbm.surface_tension(cfg, Tvb / p["Tc"])
+            slope, icpt = (np.polyfit(inv_r, dp, 1) if len(drops) >= 2 else (float("nan"), float("nan")))
+            umax = float(np.hypot(m["ux"], m["uy"]).max() / p["c"])
+            res[prec] = {"droplets_left": len(drops), "R_range": [min(d["R"] for d in drops), max(d["R"] for d in drops)],
+                         "slope_over_sigma_minus_1": float(slope / sigma - 1), "sigma_theory": sigma,
+                         "intercept_over_dp_min": float(icpt / dp.min()), "max_u_over_c": umax,
+                         "Tr_vapour": Tvb / p["Tc"], "wall_s": wall,
+                         "per_droplet": [{k: round(v, 6) for k, v in d.items()} for d in drops]}
+        if "f64" in fields and "f32" in fields:
+            res["f32_vs_f64_max_rho_err"] = float(np.abs(fields["f32"] - fields["f64"]).max() / fields["f64"].max())
+        rows.append(res)
+    return {"metric": "Laplace law, static droplets in one periodic box", "n": n, "droplets": ndrop,
+            "steps": steps, "seed": seed, "results": rows}
+
+
 def stefan_study(times=None, nx=8, ny=1024, precision="f64"):
     """The one-dimensional Stefan problem of Eq. 20, 21 at the paper's size
     (1024 nodes along the heating, 8 across), run to the four times of its
@@ -647,6 +743,8 @@ def main():
                     help="run FP64/FP32/FP16S/BF16S side by side to 1,000, 10,000 and this many steps; print the errors")
     ap.add_argument("--droplet-study", type=int, default=0,
                     help="box size n: a droplet of diameter n/4 evaporating in an n x n box heated on all sides")
+    ap.add_argument("--laplace-study", type=int, default=0,
+                    help="run eight static droplets in a periodic 512 x 512 box for this many steps (T/Tc 0.7, 0.8, 0.9; FP64 and FP32)")
     ap.add_argument("--stefan-study", action="store_true",
                     help="run the 1-D Stefan problem to the paper's Fig. 1 times and report the front against Eq. 20")
     ap.add_argument("--stefan-precision", default="f64", choices=["f64", "f32"])
@@ -666,6 +764,10 @@ def main():
     if args.batch_study:
         if rank == 0:
             print(json.dumps(batch_study(args.batch_study, precision=args.batch_precision)))
+        return
+    if args.laplace_study:
+        if rank == 0:
+            print(json.dumps(laplace_study(steps=args.laplace_study)))
         return
     if args.stefan_study:
         if rank == 0:
