@@ -20,6 +20,7 @@ Studies (one JSON line each, no timing contract):
                            at T/Tc 0.7, 0.8, 0.9: pressure jump against 1/R,
                            spurious currents, FP32 against FP64
   --stefan-study, --droplet-study N   the open heated sides (Eq. 20, D^2 law)
+  --droplet-pair-study N   the paper's evaporating droplet pair scaled to N x N
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload (the method has no exchange between independent cases); the value
@@ -505,6 +506,98 @@ def droplet_study(n=1024, D0=256.0, Tr1=0.85, cv=11.2, precision="f32", samples=
             "wall_s": time.perf_counter() - t_start, "fit": fit, "samples": rows}
 
 
+def droplet_pair_study(n=1024, stes=(0.005, 0.05, 0.5), Tr1=0.85, precision="f32", samples=40,
+                       max_steps=60_000_000, report=None):
+    """The paper's large-small droplet pair (diameters 160 and 96, centres 256
+    apart on 1024 x 1024, everything scaled by n / 1024) heated from all four
+    sides (open sides at T_r 0.85 and the liquid's saturation pressure, the
+    droplets at T_r 0.8), for each Stefan number in `stes`: Ste is set
+    through c_v (Ste = rho_v c_v (T_1 - T_0) / (rho_l h_lv) with the model's
+    latent heat h_lv); C_ref = rho_v c_v follows c_v, so the vapour's thermal
+    diffusivity alpha_v does not change and a larger Ste evaporates faster.
+    Samples, against t* = alpha_v t / D0^2 (D0 = 128 n / 1024): the total
+    liquid volume V / V0 (V0 = pi D0^2 / 4; V = sum (rho - rho_v) /
+    (rho_l - rho_v) over the liquid components grown by 4 nodes), the number
+    of droplets (connected components of rho above the mean of the two
+    coexistence densities, at least 20 nodes), the distance between the two
+    largest droplets' centroids, and max |u| / c. Each case runs at most four
+    times the quasi-steady lifetime estimate of the large droplet; `report`
+    (if given) receives each case's result as it completes."""
+    from scipy import ndimage
+    from paper_2106_01557_gb300 import inputs, lbm
+    s = n / 1024.0
+    DL, DS, sep, D0 = 160 * s, 96 * s, 256 * s, 128 * s
+    probe = lbm.Lattice(lbm.default_config(n, n, precision=precision, walls=1, open_sides=15, Tr_open=Tr1))
+    p1 = probe.params()
+    probe.close()
+    h_lv = p1["a"] * (p1["rho_l"] - p1["rho_v"]) + p1["p_s"] * (1 / p1["rho_v"] - 1 / p1["rho_l"])
+    out = []
+    for ste in stes:
+        cv = ste * p1["rho_l"] * h_lv / (p1["rho_v"] * (Tr1 * p1["Tc"] - p1["T0"]))
+        cfg = lbm.default_config(n, n, precision=precision, walls=1, open_sides=15, Tr_open=Tr1, c_v=cv)
+        lat = lbm.Lattice(cfg)
+        p = lat.params()
+        cy = n / 2 - 0.5
+        rho = inputs.droplets(n, n, p["rho_v"], p["rho_l"], [(n / 2 - sep / 2, cy), (n / 2 + sep / 2, cy)],
+                              [DL / 2, DS / 2], 4.0)
+        lat.set_fields(rho, 0 * rho, 0 * rho, 0 * rho + p["T0"])
+        alpha_v = (4 + 3 * cfg.gamma1 + 2 * cfg.gamma2) / 6 * p["Cref"] * p["c"] * cfg.tau_j_v / (p["rho_v"] * p["cv"])
+        ste_m = p["rho_v"] * p["cv"] * (Tr1 * p["Tc"] - p["T0"]) / (p["rho_l"] * h_lv)
+        life = DL * DL * math.log(1.08 * n / DL) / (8 * alpha_v * ste_m) / p["dt"]
+        every = max(200, int(life / samples))
+        cap = min(max_steps, int(4 * life))
+        mid = 0.5 * (p["rho_v"] + p["rho_l"])
+        rows, done, err, t0 = [], 0, None, time.perf_counter()
+        while done < cap:
+            m = lat.moments()
+            r = m["rho"]
+            lab, nl = ndimage.label(r > mid)
+            sizes = ndimage.sum(np.ones_like(r), lab, range(1, nl + 1)) if nl else []
+            comps = [k + 1 for k in range(nl) if sizes[k] >= 20]
+            phi = ((r - p["rho_v"]) / (p["rho_l"] - p["rho_v"]))
+            grown = ndimage.binary_dilation(np.isin(lab, comps), iterations=4) if comps else np.zeros_like(r, bool)
+            V = float(phi[grown].sum())
+            vols = sorted(((float(phi[lab == k].sum()), k) for k in comps), reverse=True)
+            dist = None
+            if len(vols) >= 2:
+                ca = ndimage.center_of_mass(phi.clip(0, None), lab, [vols[0][1], vols[1][1]])
+                dist = float(math.hypot(ca[0][0] - ca[1][0], ca[0][1] - ca[1][1]))
+            rows.append({"steps": done, "t_star": alpha_v * done * p["dt"] / D0 ** 2, "V_over_V0": V / (math.pi * D0 * D0 / 4),
+                         "droplets": len(comps), "distance": dist,
+                         "max_u_over_c": float(np.hypot(m["ux"], m["uy"]).max() / p["c"])})
+            if not comps or V < 0.02 * math.pi * D0 * D0 / 4:
+                break
+            lat.step(every)
+            try:
+                lat.synchronize()
+            except lbm.LbmError as e:
+                err = str(e)[:120]
+                break
+            done += every
+        lat.close()
+        d = [q["distance"] for q in rows if q["distance"] is not None]
+        two = [q for q in rows if q["droplets"] >= 2]
+        # coalescence: one droplet left, the pair having come closer than at the
+        # start, and no loss of volume across the transition (when the small
+        # droplet evaporates instead, its volume is gone)
+        merged = None
+        for a, b in zip(rows, rows[1:]):
+            if (a["droplets"] >= 2 and b["droplets"] == 1 and a["distance"] is not None and d
+                    and a["distance"] < d[0] and b["V_over_V0"] >= 0.97 * a["V_over_V0"]):
+                merged = b["t_star"]
+                break
+        out.append({"Ste": ste_m, "c_v": cv, "alpha_v": alpha_v, "steps_per_sample": every, "steps": done,
+                    "lifetime_estimate_steps": life, "wall_s": time.perf_counter() - t0, "error": err,
+                    "distance_initial": d[0] if d else None, "distance_min": min(d) if d else None,
+                    "distance_max": max(d) if d else None, "distance_last_pair": two[-1]["distance"] if two else None,
+                    "coalesced_at_t_star": merged, "V_over_V0_max": max(q["V_over_V0"] for q in rows),
+                    "t_star_end": rows[-1]["t_star"], "samples": rows})
+        if report:
+            report(out[-1])
+    return {"metric": "large-small droplet pair evaporating, heated from all sides", "lattice": [n, n],
+            "diameters": [DL, DS], "centre_distance": sep, "D0": D0, "storage": precision, "results": out}
+
+
 def _periodic_labels(mask):
     """Connected components of a periodic 2-D mask (4-connectivity, labels
     joined across both edges); 0 outside the mask."""
@@ -745,6 +838,8 @@ def main():
                     help="box size n: a droplet of diameter n/4 evaporating in an n x n box heated on all sides")
     ap.add_argument("--laplace-study", type=int, default=0,
                     help="run eight static droplets in a periodic 512 x 512 box for this many steps (T/Tc 0.7, 0.8, 0.9; FP64 and FP32)")
+    ap.add_argument("--droplet-pair-study", type=int, default=0,
+                    help="box size n: the paper's large-small droplet pair scaled by n/1024, Ste 0.005, 0.05, 0.5")
     ap.add_argument("--stefan-study", action="store_true",
                     help="run the 1-D Stefan problem to the paper's Fig. 1 times and report the front against Eq. 20")
     ap.add_argument("--stefan-precision", default="f64", choices=["f64", "f32"])
@@ -764,6 +859,12 @@ def main():
     if args.batch_study:
         if rank == 0:
             print(json.dumps(batch_study(args.batch_study, precision=args.batch_precision)))
+        return
+    if args.droplet_pair_study:
+        if rank == 0:
+            res = droplet_pair_study(n=args.droplet_pair_study,
+                                     report=lambda case: print(json.dumps({"case": case}), flush=True))
+            print(json.dumps({k: v for k, v in res.items() if k != "results"}))
         return
     if args.laplace_study:
         if rank == 0:

@@ -185,3 +185,26 @@ def test_droplet_heated_from_all_sides_follows_the_d2_law(gpu_lib):
     assert r2 > 0.995
     assert 0.4 < -k / qs < 1.6
     assert np.all((Tcen[sel] > 0.75) & (Tcen[sel] < 0.801))
+
+
+def test_droplet_pair_attracts_when_slow_and_repels_when_fast(gpu_lib):
+    # The paper's large-small droplet pair (text after Eq. 21, Fig. 3) at half
+    # its size: 512^2 heated from all four sides, diameters 80 and 48, centres
+    # 128 apart, Ste set through c_v. At Ste = 0.005 the evaporation is slow
+    # and the two droplets attract each other and coalesce (measured: the
+    # centres close from 128 to 86 and merge at t* = 11); at Ste = 0.5 it is
+    # fast, the vapour streaming out of the two facing surfaces pushes them
+    # apart (measured: 128 to 166) and the pair has evaporated by t* = 2.5,
+    # against t* = 264 at Ste = 0.005.
+    import bench
+    slow = bench.droplet_pair_study(n=512, stes=(0.005,), samples=400, max_steps=700_000)["results"][0]
+    assert slow["error"] is None
+    assert slow["coalesced_at_t_star"] is not None and slow["coalesced_at_t_star"] < 20
+    assert slow["distance_min"] < 0.8 * slow["distance_initial"]
+    fast = bench.droplet_pair_study(n=512, stes=(0.5,))["results"][0]
+    assert fast["error"] is None
+    assert fast["coalesced_at_t_star"] is None
+    assert fast["distance_max"] > 1.15 * fast["distance_initial"]
+    assert fast["samples"][-1]["V_over_V0"] < 0.05 and fast["t_star_end"] < 5
+    print(f"pair: Ste 0.005 closes to {slow['distance_min']:.1f} and merges at t* {slow['coalesced_at_t_star']:.2f}; "
+          f"Ste 0.5 opens to {fast['distance_max']:.1f}, gone at t* {fast['t_star_end']:.2f}")
