@@ -130,8 +130,8 @@ METRIC = "MLUPS of the fused f+g step (FP32 plain)"
 # DRAM bytes (read + write) of one k_step launch on this workload, from one
 # ncu capture (profiles/k_step_f32_4096x1024_full.md), valid only for the
 # kernel sources it was taken on: any change to them makes it null.
-STEP_TRAFFIC = {"bytes_per_launch": (309270528 + 255270912 + 308854528 + 253514752) // 2,
-                "sources_sha256": "d59e7c7ebbbcf13c82f2d6b4204e38414a76ec839ad31196c66cf54be143dc6c"}
+STEP_TRAFFIC = {"bytes_per_launch": (309504768 + 255359488 + 308919808 + 253383680) // 2,
+                "sources_sha256": "18fd04978bb82089b28181037507c512b5ec589d98fbbf17821c70b2b7e8fef6"}
 STEP_SOURCES = ["lbm_step.cu", "lbm_device.cuh", "lbm_internal.h", "lbm_ptx.cuh"]
 
 

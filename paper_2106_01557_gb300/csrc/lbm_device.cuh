@@ -483,13 +483,20 @@ __device__ __noinline__ void open_store(S* __restrict__ out, const Geometry& G, 
     C fe[9], ge[9], fo[9], go[9];
     eq_pops(k, rho, ux, uy, T, fe, ge);
     eq_pops(k, k.rho_open, ux, uy, k.T_open, fo, go);
-    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    // e_i / c of D2Q9 (SM Eq. S1); the loops are unrolled so that the choice of
+    // directions per ghost is made at compile time and the arrays stay in
+    // registers
+    constexpr int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;  // the node itself is not a ghost
             const int gx = x + dx, gy = y + dy;
             const bool ox = beyond_open(G, gx, y), oy = beyond_open(G, x, gy);
             if (!(ox || oy) || (dx != 0 && !ox) || (dy != 0 && !oy)) continue;
+#pragma unroll
             for (int i = 1; i < 9; ++i) {
                 if ((dx != 0 && ex[i] != -dx) || (dy != 0 && ey[i] != -dy)) continue;
                 if (beyond_open(G, gx + ex[i], gy + ey[i])) continue;
