@@ -285,9 +285,15 @@ class Lattice:
         _check(self.lib.lbm_moments(self.h, *(_host_ptr(res[k]) for k in ("rho", "ux", "uy", "T")), 0))
         return res
 
-    def conservation(self) -> np.ndarray:
+    def conservation(self, allow_diverged=False) -> np.ndarray:
+        """Mass, momentum, sum rho e_k, total energy, max |u| of the current
+        state; raises LbmError (LBM_ERR_DIVERGED) if a node has a
+        non-positive or non-finite density or temperature, unless
+        allow_diverged (the record is then returned all the same)."""
         out = np.zeros(6)
-        _check(self.lib.lbm_conservation(self.h, _host_ptr(out)))
+        rc = self.lib.lbm_conservation(self.h, _host_ptr(out))
+        if not (allow_diverged and rc == -4):
+            _check(rc)
         return out
 
     def step_stats(self) -> np.ndarray:
