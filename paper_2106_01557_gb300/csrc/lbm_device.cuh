@@ -154,6 +154,16 @@ __device__ __forceinline__ float ninth(float m) {
     return __fmaf_rn(m, hi, m * lo);
 }
 
+// With FP32 populations the rest population is taken as the complement of
+// the other eight, l_0 = m_0 - sum_{i >= 1} l_i: the nine then sum to m_0 up
+// to the rounding of that sum, where the back-transform's own roundings,
+// correlated across the nine values, leave a small bias in mass (f) and
+// energy (g) from step to step.
+template <class C>
+__device__ __forceinline__ void rest_as_complement(C m0, C l[9]) {
+    if constexpr (sizeof(C) == 4) l[0] = m0 - (((l[1] + l[2]) + (l[3] + l[4])) + ((l[5] + l[6]) + (l[7] + l[8])));
+}
+
 // l = M^-1 m = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m
 template <class C>
 __device__ __forceinline__ void populations9(const C m[9], C l[9]) {
@@ -357,6 +367,7 @@ __device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMa
         for (int q = 0; q < 3; ++q) mb[q] -= k.mrest[q];
     }
     populations9(mb, f);
+    if constexpr (!SH) rest_as_complement(mb[0], f);
 
     // ---- g: n_bar = n + dt q_m - L (n - n^eq + dt/2 q_m) + c^2 Y d -------
     const C E = s.rek, T = s.T, q = s.q;
@@ -389,6 +400,7 @@ __device__ __forceinline__ void collide(const K& k, C f[9], C g[9], const NodeMa
         for (int q = 0; q < 3; ++q) nb[q] -= k.nrest[q];
     }
     populations9(nb, g);
+    if constexpr (!SH) rest_as_complement(nb[0], g);
 }
 
 // Rest equilibrium of g for a fixed-temperature wall: M^-1 n^eq(rho_w c_v T_w,
